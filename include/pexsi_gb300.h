@@ -1,0 +1,229 @@
+/*
+ * pexsi_gb300.h -- C ABI of the GB300 (sm_103a) PEXSI hot path.
+ *
+ * The library computes, for a sparse symmetric pair (H, S) on a shared
+ * pattern, the selected elements (those on the pattern of H) of
+ *
+ *   DM  = Im sum_l w^rho_l (H - (z_l + mu) S)^{-1}     (Sec. II.A, Eq. gammapole)
+ *   EDM = Im sum_l w^E_l   (H - (z_l + mu) S)^{-1}     (Sec. II.A, Eq. gammaF)
+ *   FDM = Im sum_l w^F_l   (H - (z_l + mu) S)^{-1}     (Sec. II.A, Eq. gammaF)
+ *
+ * through a supernodal LDL^T factorisation of each complex-symmetric shifted
+ * matrix followed by selected inversion (Sec. II.B, steps 1-4), and the
+ * inertia count of real shifted matrices H - sigma S (Sec. II.C, Sylvester's
+ * law of inertia). Steps 1-2 (ordering, symbolic analysis) run on the host
+ * once per pattern in pexsi_setup; steps 3-4 and the pole sum run in CUDA
+ * kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *  - Patterns are 0-based CSC: colptr[n+1] (int64), rowind[nnz] (int32), row
+ *    indices strictly increasing within each column, every diagonal entry
+ *    present, and the pattern structurally symmetric (the FULL symmetric
+ *    pattern is stored, both triangles). It is the pattern of H; the pattern
+ *    of S must be a subset (store explicit zeros).
+ *  - Value arrays (H, S, DM, EDM, FDM) hold nnz float64 entries in that CSC
+ *    order. Selected-inverse outputs hold nnz complex values as interleaved
+ *    (re, im) float64 pairs.
+ *  - Every call returns PEXSI_OK (0) or a negative PEXSI_ERR_* code; no C++
+ *    exception crosses the ABI. pexsi_strerror() names a code and
+ *    pexsi_last_error_detail() gives the plan's last message.
+ *  - A plan is not thread-safe: callers serialise calls on one plan.
+ *  - "Host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory on the plan's device; `stream` is a cudaStream_t passed as
+ *    void* (NULL = the legacy default stream).
+ */
+#ifndef PEXSI_GB300_H
+#define PEXSI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+enum {
+  PEXSI_OK = 0,
+  PEXSI_ERR_INVALID_ARG = -1,   /* bad size, NULL where required, bad CSC      */
+  PEXSI_ERR_NOT_SYMMETRIC = -2, /* pattern not structurally symmetric          */
+  PEXSI_ERR_NOMEM = -3,         /* host or device allocation failed            */
+  PEXSI_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed */
+  PEXSI_ERR_BREAKDOWN = -5,     /* zero / non-finite pivot in a diagonal block */
+  PEXSI_ERR_INTERNAL = -6       /* violated internal invariant (a bug)         */
+};
+
+typedef struct pexsi_plan pexsi_plan;
+
+/* Options of pexsi_setup. Zero-initialised fields take the defaults that
+ * pexsi_opts_default() writes. */
+typedef struct pexsi_opts {
+  int32_t device;          /* CUDA device ordinal (default 0); -1 builds a host-only
+                              plan (ordering and symbolic analysis, no device memory)
+                              on which the numeric calls return INVALID_ARG          */
+  int32_t panel;           /* panel width b of the blocked front factorisation,
+                              16..64 (default 64)                                    */
+  int32_t leaf_cols;       /* nested-dissection leaf size in columns (default 96)    */
+  int32_t amalgamate;      /* 1: relaxed supernode amalgamation (default), 0: off    */
+  int32_t max_batch;       /* poles / shifts per device batch, 0 = automatic         */
+  int32_t reserved0;
+  int64_t hbm_budget;      /* bytes of device workspace the batch may use, 0 = auto  */
+} pexsi_opts;
+
+/* Symbolic statistics of a plan. Flop counts are algorithmic real flops of
+ * ONE pole (complex multiply-add = 8 flops) for the blocked front algorithm
+ * the kernels run; the diagonal-block inversions are counted separately. */
+typedef struct pexsi_plan_stats {
+  int64_t n, nnz;
+  int64_t nsuper;          /* supernodes (fronts) after amalgamation      */
+  int64_t nlevels;         /* height of the supernodal elimination tree   */
+  int64_t nnz_L;           /* entries of L below and on the diagonal      */
+  int64_t front_elems;     /* sum over fronts of m_K^2 (one pole)         */
+  int64_t max_front;       /* max m_K = s_K + r_K                         */
+  int64_t max_width;       /* max s_K                                     */
+  double factor_gemm_flops;/* panel solves + Schur (trailing) updates     */
+  double selinv_gemm_flops;/* Y(S,P) = -Y(S,S) L(S,P) and Y(P,P) updates  */
+  double diag_flops;       /* diagonal-block inversions                   */
+  double gather_bytes;     /* bytes moved by the Ainv(C,C) gathers, 1 pole*/
+  int64_t batch;           /* poles per device batch chosen for this plan */
+  int64_t workspace_bytes; /* device workspace at that batch              */
+} pexsi_plan_stats;
+
+/* Per-call report of pexsi_dm / pexsi_dm_device. */
+typedef struct pexsi_dm_info {
+  double trace_dm_s;       /* Tr[DM S] = N_e (Eq. Nmu); computed on the device   */
+  double trace_edm_s;      /* Tr[EDM S]                                          */
+  double trace_fdm_s;      /* Tr[FDM S] (grand potential)                        */
+  double min_pivot_ratio;  /* min over diagonal blocks of |pivot| / max |entry| */
+  double ms_total;         /* wall time of the call (device events)             */
+  double gemm_flops;       /* algorithmic GEMM flops executed by the call       */
+  int32_t n_poles;         /* poles evaluated by the call                       */
+  int32_t breakdown_front; /* front of the first breakdown, -1 if none          */
+} pexsi_dm_info;
+
+/* Fill *opts with the defaults. */
+int pexsi_opts_default(pexsi_opts* opts);
+
+/* Steps 1-2 of Sec. II.B: fill-reducing ordering (nested dissection on the
+ * supervariable graph, or the caller's permutation), elimination tree
+ * (Sec. II.B, Eq. parent), supernodes, front structure and the maps that the
+ * kernels use; then uploads the plan to the device.
+ *   n, colptr, rowind : the pattern (see conventions); the library copies it.
+ *   perm_or_null      : optional fill-reducing order, perm[new] = old; the
+ *                       library still post-orders it. NULL = own ordering.
+ *   opts              : NULL = defaults.
+ *   out               : receives the plan; free it with pexsi_plan_destroy.
+ * Errors: INVALID_ARG (bad CSC, missing diagonal, bad perm), NOT_SYMMETRIC,
+ * NOMEM, CUDA. On error *out is NULL. */
+int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind,
+                const int32_t* perm_or_null, const pexsi_opts* opts, pexsi_plan** out);
+
+/* Release the plan and all of its host and device memory. NULL is a no-op. */
+int pexsi_plan_destroy(pexsi_plan* plan);
+
+int pexsi_plan_get_stats(const pexsi_plan* plan, pexsi_plan_stats* stats);
+
+/* Write the final column order, perm[new] = old (n entries). */
+int pexsi_plan_get_perm(const pexsi_plan* plan, int32_t* perm);
+
+/* The pole expansion of Eq. polerho / Eq. gammaF (the construction the paper
+ * cites: contour quadrature of the Fermi-Dirac function around the spectrum
+ * through an elliptic-function map). For n_poles = P (even, >= 2) it writes
+ * P complex shifts z_l + mu (Im > 0) and the weights w^rho, w^E, w^F as
+ * interleaved (re, im) pairs, 2P doubles each. Any weight pointer may be
+ * NULL. Such that for eps in [mu - delta_e, mu + delta_e]:
+ *   2/(1+exp(beta (eps-mu)))          ~= Im sum_l w^rho_l / (eps - z_l)
+ *   eps * 2/(1+exp(beta (eps-mu)))    ~= Im sum_l w^E_l   / (eps - z_l)
+ *   -(2/beta) ln(1+exp(-beta(eps-mu)))~= Im sum_l w^F_l   / (eps - z_l)
+ * Errors: INVALID_ARG (P odd or < 2, beta or delta_e not positive). */
+int pexsi_pole_table(double beta, double delta_e, int32_t n_poles, double mu,
+                     double* z, double* w_rho, double* w_E, double* w_F);
+
+/* DM, EDM and FDM on the pattern for the P-pole expansion at (mu, beta,
+ * delta_e) -- Eq. gammapole and Eq. gammaF. Host buffers of nnz doubles; any
+ * output may be NULL. S == NULL means S = I (H's diagonal positions). The
+ * call is synchronous. On error the outputs are undefined.
+ * Errors: INVALID_ARG, NOMEM, CUDA, BREAKDOWN (info->breakdown_front). */
+int pexsi_dm(pexsi_plan* plan, const double* H, const double* S, double mu, double beta,
+             int32_t n_poles, double delta_e, double* dm, double* edm, double* fdm,
+             pexsi_dm_info* info);
+
+/* Host-buffer form over the pole subrange [pole_begin, pole_end) of the
+ * P-pole table (the end-to-end call: copies H and S to the device, computes,
+ * copies the outputs back; synchronous). accumulate = 1 adds to the outputs.
+ * Errors as pexsi_dm. */
+int pexsi_dm_poles(pexsi_plan* plan, const double* H, const double* S, double mu, double beta,
+                   int32_t n_poles, double delta_e, int32_t pole_begin, int32_t pole_end,
+                   int32_t accumulate, double* dm, double* edm, double* fdm, pexsi_dm_info* info);
+
+/* Device form of pexsi_dm over the pole subrange [pole_begin, pole_end) of
+ * the same P-pole table: dH, dS, d_dm, d_edm, d_fdm are device buffers of nnz
+ * doubles (dS may be NULL for S = I; outputs may be NULL). accumulate = 0
+ * overwrites the outputs, 1 adds this subrange's contribution to them. The
+ * work is enqueued on `stream`; the call returns after enqueueing unless
+ * info != NULL, in which case it synchronises `stream` to fill info. */
+int pexsi_dm_device(pexsi_plan* plan, const double* dH, const double* dS, double mu,
+                    double beta, int32_t n_poles, double delta_e, int32_t pole_begin,
+                    int32_t pole_end, int32_t accumulate, double* d_dm, double* d_edm,
+                    double* d_fdm, void* stream, pexsi_dm_info* info);
+
+/* Selected elements of (H - z S)^{-1} on the pattern for one complex shift z
+ * with Im z != 0 (one pole of Sec. II.A; also the LDOS kernel of Sec. II.D,
+ * Eq. LDOSGreen, with z = eps + i eta). Host buffers; ainv receives nnz
+ * interleaved complex values. Errors as pexsi_dm. */
+int pexsi_selinv(pexsi_plan* plan, const double* H, const double* S, double z_re,
+                 double z_im, double* ainv);
+
+/* Inertia counts (Sec. II.C): counts[m] = number of generalised eigenvalues
+ * of (H, S) below shifts[m] (per spin; N_infinity = 2 * counts), obtained as
+ * the number of negative eigenvalues of D in the real block LDL^T of
+ * H - shifts[m] S. Host buffers. A shift on (or numerically at) an
+ * eigenvalue gives BREAKDOWN; perturb it and retry. */
+int pexsi_inertia(pexsi_plan* plan, const double* H, const double* S, const double* shifts,
+                  int32_t n_shifts, int64_t* counts);
+
+/* Device form of pexsi_inertia: dH, dS device buffers; shifts and counts are
+ * host arrays; synchronises `stream` before returning. */
+int pexsi_inertia_device(pexsi_plan* plan, const double* dH, const double* dS,
+                         const double* shifts, int32_t n_shifts, int64_t* counts, void* stream);
+
+/* Supernodal structure of a plan (Sec. II.B, Eq. parent), new numbering:
+ * first[nsuper+1] first column of each supernode, rptr[nsuper+1] offsets of
+ * each off-diagonal row structure in rows[rptr[nsuper]] (ascending rows), and
+ * parent[nsuper] (-1 for roots). Sizes come from pexsi_plan_get_stats (nsuper)
+ * and this call with rows == NULL, which only writes first, rptr and parent. */
+int pexsi_plan_get_supernodes(const pexsi_plan* plan, int32_t* first, int64_t* rptr, int32_t* rows,
+                              int32_t* parent);
+
+/* Per-kernel-class timing (instrumentation, not part of the method). When
+ * enabled, every kernel launch of the plan is bracketed by CUDA events on the
+ * stream it runs on; pexsi_profile_read accumulates the elapsed times after
+ * the work has completed. Classes (index: name):
+ *   0 assemble, 1 extend_add, 2 diag_inv, 3 panel_solve, 4 schur_update,
+ *   5 gather, 6 selinv_offdiag, 7 selinv_diag_partial, 8 selinv_diag_reduce,
+ *   9 pole_sum, 10 trace
+ * flops / bytes are the algorithmic counts of the launches (complex
+ * multiply-add = 8 flops, real = 2; bytes = one read of each input element and
+ * one write of each output element). */
+typedef struct pexsi_kernel_profile {
+  char name[24];
+  int64_t launches;
+  double ms;
+  double flops;
+  double bytes;
+} pexsi_kernel_profile;
+
+#define PEXSI_PROFILE_CLASSES 11
+
+int pexsi_profile_enable(pexsi_plan* plan, int32_t on);
+/* Synchronises the plan's pending work, then writes PEXSI_PROFILE_CLASSES
+ * entries (totals since the last reset) into out. */
+int pexsi_profile_read(pexsi_plan* plan, pexsi_kernel_profile* out);
+int pexsi_profile_reset(pexsi_plan* plan);
+
+const char* pexsi_strerror(int code);
+const char* pexsi_last_error_detail(const pexsi_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PEXSI_GB300_H */

@@ -1,0 +1,312 @@
+"""ctypes binding of libpexsi_gb300.so (argument marshalling only).
+
+Every function carries the name of the C entry point it calls and does no
+arithmetic of the method: all numeric work runs in the library's CUDA
+kernels. There is no CPU fallback; if the library is missing the first call
+raises.
+
+Host arrays are numpy arrays; device buffers are passed as integer addresses
+(for example ``tensor.data_ptr()`` of a CUDA torch tensor) and streams as
+integer ``cudaStream_t`` handles (``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+c_int64_p = ctypes.POINTER(ctypes.c_int64)
+c_double_p = ctypes.POINTER(ctypes.c_double)
+
+ERR_NAMES = {0: "PEXSI_OK", -1: "PEXSI_ERR_INVALID_ARG", -2: "PEXSI_ERR_NOT_SYMMETRIC", -3: "PEXSI_ERR_NOMEM",
+             -4: "PEXSI_ERR_CUDA", -5: "PEXSI_ERR_BREAKDOWN", -6: "PEXSI_ERR_INTERNAL"}
+
+
+class PexsiError(RuntimeError):
+    def __init__(self, code: int, detail: str = ""):
+        self.code = code
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {detail}")
+
+
+class pexsi_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("panel", ctypes.c_int32), ("leaf_cols", ctypes.c_int32),
+                ("amalgamate", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_int64)]
+
+
+class pexsi_plan_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nsuper", ctypes.c_int64),
+                ("nlevels", ctypes.c_int64), ("nnz_L", ctypes.c_int64), ("front_elems", ctypes.c_int64),
+                ("max_front", ctypes.c_int64), ("max_width", ctypes.c_int64),
+                ("factor_gemm_flops", ctypes.c_double), ("selinv_gemm_flops", ctypes.c_double),
+                ("diag_flops", ctypes.c_double), ("gather_bytes", ctypes.c_double),
+                ("batch", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+class pexsi_dm_info(ctypes.Structure):
+    _fields_ = [("trace_dm_s", ctypes.c_double), ("trace_edm_s", ctypes.c_double),
+                ("trace_fdm_s", ctypes.c_double), ("min_pivot_ratio", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("n_poles", ctypes.c_int32), ("breakdown_front", ctypes.c_int32)]
+
+
+class pexsi_kernel_profile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+PROFILE_CLASSES = 11
+
+
+def _as_dict(st: ctypes.Structure) -> dict:
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+# (name, restype, argtypes) of every entry point declared in include/pexsi_gb300.h
+SIGNATURES = [
+    ("pexsi_opts_default", ctypes.c_int, [ctypes.POINTER(pexsi_opts)]),
+    ("pexsi_setup", ctypes.c_int, [ctypes.c_int64, c_int64_p, c_int32_p, c_int32_p, ctypes.POINTER(pexsi_opts),
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    ("pexsi_plan_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("pexsi_plan_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pexsi_plan_stats)]),
+    ("pexsi_plan_get_perm", ctypes.c_int, [ctypes.c_void_p, c_int32_p]),
+    ("pexsi_plan_get_supernodes", ctypes.c_int, [ctypes.c_void_p, c_int32_p, c_int64_p, c_int32_p, c_int32_p]),
+    ("pexsi_pole_table", ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                        c_double_p, c_double_p, c_double_p, c_double_p]),
+    ("pexsi_dm", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_int32, ctypes.c_double, c_double_p, c_double_p, c_double_p,
+                                ctypes.POINTER(pexsi_dm_info)]),
+    ("pexsi_dm_poles", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      c_double_p, c_double_p, c_double_p, ctypes.POINTER(pexsi_dm_info)]),
+    ("pexsi_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("pexsi_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pexsi_kernel_profile)]),
+    ("pexsi_profile_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("pexsi_dm_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(pexsi_dm_info)]),
+    ("pexsi_selinv", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double, ctypes.c_double,
+                                    c_double_p]),
+    ("pexsi_inertia", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_double_p, ctypes.c_int32,
+                                     c_int64_p]),
+    ("pexsi_inertia_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p,
+                                            ctypes.c_int32, c_int64_p, ctypes.c_void_p]),
+    ("pexsi_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("pexsi_last_error_detail", ctypes.c_char_p, [ctypes.c_void_p]),
+]
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1405_0194_gb300.build.build(); "
+                               "this package has no CPU fallback")
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _check(rc: int, plan=None):
+    if rc != 0:
+        detail = ""
+        if plan is not None:
+            d = lib().pexsi_last_error_detail(plan)
+            detail = d.decode() if d else ""
+        if not detail:
+            detail = lib().pexsi_strerror(rc).decode()
+        raise PexsiError(rc, detail)
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.shape[0] != n:
+        raise ValueError(f"expected {n} values, got {a.shape[0]}")
+    return a
+
+
+# ---------------------------------------------------------------- calls
+def pexsi_opts_default(**overrides) -> pexsi_opts:
+    o = pexsi_opts()
+    _check(lib().pexsi_opts_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def pexsi_setup(n, colptr, rowind, perm=None, opts: pexsi_opts | None = None):
+    """Returns an opaque plan handle (int)."""
+    colptr = np.ascontiguousarray(colptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(rowind, dtype=np.int32)
+    perm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    h = ctypes.c_void_p()
+    rc = lib().pexsi_setup(int(n), _ptr(colptr, ctypes.c_int64), _ptr(rowind, ctypes.c_int32),
+                           _ptr(perm, ctypes.c_int32), None if opts is None else ctypes.byref(opts), ctypes.byref(h))
+    _check(rc)
+    return h.value
+
+
+def pexsi_plan_destroy(plan):
+    _check(lib().pexsi_plan_destroy(plan))
+
+
+def pexsi_plan_get_stats(plan) -> dict:
+    st = pexsi_plan_stats()
+    _check(lib().pexsi_plan_get_stats(plan, ctypes.byref(st)), plan)
+    return _as_dict(st)
+
+
+def pexsi_plan_get_perm(plan) -> np.ndarray:
+    n = pexsi_plan_get_stats(plan)["n"]
+    perm = np.empty(n, dtype=np.int32)
+    _check(lib().pexsi_plan_get_perm(plan, _ptr(perm, ctypes.c_int32)), plan)
+    return perm
+
+
+def pexsi_plan_get_supernodes(plan):
+    """(first, rptr, rows, parent) of the supernodal structure."""
+    ns = pexsi_plan_get_stats(plan)["nsuper"]
+    first = np.empty(ns + 1, dtype=np.int32)
+    rptr = np.empty(ns + 1, dtype=np.int64)
+    parent = np.empty(ns, dtype=np.int32)
+    _check(lib().pexsi_plan_get_supernodes(plan, _ptr(first, ctypes.c_int32), _ptr(rptr, ctypes.c_int64), None,
+                                           _ptr(parent, ctypes.c_int32)), plan)
+    rows = np.empty(int(rptr[-1]), dtype=np.int32)
+    _check(lib().pexsi_plan_get_supernodes(plan, _ptr(first, ctypes.c_int32), _ptr(rptr, ctypes.c_int64),
+                                           _ptr(rows, ctypes.c_int32), _ptr(parent, ctypes.c_int32)), plan)
+    return first, rptr, rows, parent
+
+
+def pexsi_pole_table(beta, delta_e, n_poles, mu=0.0) -> dict:
+    """Shifts z_l + mu and weights (complex numpy arrays of length n_poles)."""
+    bufs = [np.empty(2 * n_poles) for _ in range(4)]
+    rc = lib().pexsi_pole_table(float(beta), float(delta_e), int(n_poles), float(mu),
+                                *[_ptr(b, ctypes.c_double) for b in bufs])
+    _check(rc)
+    z, wr, we, wf = [b.view(np.complex128) for b in bufs]
+    return {"z": z, "w_rho": wr, "w_E": we, "w_F": wf}
+
+
+def pexsi_dm(plan, H, S, mu, beta, n_poles, delta_e, want=("dm", "edm", "fdm")):
+    """Host-buffer DM/EDM/FDM. Returns (dm, edm, fdm, info); unwanted outputs are None."""
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _f64(H, nnz)
+    S = None if S is None else _f64(S, nnz)
+    outs = {k: (np.empty(nnz) if k in want else None) for k in ("dm", "edm", "fdm")}
+    info = pexsi_dm_info()
+    rc = lib().pexsi_dm(plan, _ptr(H, ctypes.c_double), _ptr(S, ctypes.c_double), float(mu), float(beta),
+                        int(n_poles), float(delta_e), _ptr(outs["dm"], ctypes.c_double),
+                        _ptr(outs["edm"], ctypes.c_double), _ptr(outs["fdm"], ctypes.c_double), ctypes.byref(info))
+    _check(rc, plan)
+    return outs["dm"], outs["edm"], outs["fdm"], _as_dict(info)
+
+
+def pexsi_dm_poles(plan, H, S, mu, beta, n_poles, delta_e, pole_begin, pole_end, accumulate=0, dm=None, edm=None,
+                   fdm=None):
+    """Host-buffer DM/EDM/FDM over a pole subrange. ``dm``/``edm``/``fdm`` are
+    float64 numpy arrays of nnz (or None to skip); they are written (or added
+    to when ``accumulate``). Returns the info dict."""
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _f64(H, nnz) if not (isinstance(H, np.ndarray) and H.flags.c_contiguous and H.dtype == np.float64) else H
+    if S is not None and not (isinstance(S, np.ndarray) and S.flags.c_contiguous and S.dtype == np.float64):
+        S = _f64(S, nnz)
+    for a in (dm, edm, fdm):
+        if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous or a.shape[0] != nnz):
+            raise ValueError("outputs must be contiguous float64 arrays of nnz")
+    info = pexsi_dm_info()
+    rc = lib().pexsi_dm_poles(plan, _ptr(H, ctypes.c_double), _ptr(S, ctypes.c_double), float(mu), float(beta),
+                              int(n_poles), float(delta_e), int(pole_begin), int(pole_end), int(accumulate),
+                              _ptr(dm, ctypes.c_double), _ptr(edm, ctypes.c_double), _ptr(fdm, ctypes.c_double),
+                              ctypes.byref(info))
+    _check(rc, plan)
+    return _as_dict(info)
+
+
+def pexsi_profile_enable(plan, on=True):
+    _check(lib().pexsi_profile_enable(plan, int(bool(on))), plan)
+
+
+def pexsi_profile_reset(plan):
+    _check(lib().pexsi_profile_reset(plan), plan)
+
+
+def pexsi_profile_read(plan) -> list:
+    """Per-kernel-class totals: list of dicts (name, launches, ms, flops, bytes)."""
+    arr = (pexsi_kernel_profile * PROFILE_CLASSES)()
+    _check(lib().pexsi_profile_read(plan, arr), plan)
+    return [{"name": a.name.decode(), "launches": a.launches, "ms": a.ms, "flops": a.flops, "bytes": a.bytes}
+            for a in arr]
+
+
+def pexsi_dm_device(plan, dH, dS, mu, beta, n_poles, delta_e, pole_begin, pole_end, accumulate, d_dm, d_edm, d_fdm,
+                    stream=0, want_info=False):
+    """Device-buffer form; pointers and stream are integers (0 / None = NULL)."""
+    info = pexsi_dm_info() if want_info else None
+    rc = lib().pexsi_dm_device(plan, dH or None, dS or None, float(mu), float(beta), int(n_poles), float(delta_e),
+                               int(pole_begin), int(pole_end), int(accumulate), d_dm or None, d_edm or None,
+                               d_fdm or None, stream or None, None if info is None else ctypes.byref(info))
+    _check(rc, plan)
+    return None if info is None else _as_dict(info)
+
+
+def pexsi_selinv(plan, H, S, z) -> np.ndarray:
+    """Selected elements of (H - z S)^{-1} on the pattern (complex, CSC order)."""
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _f64(H, nnz)
+    S = None if S is None else _f64(S, nnz)
+    out = np.empty(2 * nnz)
+    rc = lib().pexsi_selinv(plan, _ptr(H, ctypes.c_double), _ptr(S, ctypes.c_double), float(np.real(z)),
+                            float(np.imag(z)), _ptr(out, ctypes.c_double))
+    _check(rc, plan)
+    return out.view(np.complex128)
+
+
+def pexsi_inertia(plan, H, S, shifts) -> np.ndarray:
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _f64(H, nnz)
+    S = None if S is None else _f64(S, nnz)
+    shifts = _f64(np.atleast_1d(shifts))
+    counts = np.empty(shifts.shape[0], dtype=np.int64)
+    rc = lib().pexsi_inertia(plan, _ptr(H, ctypes.c_double), _ptr(S, ctypes.c_double), _ptr(shifts, ctypes.c_double),
+                             int(shifts.shape[0]), _ptr(counts, ctypes.c_int64))
+    _check(rc, plan)
+    return counts
+
+
+def pexsi_inertia_device(plan, dH, dS, shifts, stream=0) -> np.ndarray:
+    shifts = _f64(np.atleast_1d(shifts))
+    counts = np.empty(shifts.shape[0], dtype=np.int64)
+    rc = lib().pexsi_inertia_device(plan, dH or None, dS or None, _ptr(shifts, ctypes.c_double),
+                                    int(shifts.shape[0]), _ptr(counts, ctypes.c_int64), stream or None)
+    _check(rc, plan)
+    return counts
+
+
+def pexsi_strerror(code: int) -> str:
+    return lib().pexsi_strerror(int(code)).decode()
+
+
+def pexsi_last_error_detail(plan) -> str:
+    d = lib().pexsi_last_error_detail(plan)
+    return d.decode() if d else ""

@@ -1,0 +1,726 @@
+// CUDA kernels of the multifrontal LDL^T factorisation and selected inversion
+// (Sec. II.B, steps 3-4) and of the pole sum (Eq. gammapole, Eq. gammaF).
+//
+// Storage: every front K of every batch member is an m_K x m_K column-major
+// block in a pool (one pool per batch member, `pool` elements apart).
+//   factor pool F: lower triangle = the front; after the panel loop its first
+//     s_K columns hold L (unit lower, diagonal blocks overwritten by D^{-1} of
+//     each panel) and its trailing r_K x r_K block the Schur complement that
+//     the parent assembles. The upper triangle holds W^T = (L D)^T of the
+//     current panel (the unscaled panel the Schur update needs).
+//   inverse pool Y: the full (both triangles) selected inverse restricted to
+//     the front's rows and columns, Ainv(K u C_K, K u C_K).
+//
+// Panel algorithm for front K (panel of width bb at p0, rows below q0 = p0+bb):
+//   D = F[P,P];  F[P,P] <- D^{-1}                      (in-block pivoting)
+//   W = F[S,P];  F[P,S] <- W^T;  F[S,P] <- L = W D^{-1}
+//   F[S,S] -= L W^T                                   (lower triangle)
+// Selected inversion for K, panels from last to first (Takahashi recursion,
+// derived from A^{-1} = L^{-T} D^{-1} L^{-1}):
+//   Y[C,C]  <- gathered from the parent's Y through the relative indices
+//   Y[S,P]  = -Y[S,S] L[S,P];   Y[P,S] = Y[S,P]^T
+//   Y[P,P]  = D^{-1} - L[S,P]^T Y[S,P]
+#include <cfloat>
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace pexsi {
+namespace {
+
+// ------------------------------------------------------------ arithmetic
+__device__ __forceinline__ double zero_of(double) { return 0.0; }
+__device__ __forceinline__ double2 zero_of(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double one_of(double) { return 1.0; }
+__device__ __forceinline__ double2 one_of(double2) { return make_double2(1.0, 0.0); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double2 fmac(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double mulv(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 mulv(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double subv(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 subv(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double addv(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 addv(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double negv(double a) { return -a; }
+__device__ __forceinline__ double2 negv(double2 a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ double scalev(double a, double s) { return a * s; }
+__device__ __forceinline__ double2 scalev(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double absv(double a) { return fabs(a); }
+__device__ __forceinline__ double absv(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double recipv(double a) { return 1.0 / a; }
+__device__ __forceinline__ double2 recipv(double2 a) {
+  // 1/(x+iy) with scaling against overflow (Smith's method)
+  if (fabs(a.x) >= fabs(a.y)) {
+    double r = a.y / a.x, d = a.x + a.y * r;
+    return make_double2(1.0 / d, -r / d);
+  }
+  double r = a.x / a.y, d = a.x * r + a.y;
+  return make_double2(r / d, -1.0 / d);
+}
+__device__ __forceinline__ bool finitev(double a) { return isfinite(a); }
+__device__ __forceinline__ bool finitev(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+template <typename T> __device__ __forceinline__ T make_shift(double h, double s, const BatchShifts& sh, int b);
+template <> __device__ __forceinline__ double make_shift<double>(double h, double s, const BatchShifts& sh, int b) {
+  return fma(-sh.re[b], s, h);
+}
+template <> __device__ __forceinline__ double2 make_shift<double2>(double h, double s, const BatchShifts& sh, int b) {
+  return make_double2(fma(-sh.re[b], s, h), -sh.im[b] * s);
+}
+
+// lower-triangle tile index t -> (I, J), I >= J
+__device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
+  int i = int((sqrt(8.0 * double(t) + 1.0) - 1.0) * 0.5);
+  while (i * (i + 1) / 2 > t) --i;
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  I = i;
+  J = t - i * (i + 1) / 2;
+}
+
+// ------------------------------------------------------------ GEMM tile
+// acc[i][j] += sum_k A(r, k) B(k, c) for the 64 x 64 output tile, r = tx + 16 i,
+// c = ty + 16 j (tx = tid & 15, ty = tid >> 4, 256 threads).
+// A(r, k) is A[r + lda k] (AT = false) or A[k + lda r] (AT = true);
+// B(k, c) is B[k + ldb c]. Rows >= Mv, columns >= Nv and k >= K read as 0.
+constexpr int kKc = 16;      // k-chunk staged per step
+constexpr int kLd = 65;      // padded smem row stride (elements)
+
+template <typename T, bool AT>
+__device__ __forceinline__ void gemm_tile(T (&acc)[4][4], const T* __restrict__ A, int64_t lda,
+                                          const T* __restrict__ B, int64_t ldb, int Mv, int Nv, int K, T* As,
+                                          T* Bs) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const T z = zero_of(T());
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q, r, k;
+      if (!AT) { r = idx & 63; k = idx >> 6; }
+      else { k = idx & 15; r = idx >> 4; }
+      T v = z;
+      if (r < Mv && k0 + k < K) v = AT ? A[(k0 + k) + lda * r] : A[r + lda * (k0 + k)];
+      As[k * kLd + r] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q, k = idx & 15, c = idx >> 4;
+      T v = z;
+      if (c < Nv && k0 + k < K) v = B[(k0 + k) + ldb * c];
+      Bs[k * kLd + c] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kKc; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k * kLd + tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k * kLd + ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmac(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void zero_acc(T (&acc)[4][4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = zero_of(T());
+}
+
+// ------------------------------------------------------------ assembly
+template <typename T>
+__global__ void k_assemble(T* __restrict__ F, const double* __restrict__ H, const double* __restrict__ S,
+                           const int64_t* __restrict__ src, const int64_t* __restrict__ pos, int64_t nlow,
+                           int64_t pool, BatchShifts sh) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < nlow; t += int64_t(gridDim.x) * blockDim.x) {
+    int64_t e = src[t], p = pos[t];
+    double h = H[e], s = S[e];
+    for (int b = 0; b < sh.nb; ++b) F[b * pool + p] = make_shift<T>(h, s, sh, b);
+  }
+}
+
+// U_c (trailing r x r lower block of child c) added into the parent front.
+template <typename T>
+__global__ void k_extend_add(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ children, int nchild) {
+  const int ci = blockIdx.y;
+  if (ci >= nchild) return;
+  const int c = children[ci];
+  const int64_t base = int64_t(blockIdx.z) * fr.pool;
+  const int s = fr.s[c], m = fr.m[c], r = m - s;
+  const int P = fr.parent[c];
+  const int mP = fr.m[P];
+  const int Tn = (r + 31) / 32;
+  if (int(blockIdx.x) >= Tn * (Tn + 1) / 2) return;
+  int I, J;
+  tri_tile(blockIdx.x, I, J);
+  const T* Fc = F + base + fr.off[c];
+  T* Fp = F + base + fr.off[P];
+  const int32_t* rel = fr.rel + fr.rptr[c];
+  const int i = I * 32 + threadIdx.x;
+  if (i >= r) return;
+  const int64_t ri = rel[i];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int j = J * 32 + threadIdx.y + 8 * q;
+    if (j < r && j <= i) {
+      T u = Fc[(s + i) + int64_t(m) * (s + j)];
+      T* d = Fp + ri + int64_t(mP) * rel[j];
+      *d = addv(*d, u);
+    }
+  }
+}
+
+// ------------------------------------------------------------ diagonal blocks
+// Inverse of the (complex-)symmetric panel block D by Gauss-Jordan with
+// partial (row) pivoting, written back as the full block; for real symmetric
+// D (inertia) also the number of negative eigenvalues, from a Bunch-Kaufman
+// symmetric-pivoted LDL^T of D (Sylvester's law, Sec. II.C).
+template <typename T>
+__device__ void bk_count(T* Bm, int n, int ld, int* out_neg, bool* singular) {}
+
+template <>
+__device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* singular) {
+  __shared__ int s_piv[3];  // kind (1 or 2), row r, flag
+  __shared__ int s_neg;
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  if (threadIdx.x == 0) s_neg = 0;
+  __syncthreads();
+  int k = 0;
+  while (k < n) {
+    if (threadIdx.x == 0) {
+      double akk = fabs(Bm[k * ld + k]);
+      double lam = 0.0;
+      int r = k;
+      for (int i = k + 1; i < n; ++i)
+        if (fabs(Bm[i * ld + k]) > lam) { lam = fabs(Bm[i * ld + k]); r = i; }
+      int kind = 1, swapr = k;
+      if (lam == 0.0 && akk == 0.0) { *singular = true; kind = 1; }
+      else if (akk >= alpha * lam) { kind = 1; }
+      else {
+        double sig = 0.0;
+        for (int j = k; j < n; ++j)
+          if (j != r) sig = fmax(sig, fabs(Bm[r * ld + j]));
+        if (akk * sig >= alpha * lam * lam) kind = 1;
+        else if (fabs(Bm[r * ld + r]) >= alpha * sig) { kind = 1; swapr = r; }
+        else { kind = 2; swapr = r; }
+      }
+      s_piv[0] = kind;
+      s_piv[1] = swapr;
+    }
+    __syncthreads();
+    const int kind = s_piv[0], sr = s_piv[1];
+    const int tgt = (kind == 1) ? k : k + 1;
+    if (sr != tgt) {  // symmetric swap of rows/columns tgt and sr
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t = Bm[tgt * ld + j]; Bm[tgt * ld + j] = Bm[sr * ld + j]; Bm[sr * ld + j] = t;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double t = Bm[i * ld + tgt]; Bm[i * ld + tgt] = Bm[i * ld + sr]; Bm[i * ld + sr] = t;
+      }
+      __syncthreads();
+    }
+    if (kind == 1) {
+      double d = Bm[k * ld + k];
+      if (threadIdx.x == 0) {
+        if (d < 0) ++s_neg;
+        if (d == 0.0) *singular = true;
+      }
+      double inv = d != 0.0 ? 1.0 / d : 0.0;
+      for (int idx = threadIdx.x; idx < (n - k - 1) * (n - k - 1); idx += blockDim.x) {
+        int i = k + 1 + idx % (n - k - 1), j = k + 1 + idx / (n - k - 1);
+        Bm[i * ld + j] -= Bm[i * ld + k] * Bm[j * ld + k] * inv;
+      }
+      __syncthreads();
+      k += 1;
+    } else {
+      double a = Bm[k * ld + k], b = Bm[(k + 1) * ld + k], c = Bm[(k + 1) * ld + (k + 1)];
+      double det = a * c - b * b;
+      if (threadIdx.x == 0) {
+        if (det < 0) s_neg += 1;
+        else if (det > 0 && a + c < 0) s_neg += 2;
+        if (det == 0.0) *singular = true;
+      }
+      double id = det != 0.0 ? 1.0 / det : 0.0;
+      int nn = n - k - 2;
+      for (int idx = threadIdx.x; idx < nn * nn; idx += blockDim.x) {
+        int i = k + 2 + idx % nn, j = k + 2 + idx / nn;
+        double xi0 = Bm[i * ld + k], xi1 = Bm[i * ld + k + 1];
+        double xj0 = Bm[j * ld + k], xj1 = Bm[j * ld + k + 1];
+        // [xi0 xi1] E^{-1} [xj0; xj1], E^{-1} = [c -b; -b a] / det
+        double v = (xi0 * (c * xj0 - b * xj1) + xi1 * (-b * xj0 + a * xj1)) * id;
+        Bm[i * ld + j] -= v;
+      }
+      __syncthreads();
+      k += 2;
+    }
+  }
+  if (threadIdx.x == 0) *out_neg = s_neg;
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
+                           DevStatus st, int count_inertia) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Aug = reinterpret_cast<T*>(smem_raw);  // bb x (2 bb), row-major, stride 2b+1
+  const int f = fronts[blockIdx.x];
+  const int pb = blockIdx.y;
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0);
+  const int ld = 2 * b + 1;
+  T* Fd = F + int64_t(pb) * fr.pool + fr.off[f] + p0 + int64_t(m) * p0;
+  __shared__ double s_max;
+  __shared__ int s_piv;
+  __shared__ double s_pmin;
+  __shared__ bool s_bad;
+  __shared__ T s_fac[64];
+  if (threadIdx.x == 0) { s_max = 0.0; s_pmin = DBL_MAX; s_bad = false; }
+  __syncthreads();
+  double lmax = 0.0;
+  for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+    int i = idx % bb, j = idx / bb;
+    T v = (i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
+    Aug[i * ld + j] = v;
+    Aug[i * ld + bb + j] = (i == j) ? one_of(T()) : zero_of(T());
+    lmax = fmax(lmax, absv(v));
+  }
+  // block max |entry| for the pivot ratio
+  for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&s_max), __double_as_longlong(lmax));
+  __syncthreads();
+
+  if (count_inertia) {
+    // Bunch-Kaufman count on a copy placed after the augmented matrix
+    if constexpr (sizeof(T) == sizeof(double)) {
+      double* Bm = reinterpret_cast<double*>(Aug + bb * ld);
+      for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+        int i = idx % bb, j = idx / bb;
+        Bm[i * b + j] = Aug[i * ld + j];
+      }
+      __syncthreads();
+      __shared__ int s_neg;
+      __shared__ bool s_sing;
+      if (threadIdx.x == 0) s_sing = false;
+      __syncthreads();
+      bk_count<double>(Bm, bb, b, &s_neg, &s_sing);
+      if (threadIdx.x == 0) {
+        atomicAdd(&st.neg_count[pb], s_neg);
+        if (s_sing) atomicMin(st.breakdown_front, f);
+      }
+    }
+  }
+
+  for (int k = 0; k < bb; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < bb; i += 32) {
+        double a = absv(Aug[i * ld + k]);
+        if (a > best) { best = a; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        s_piv = bi;
+        s_pmin = fmin(s_pmin, best);
+        if (!(best > 0.0) || !isfinite(best)) s_bad = true;
+      }
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != k)
+      for (int j = threadIdx.x; j < 2 * bb; j += blockDim.x) {
+        T t = Aug[k * ld + j]; Aug[k * ld + j] = Aug[pr * ld + j]; Aug[pr * ld + j] = t;
+      }
+    __syncthreads();
+    const T inv = s_bad ? zero_of(T()) : recipv(Aug[k * ld + k]);
+    for (int j = k + threadIdx.x; j < 2 * bb; j += blockDim.x) Aug[k * ld + j] = mulv(Aug[k * ld + j], inv);
+    for (int i = threadIdx.x; i < bb; i += blockDim.x) s_fac[i] = Aug[i * ld + k];
+    __syncthreads();
+    const int w = 2 * bb - k - 1;
+    for (int idx = threadIdx.x; idx < bb * w; idx += blockDim.x) {
+      int i = idx / w, j = k + 1 + idx % w;
+      if (i != k) Aug[i * ld + j] = subv(Aug[i * ld + j], mulv(s_fac[i], Aug[k * ld + j]));
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+    int i = idx % bb, j = idx / bb;
+    Fd[i + int64_t(m) * j] = Aug[i * ld + bb + j];
+  }
+  if (threadIdx.x == 0) {
+    double ratio = s_max > 0 ? s_pmin / s_max : 0.0;
+    atomicMin(st.min_pivot, (unsigned long long)__double_as_longlong(ratio));
+    if (s_bad || ratio < 1e-13) atomicMin(st.breakdown_front, f);
+  }
+}
+
+// ------------------------------------------------------------ panel solve
+template <typename T>
+__global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts,
+                                                     int p0, int b) {
+  __shared__ __align__(16) T As[kKc * kLd];
+  __shared__ __align__(16) T Bs[kKc * kLd];
+  const int f = fronts[blockIdx.y];
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
+  const int I0 = blockIdx.x * kTile;
+  if (I0 >= mp) return;
+  T* Fb = F + int64_t(blockIdx.z) * fr.pool + fr.off[f];
+  const int Mv = min(kTile, mp - I0);
+  T acc[4][4];
+  zero_acc(acc);
+  gemm_tile<T, false>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * p0, m, Mv, bb, bb, As, Bs);
+  // W^T into the upper triangle (rows p0.., columns q0+I0..)
+  for (int idx = threadIdx.x; idx < Mv * bb; idx += blockDim.x) {
+    int k = idx % bb, r = idx / bb;
+    Fb[(p0 + k) + int64_t(m) * (q0 + I0 + r)] = Fb[(q0 + I0 + r) + int64_t(m) * (p0 + k)];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = tx + 16 * i, c = ty + 16 * j;
+      if (r < Mv && c < bb) Fb[(q0 + I0 + r) + int64_t(m) * (p0 + c)] = acc[i][j];
+    }
+}
+
+// ------------------------------------------------------------ Schur update
+template <typename T>
+__global__ void __launch_bounds__(256) k_trailing(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts,
+                                                  int p0, int b) {
+  __shared__ __align__(16) T As[kKc * kLd];
+  __shared__ __align__(16) T Bs[kKc * kLd];
+  const int f = fronts[blockIdx.y];
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
+  const int Tn = (mp + kTile - 1) / kTile;
+  if (int(blockIdx.x) >= Tn * (Tn + 1) / 2) return;
+  int I, J;
+  tri_tile(blockIdx.x, I, J);
+  T* Fb = F + int64_t(blockIdx.z) * fr.pool + fr.off[f];
+  const int r0 = q0 + I * kTile, c0 = q0 + J * kTile;
+  const int Mv = min(kTile, m - r0), Nv = min(kTile, m - c0);
+  T acc[4][4];
+  zero_acc(acc);
+  gemm_tile<T, false>(acc, Fb + r0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * c0, m, Mv, Nv, bb, As, Bs);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = tx + 16 * i, c = ty + 16 * j;
+      if (r < Mv && c < Nv && (I != J || r >= c)) {
+        T* d = Fb + (r0 + r) + int64_t(m) * (c0 + c);
+        *d = subv(*d, acc[i][j]);
+      }
+    }
+}
+
+// ------------------------------------------------------------ selected inversion
+__global__ void k_gather(double2* __restrict__ Y, DevFronts fr, const int32_t* __restrict__ fronts) {
+  const int f = fronts[blockIdx.y];
+  const int P = fr.parent[f];
+  if (P < 0) return;
+  const int s = fr.s[f], m = fr.m[f], r = m - s, mP = fr.m[P];
+  const int Tn = (r + 31) / 32;
+  if (int(blockIdx.x) >= Tn * Tn) return;
+  const int I = blockIdx.x % Tn, J = blockIdx.x / Tn;
+  const int64_t base = int64_t(blockIdx.z) * fr.pool;
+  double2* Yf = Y + base + fr.off[f];
+  const double2* Yp = Y + base + fr.off[P];
+  const int32_t* rel = fr.rel + fr.rptr[f];
+  const int i = I * 32 + threadIdx.x;
+  if (i >= r) return;
+  const int64_t ri = rel[i];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int j = J * 32 + threadIdx.y + 8 * q;
+    if (j < r) Yf[(s + i) + int64_t(m) * (s + j)] = Yp[ri + int64_t(mP) * rel[j]];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y, const double2* __restrict__ F, DevFronts fr,
+                                                        const int32_t* __restrict__ fronts, int p0, int b) {
+  __shared__ __align__(16) double2 As[kKc * kLd];
+  __shared__ __align__(16) double2 Bs[kKc * kLd];
+  const int f = fronts[blockIdx.y];
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
+  const int I0 = blockIdx.x * kTile;
+  if (I0 >= mp) return;
+  const int64_t base = int64_t(blockIdx.z) * fr.pool + fr.off[f];
+  double2* Yb = Y + base;
+  const double2* Fb = F + base;
+  const int Mv = min(kTile, mp - I0);
+  double2 acc[4][4];
+  zero_acc(acc);
+  gemm_tile<double2, false>(acc, Yb + q0 + I0 + int64_t(m) * q0, m, Fb + q0 + int64_t(m) * p0, m, Mv, bb, mp, As, Bs);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = tx + 16 * i, c = ty + 16 * j;
+      if (r < Mv && c < bb) {
+        double2 v = negv(acc[i][j]);
+        Yb[(q0 + I0 + r) + int64_t(m) * (p0 + c)] = v;
+        Yb[(p0 + c) + int64_t(m) * (q0 + I0 + r)] = v;
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_selinv_diag_partial(const double2* __restrict__ Y, const double2* __restrict__ F,
+                                                             double2* __restrict__ part, const int64_t* __restrict__ part_off,
+                                                             int64_t part_stride, DevFronts fr,
+                                                             const int32_t* __restrict__ fronts, int p0, int b) {
+  __shared__ __align__(16) double2 As[kKc * kLd];
+  __shared__ __align__(16) double2 Bs[kKc * kLd];
+  const int f = fronts[blockIdx.y];
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
+  const int I0 = blockIdx.x * kTile;
+  if (I0 >= mp) return;
+  const int64_t base = int64_t(blockIdx.z) * fr.pool + fr.off[f];
+  const double2* Yb = Y + base;
+  const double2* Fb = F + base;
+  const int Kv = min(kTile, mp - I0);
+  double2 acc[4][4];
+  zero_acc(acc);
+  // partial(c1, c2) = sum_{i in tile} L[i, p0+c1] Y[i, p0+c2]
+  gemm_tile<double2, true>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Yb + q0 + I0 + int64_t(m) * p0, m, bb, bb, Kv, As, Bs);
+  double2* out = part + int64_t(blockIdx.z) * part_stride + part_off[f] + int64_t(blockIdx.x) * b * b;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = tx + 16 * i, c = ty + 16 * j;
+      if (r < bb && c < bb) out[r + b * c] = acc[i][j];
+    }
+}
+
+__global__ void k_selinv_diag_reduce(double2* __restrict__ Y, const double2* __restrict__ F,
+                                     const double2* __restrict__ part, const int64_t* __restrict__ part_off,
+                                     int64_t part_stride, DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tmp = reinterpret_cast<double2*>(smem_raw);  // bb x bb
+  const int f = fronts[blockIdx.x];
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
+  const int nt = (mp + kTile - 1) / kTile;
+  const int64_t base = int64_t(blockIdx.y) * fr.pool + fr.off[f];
+  double2* Yb = Y + base;
+  const double2* Fb = F + base;
+  const double2* pp = part + int64_t(blockIdx.y) * part_stride + part_off[f];
+  for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+    int r = idx % bb, c = idx / bb;
+    double2 v = Fb[(p0 + r) + int64_t(m) * (p0 + c)];
+    for (int t = 0; t < nt; ++t) v = subv(v, pp[int64_t(t) * b * b + r + b * c]);
+    tmp[r + bb * c] = v;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+    int r = idx % bb, c = idx / bb;
+    double2 a = tmp[r + bb * c], t = tmp[c + bb * r];
+    Yb[(p0 + r) + int64_t(m) * (p0 + c)] = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y + t.y));
+  }
+}
+
+// ------------------------------------------------------------ pole sum
+__global__ void k_pole_sum(const double2* __restrict__ Y, int64_t pool, const int64_t* __restrict__ entry_pos,
+                           int64_t nnz, BatchShifts sh, int overwrite, double* __restrict__ dm,
+                           double* __restrict__ edm, double* __restrict__ fdm) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t p = entry_pos[e];
+    double a = 0.0, ae = 0.0, af = 0.0;
+    for (int b = 0; b < sh.nb; ++b) {
+      double2 v = Y[b * pool + p];
+      // Im(w v) = w.re v.im + w.im v.re
+      a = fma(sh.wr_re[b], v.y, fma(sh.wr_im[b], v.x, a));
+      ae = fma(sh.we_re[b], v.y, fma(sh.we_im[b], v.x, ae));
+      af = fma(sh.wf_re[b], v.y, fma(sh.wf_im[b], v.x, af));
+    }
+    if (dm) dm[e] = overwrite ? a : dm[e] + a;
+    if (edm) edm[e] = overwrite ? ae : edm[e] + ae;
+    if (fdm) fdm[e] = overwrite ? af : fdm[e] + af;
+  }
+}
+
+__global__ void k_extract(const double2* __restrict__ Y, const int64_t* __restrict__ entry_pos, int64_t nnz,
+                          double2* __restrict__ out) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x)
+    out[e] = Y[entry_pos[e]];
+}
+
+__global__ void k_trace_partial(const double* dm, const double* edm, const double* fdm, const double* __restrict__ S,
+                                int64_t nnz, double* partials) {
+  __shared__ double red[3][256];
+  const int64_t chunk = (nnz + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = min(nnz, lo + chunk);
+  double a = 0, b = 0, c = 0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    double sv = S[e];
+    if (dm) a = fma(dm[e], sv, a);
+    if (edm) b = fma(edm[e], sv, b);
+    if (fdm) c = fma(fdm[e], sv, c);
+  }
+  red[0][threadIdx.x] = a; red[1][threadIdx.x] = b; red[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = red[q][0];
+}
+
+__global__ void k_trace_final(const double* partials, int nblocks, double* out3) {
+  if (threadIdx.x < 3) {
+    double s = 0;
+    for (int t = 0; t < nblocks; ++t) s += partials[3 * t + threadIdx.x];
+    out3[threadIdx.x] = s;
+  }
+}
+
+inline int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return int(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+template <typename T>
+void launch_assemble(T* F, const double* H, const double* S, const int64_t* src, const int64_t* pos, int64_t nlow,
+                     int64_t pool, const BatchShifts& sh, cudaStream_t st) {
+  k_assemble<T><<<grid_for(nlow, 256), 256, 0, st>>>(F, H, S, src, pos, nlow, pool, sh);
+}
+
+template <typename T>
+void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int nchild, int max_tiles,
+                       const BatchShifts& sh, cudaStream_t st) {
+  if (nchild <= 0 || max_tiles <= 0) return;
+  dim3 grid(max_tiles, nchild, sh.nb), block(32, 8);
+  k_extend_add<T><<<grid, block, 0, st>>>(F, fr, children, nchild);
+}
+
+template <typename T>
+void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+                     const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
+  if (nfronts <= 0) return;
+  size_t smem = sizeof(T) * size_t(b) * (2 * b + 1) + (count_inertia ? sizeof(double) * b * b : 0);
+  dim3 grid(nfronts, sh.nb);
+  k_diag_inv<T><<<grid, 256, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
+}
+
+template <typename T>
+void launch_panel_solve(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_row_tiles, int p0,
+                        int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_row_tiles <= 0) return;
+  dim3 grid(max_row_tiles, nfronts, sh.nb);
+  k_panel_solve<T><<<grid, 256, 0, st>>>(F, fr, fronts, p0, b);
+}
+
+template <typename T>
+void launch_trailing(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0, int b,
+                     const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_tiles <= 0) return;
+  dim3 grid(max_tiles, nfronts, sh.nb);
+  k_trailing<T><<<grid, 256, 0, st>>>(F, fr, fronts, p0, b);
+}
+
+void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
+                   const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_tiles <= 0) return;
+  dim3 grid(max_tiles, nfronts, sh.nb), block(32, 8);
+  k_gather<<<grid, block, 0, st>>>(Y, fr, fronts);
+}
+
+void launch_selinv_offdiag(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                           int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_row_tiles <= 0) return;
+  dim3 grid(max_row_tiles, nfronts, sh.nb);
+  k_selinv_offdiag<<<grid, 256, 0, st>>>(Y, F, fr, fronts, p0, b);
+}
+
+void launch_selinv_diag_partial(const double2* Y, const double2* F, double2* part, const int64_t* part_off,
+                                int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                                int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_row_tiles <= 0) return;
+  dim3 grid(max_row_tiles, nfronts, sh.nb);
+  k_selinv_diag_partial<<<grid, 256, 0, st>>>(Y, F, part, part_off, part_stride, fr, fronts, p0, b);
+}
+
+void launch_selinv_diag_reduce(double2* Y, const double2* F, const double2* part, const int64_t* part_off,
+                               int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0,
+                               int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0) return;
+  dim3 grid(nfronts, sh.nb);
+  k_selinv_diag_reduce<<<grid, 256, sizeof(double2) * b * b, st>>>(Y, F, part, part_off, part_stride, fr, fronts, p0, b);
+}
+
+void launch_pole_sum(const double2* Y, int64_t pool, const int64_t* entry_pos, int64_t nnz, const BatchShifts& sh,
+                     int overwrite, double* dm, double* edm, double* fdm, cudaStream_t st) {
+  k_pole_sum<<<grid_for(nnz, 256), 256, 0, st>>>(Y, pool, entry_pos, nnz, sh, overwrite, dm, edm, fdm);
+}
+
+void launch_extract(const double2* Y, const int64_t* entry_pos, int64_t nnz, double2* out, cudaStream_t st) {
+  k_extract<<<grid_for(nnz, 256), 256, 0, st>>>(Y, entry_pos, nnz, out);
+}
+
+void launch_traces(const double* dm, const double* edm, const double* fdm, const double* S, int64_t nnz,
+                   double* partials, int nblocks, double* out3, cudaStream_t st) {
+  k_trace_partial<<<nblocks, 256, 0, st>>>(dm, edm, fdm, S, nnz, partials);
+  k_trace_final<<<1, 32, 0, st>>>(partials, nblocks, out3);
+}
+
+cudaError_t configure_kernels(int b) {
+  size_t need_c = sizeof(double2) * size_t(b) * (2 * b + 1);
+  size_t need_r = sizeof(double) * size_t(b) * (2 * b + 1) + sizeof(double) * b * b;
+  cudaError_t e = cudaFuncSetAttribute(k_diag_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_c));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_r));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_selinv_diag_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(sizeof(double2) * b * b));
+}
+
+#define PEXSI_INSTANTIATE(T)                                                                                        \
+  template void launch_assemble<T>(T*, const double*, const double*, const int64_t*, const int64_t*, int64_t,    \
+                                   int64_t, const BatchShifts&, cudaStream_t);                                   \
+  template void launch_extend_add<T>(T*, const DevFronts&, const int32_t*, int, int, const BatchShifts&,         \
+                                     cudaStream_t);                                                               \
+  template void launch_diag_inv<T>(T*, const DevFronts&, const int32_t*, int, int, int, const BatchShifts&,      \
+                                   DevStatus, bool, cudaStream_t);                                                \
+  template void launch_panel_solve<T>(T*, const DevFronts&, const int32_t*, int, int, int, int,                  \
+                                      const BatchShifts&, cudaStream_t);                                          \
+  template void launch_trailing<T>(T*, const DevFronts&, const int32_t*, int, int, int, int, const BatchShifts&, \
+                                   cudaStream_t);
+PEXSI_INSTANTIATE(double)
+PEXSI_INSTANTIATE(double2)
+
+}  // namespace pexsi

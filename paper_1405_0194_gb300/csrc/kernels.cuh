@@ -1,0 +1,89 @@
+// Device kernels of the multifrontal LDL^T + selected inversion (Sec. II.B,
+// steps 3 and 4) and of the pole sum (Eq. gammapole, Eq. gammaF).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pexsi {
+
+constexpr int kMaxBatch = 64;  // poles (or shifts) processed together
+constexpr int kTile = 64;      // GEMM output tile edge
+
+// Shifts of one batch, passed by value: complex z_b (re, im) for poles, or
+// real sigma_b (im = 0) for inertia shifts. Weights of the pole sum.
+struct BatchShifts {
+  int nb;
+  double re[kMaxBatch], im[kMaxBatch];
+  double wr_re[kMaxBatch], wr_im[kMaxBatch];  // w^rho
+  double we_re[kMaxBatch], we_im[kMaxBatch];  // w^E
+  double wf_re[kMaxBatch], wf_im[kMaxBatch];  // w^F
+};
+
+// Front geometry on the device.
+struct DevFronts {
+  const int64_t* off;   // element offset of each front in one pole's pool
+  const int32_t* s;     // width s_K
+  const int32_t* m;     // m_K = s_K + r_K
+  const int32_t* parent;
+  const int64_t* rptr;  // offsets into rel
+  const int32_t* rel;   // child structure rows -> parent front rows
+  int64_t pool;         // elements per pole
+};
+
+// Error reporting shared by all kernels of one call.
+struct DevStatus {
+  int* breakdown_front;              // atomicMin of the first failing front (INT_MAX = none)
+  unsigned long long* min_pivot;     // atomicMin of the bit pattern of min |pivot| / max |entry|
+  int* neg_count;                    // per batch member: negative eigenvalues of D (inertia)
+};
+
+// ---- launchers (T = double for real inertia, double2 for complex poles) ----
+template <typename T>
+void launch_assemble(T* F, const double* H, const double* S, const int64_t* src, const int64_t* pos, int64_t nlow,
+                     int64_t pool, const BatchShifts& sh, cudaStream_t st);
+
+template <typename T>
+void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int nchild, int max_tiles,
+                       const BatchShifts& sh, cudaStream_t st);
+
+template <typename T>
+void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+                     const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st);
+
+template <typename T>
+void launch_panel_solve(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_row_tiles, int p0,
+                        int b, const BatchShifts& sh, cudaStream_t st);
+
+template <typename T>
+void launch_trailing(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0, int b,
+                     const BatchShifts& sh, cudaStream_t st);
+
+void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
+                   const BatchShifts& sh, cudaStream_t st);
+
+void launch_selinv_offdiag(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                           int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st);
+
+void launch_selinv_diag_partial(const double2* Y, const double2* F, double2* part, const int64_t* part_off,
+                                int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                                int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st);
+
+void launch_selinv_diag_reduce(double2* Y, const double2* F, const double2* part, const int64_t* part_off,
+                               int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0,
+                               int b, const BatchShifts& sh, cudaStream_t st);
+
+void launch_pole_sum(const double2* Y, int64_t pool, const int64_t* entry_pos, int64_t nnz, const BatchShifts& sh,
+                     int overwrite, double* dm, double* edm, double* fdm, cudaStream_t st);
+
+void launch_extract(const double2* Y, const int64_t* entry_pos, int64_t nnz, double2* out, cudaStream_t st);
+
+// Raises the dynamic shared-memory limits the kernels need for panel width b.
+cudaError_t configure_kernels(int b);
+
+// Deterministic Tr[X S] for up to three X (NULL entries skipped): partial sums
+// of fixed ranges in `partials` (3 * nblocks doubles), then one ordered sum.
+void launch_traces(const double* dm, const double* edm, const double* fdm, const double* S, int64_t nnz,
+                   double* partials, int nblocks, double* out3, cudaStream_t st);
+
+}  // namespace pexsi
