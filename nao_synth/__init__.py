@@ -253,8 +253,11 @@ def spectral_interval(sys: System, dense_limit: int = 4096, margin: float = 0.05
         return float(ev[0]), float(ev[-1])
     rng = np.random.default_rng(12345)
     X = rng.standard_normal((sys.n, 4))
-    lo = spla.lobpcg(Hm, X, B=Sm, largest=False, maxiter=300, tol=1e-7)[0][0]
-    hi = spla.lobpcg(Hm, X, B=Sm, largest=True, maxiter=300, tol=1e-7)[0][0]
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        lo = spla.lobpcg(Hm, X, B=Sm, largest=False, maxiter=120, tol=1e-5)[0][0]
+        hi = spla.lobpcg(Hm, X, B=Sm, largest=True, maxiter=120, tol=1e-5)[0][0]
     w = hi - lo
     return float(lo - margin * w), float(hi + margin * w)
 

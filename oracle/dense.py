@@ -86,3 +86,42 @@ def inertia_counts(n, colptr, rowind, H, S, shifts):
     Sd = dense_from_csc(n, colptr, rowind, S)
     ev = sla.eigh(Hd, Sd, eigvals_only=True)
     return np.array([int(np.sum(ev < s)) for s in np.atleast_1d(shifts)], dtype=np.int64)
+
+
+def eig_pencil(n, colptr, rowind, H, S):
+    """Generalised eigenpairs H C = S C Lambda with C^T S C = I (LAPACK sygvd
+    through scipy, a library primitive)."""
+    Hd = dense_from_csc(n, colptr, rowind, H)
+    Sd = dense_from_csc(n, colptr, rowind, S)
+    return sla.eigh(Hd, Sd, overwrite_a=True, overwrite_b=True, check_finite=False)
+
+
+def dm_columns_eig(lam, C, colptr, rowind, table, cols, poles_idx):
+    """DM / EDM / FDM in the given columns, summed over the poles in
+    poles_idx, from the closed form (H - z S)^{-1} = C (Lambda - z)^{-1} C^T.
+
+    Returns {j: (dm_col, edm_col, fdm_col)} at the pattern rows of column j.
+    """
+    out = {}
+    for j in np.asarray(cols).tolist():
+        rows = rowind[colptr[j]:colptr[j + 1]]
+        Cr = C[rows, :]
+        cj = C[j, :]
+        acc = [np.zeros(rows.shape[0]) for _ in range(3)]
+        for l in poles_idx:
+            col = Cr @ (cj / (lam - table["z"][l]))
+            for q, key in enumerate(("w_rho", "w_E", "w_F")):
+                acc[q] += np.imag(table[key][l] * col)
+        out[j] = tuple(acc)
+    return out
+
+
+def trace_eig(lam, table, poles_idx):
+    """Tr[Gamma S] for the poles in poles_idx from the eigenvalues:
+    sum_i Im sum_l w_l / (lam_i - z_l) (DM, EDM, FDM)."""
+    z = table["z"][list(poles_idx)]
+    out = []
+    for key in ("w_rho", "w_E", "w_F"):
+        w = table[key][list(poles_idx)]
+        out.append(float(np.sum(np.imag(w[None, :] / (lam[:, None] - z[None, :])))))
+    return out

@@ -58,3 +58,26 @@ def dm_columns(n, colptr, rowind, H, S, table, cols, poles_idx=None):
             acc[j][1] = acc[j][1] + np.imag(table["w_E"][l] * v)
             acc[j][2] = acc[j][2] + np.imag(table["w_F"][l] * v)
     return acc
+
+
+def factor_shifted_dense(n, colptr, rowind, H, S, z):
+    """Dense LU with partial pivoting of A = H - z S (scipy's LAPACK getrf,
+    a library primitive used as one step); for the near-dense 3D systems where
+    a sparse LU fills in completely anyway."""
+    import scipy.linalg as sla
+    from .dense import dense_from_csc
+    A = dense_from_csc(n, colptr, rowind, np.asarray(H, complex))
+    A -= z * dense_from_csc(n, colptr, rowind, np.asarray(S, float))
+    return sla.lu_factor(A, overwrite_a=True, check_finite=False)
+
+
+def selected_columns_dense(n, colptr, rowind, H, S, z, cols, lu=None):
+    """As selected_columns, with the dense LU of factor_shifted_dense."""
+    import scipy.linalg as sla
+    if lu is None:
+        lu = factor_shifted_dense(n, colptr, rowind, H, S, z)
+    cols = np.asarray(cols, dtype=np.int64)
+    E = np.zeros((n, cols.shape[0]), dtype=complex)
+    E[cols, np.arange(cols.shape[0])] = 1.0
+    X = sla.lu_solve(lu, E, check_finite=False)
+    return {j: X[rowind[colptr[j]:colptr[j + 1]], k] for k, j in enumerate(cols.tolist())}

@@ -156,19 +156,41 @@ def test_tiny_systems():
         assert cnt[0] == int(np.sum(H / 1.5 < 0.05))
 
 
-def test_full_size_sheet_sampled_columns():
-    """n = 26,624 honeycomb sheet at one pole of its 60-pole table: sampled
-    columns of the selected inverse against sparse-LU column solves."""
-    s = ns.make_sheet(ncell=32, seed=0)
-    lo, hi = -8.0, 8.0  # a fixed shift; the solve does not need the spectrum
-    tab = poles.pole_table(s.beta, 8.0, 60, 0.0)
-    z = tab["z"][0]
-    plan = _plan(s)
-    got = px.pexsi_selinv(plan, s.H, s.S, z)
+@pytest.fixture(scope="module")
+def full_fluid():
+    """The benchmark workload at full size (n = 11,776) with its generalised
+    eigen-decomposition (one dense sygvd on the host, about a minute)."""
+    s = ns.make_fluid(nmol=512, seed=0)
+    mu, dE = ns.mu_and_delta_e(s)
+    lam, C = dense.eig_pencil(s.n, s.colptr, s.rowind, s.H, s.S)
+    return s, mu, dE, lam, C
+
+
+@pytest.mark.slow
+def test_full_size_fluid_bench_batch(full_fluid):
+    """Poles [0, 10) of the 60-pole table in the launch configuration the
+    benchmark times (one 10-pole batch): sampled DM/EDM/FDM columns and the
+    traces against the eigen closed form; inertia at 3 shifts exact."""
+    s, mu, dE, lam, C = full_fluid
+    tab = poles.pole_table(s.beta, dE, 60, mu)
+    plan = _plan(s, max_batch=10)
+    dH = torch.from_numpy(s.H).cuda(); dS = torch.from_numpy(s.S).cuda()
+    out = torch.zeros(3, s.nnz, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    info = px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, 60, dE, 0, 10, 0,
+                              out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), st, want_info=True)
+    shifts = mu + np.array([-0.31, 0.0, 0.27]) + 1.0e-4
+    cnt = px.pexsi_inertia_device(plan, dH.data_ptr(), dS.data_ptr(), shifts, st)
     px.pexsi_plan_destroy(plan)
+    got = out.cpu().numpy()
     rng = np.random.default_rng(0)
-    cols = np.sort(rng.choice(s.n, 6, replace=False))
-    ref = sampled.selected_columns(s.n, s.colptr, s.rowind, s.H, s.S, z, cols)
+    cols = np.sort(rng.choice(s.n, 8, replace=False))
+    ref = dense.dm_columns_eig(lam, C, s.colptr, s.rowind, tab, cols, range(10))
     for j in cols:
-        g = got[s.colptr[j]:s.colptr[j + 1]]
-        assert np.max(np.abs(g - ref[j])) <= 1e-10 * max(1.0, np.max(np.abs(ref[j])))
+        sl = slice(s.colptr[j], s.colptr[j + 1])
+        for q in range(3):
+            assert np.max(np.abs(got[q, sl] - ref[j][q])) <= TOL_DM, (j, q)
+    tr = dense.trace_eig(lam, tab, range(10))
+    assert abs(info["trace_dm_s"] - tr[0]) <= 1e-8
+    assert abs(info["trace_fdm_s"] - tr[2]) <= 1e-8 * max(1.0, abs(tr[2]))
+    assert cnt.tolist() == [int(np.sum(lam < x)) for x in shifts]

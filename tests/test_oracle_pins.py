@@ -214,3 +214,34 @@ def test_sampled_columns_match_dense(small_fluid):
         assert np.max(np.abs(acc[j][0] - dm[sl])) < 1e-11
         assert np.max(np.abs(acc[j][1] - edm[sl])) < 1e-10
         assert np.max(np.abs(acc[j][2] - fdm[sl])) < 1e-10
+
+
+def test_sampled_dense_lu_matches_dense(small_fluid):
+    s, mu, dE, (lam, C) = small_fluid
+    z = mu + 0.21 + 0.003j
+    cols = [1, s.n // 2, s.n - 2]
+    got = sampled.selected_columns_dense(s.n, s.colptr, s.rowind, s.H, s.S, z, cols)
+    ref = ((C / (lam - z)) @ C.T)
+    for j in cols:
+        rows = s.rowind[s.colptr[j]:s.colptr[j + 1]]
+        assert np.max(np.abs(got[j] - ref[rows, j])) < 1e-10 * np.max(np.abs(ref))
+
+
+def test_eig_closed_form_columns_match_definition(small_fluid):
+    s, mu, dE, (lam, C) = small_fluid
+    tab = poles.pole_table(s.beta, dE, 20, mu)
+    dm, edm, fdm, _ = dense.density_matrices(s.n, s.colptr, s.rowind, s.H, s.S, mu, s.beta, 20, dE, table=tab)
+    lam2, C2 = dense.eig_pencil(s.n, s.colptr, s.rowind, s.H, s.S)
+    sub = range(3, 11)
+    dm_s, edm_s, fdm_s, _ = dense.density_matrices(s.n, s.colptr, s.rowind, s.H, s.S, mu, s.beta, 20, dE,
+                                                   table={k: v[3:11] for k, v in tab.items()})
+    cols = [0, 7, s.n - 1]
+    got = dense.dm_columns_eig(lam2, C2, s.colptr, s.rowind, tab, cols, sub)
+    for j in cols:
+        sl = slice(s.colptr[j], s.colptr[j + 1])
+        assert np.max(np.abs(got[j][0] - dm_s[sl])) < 1e-11
+        assert np.max(np.abs(got[j][1] - edm_s[sl])) < 1e-11
+        assert np.max(np.abs(got[j][2] - fdm_s[sl])) < 1e-11
+    tr = dense.trace_eig(lam2, tab, sub)
+    assert abs(tr[0] - dense.trace_with_s(dm_s, s.S)) < 1e-9
+    assert abs(tr[2] - dense.trace_with_s(fdm_s, s.S)) < 1e-9
