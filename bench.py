@@ -50,6 +50,10 @@ WORKLOADS = {
                   desc="sheet32x32: periodic honeycomb sheet, 2048 atoms x 13 orb, n=26624, 8 A pair cutoff, "
                        "decay 3 bohr, beta=2000/Ha, 60 poles, complex FP64",
                   shifts_per_60=16),
+    "fluid256": dict(make=lambda seed: ns.make_fluid(nmol=256, seed=seed),
+                     desc="fluid256: the fluid recipe at half size (256 O + 512 H), n=5888, box 37.2 bohr, "
+                          "beta=1000/Ha, 60 poles (profiling case)",
+                     shifts_per_60=16),
     "chain": dict(make=lambda seed: ns.make_chain(seed=seed),
                   desc="chain64: 1D chain 64 atoms x 4 orb, n=256, 6 bohr cutoff, beta=1000/Ha, 40 poles",
                   shifts_per_60=16),
