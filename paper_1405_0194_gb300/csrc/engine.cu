@@ -163,10 +163,11 @@ struct pexsi_plan {
 namespace {
 
 void free_plan_device(pexsi_plan* p) {
+  // d_edm and d_fdm point into the d_dm allocation and are not freed separately
   void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
                   p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_F, p->d_Y, p->d_part, p->d_H,
-                  p->d_S, p->d_ident, p->d_dm, p->d_edm, p->d_fdm, p->d_ainv, p->d_break, p->d_minpiv, p->d_neg,
-                  p->d_partials, p->d_trace3};
+                  p->d_S, p->d_ident, p->d_dm, p->d_ainv, p->d_break, p->d_minpiv, p->d_neg, p->d_partials,
+                  p->d_trace3};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->prof.destroy();
