@@ -194,6 +194,32 @@ int pexsi_inertia_device(pexsi_plan* plan, const double* dH, const double* dS,
 int pexsi_plan_get_supernodes(const pexsi_plan* plan, int32_t* first, int64_t* rptr, int32_t* rows,
                               int32_t* parent);
 
+/* Allocation-free Tr[X S] for device-resident DM / EDM / FDM (no counterpart
+ * in the paper; the traces themselves are Eq. Nmu and its energy analogues).
+ * For callers that cannot allocate device memory when they need the traces --
+ * for example while capturing a stream into a CUDA graph, inside a runtime
+ * that owns a fixed memory arena, or in a serving loop that must not touch
+ * the allocator -- this call allocates nothing: its scratch (the block
+ * partial sums) is a file-scope device array of 3 x 1024 doubles (24 KiB)
+ * that every GPU which loads the library holds until the process exits.
+ *   d_dm, d_edm, d_fdm : device arrays of nnz doubles, any may be NULL (its
+ *                        trace is then written as 0)
+ *   d_S                : device array of nnz doubles (the overlap on the same
+ *                        pattern; an identity S gives the plain trace)
+ *   nnz                : 0 <= nnz <= 2^30 (1024 blocks x 2^20 entries);
+ *                        larger sizes return PEXSI_ERR_INVALID_ARG
+ *   d_out3             : device array of 3 doubles, receives
+ *                        (Tr[DM S], Tr[EDM S], Tr[FDM S])
+ *   stream             : cudaStream_t (void*), NULL = legacy default stream
+ * Runs on the current device and returns after enqueueing. The first call on
+ * a device looks up the scratch array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.
+ * Every call shares the one scratch array per device and overwrites it, so
+ * calls that overlap on the GPU (concurrent streams) race; serialise them.
+ * Errors: INVALID_ARG (NULL d_S / d_out3, nnz out of range), CUDA. */
+int pexsi_trace_noalloc(const double* d_dm, const double* d_edm, const double* d_fdm,
+                        const double* d_S, int64_t nnz, double* d_out3, void* stream);
+
 /* Per-kernel-class timing (instrumentation, not part of the method). When
  * enabled, every kernel launch of the plan is bracketed by CUDA events on the
  * stream it runs on; pexsi_profile_read accumulates the elapsed times after

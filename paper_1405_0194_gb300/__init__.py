@@ -22,4 +22,5 @@ from .capi import (  # noqa: F401
     pexsi_selinv,
     pexsi_setup,
     pexsi_strerror,
+    pexsi_trace_noalloc,
 )

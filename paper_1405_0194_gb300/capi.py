@@ -96,6 +96,8 @@ SIGNATURES = [
                                      c_int64_p]),
     ("pexsi_inertia_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p,
                                             ctypes.c_int32, c_int64_p, ctypes.c_void_p]),
+    ("pexsi_trace_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("pexsi_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("pexsi_last_error_detail", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -301,6 +303,14 @@ def pexsi_inertia_device(plan, dH, dS, shifts, stream=0) -> np.ndarray:
                                     int(shifts.shape[0]), _ptr(counts, ctypes.c_int64), stream or None)
     _check(rc, plan)
     return counts
+
+
+def pexsi_trace_noalloc(d_dm, d_edm, d_fdm, d_S, nnz, d_out3, stream=0):
+    """Allocation-free (Tr[DM S], Tr[EDM S], Tr[FDM S]) into the device array
+    at d_out3; all arguments are device addresses (0 / None = NULL)."""
+    rc = lib().pexsi_trace_noalloc(d_dm or None, d_edm or None, d_fdm or None, d_S or None, int(nnz),
+                                   d_out3 or None, stream or None)
+    _check(rc)
 
 
 def pexsi_strerror(code: int) -> str:
