@@ -129,6 +129,108 @@ __device__ __forceinline__ void gemm_tile(T (&acc)[4][4], const T* __restrict__ 
   }
 }
 
+// Complex tile by the 3-multiplication (Gauss) form: with T1 = sum ar br,
+// T2 = sum ai bi, T3 = sum (ar + ai)(br + bi), the product is T1 - T2 +
+// i (T3 - T1 - T2). Three real multiply-adds per complex multiply-add instead
+// of four; the operand sums are formed once per staged element. Shared memory
+// (dynamic, kSmem3m bytes): six 16 x 65 double planes.
+constexpr int kPlane = kKc * kLd;
+constexpr size_t kSmem3m = 6 * kPlane * sizeof(double);
+
+template <bool AT>
+__device__ __forceinline__ void gemm_tile_3m(double2 (&acc)[4][4], const double2* __restrict__ A, int64_t lda,
+                                             const double2* __restrict__ B, int64_t ldb, int Mv, int Nv, int K,
+                                             double* sm) {
+  double* Ar = sm;
+  double* Ai = sm + kPlane;
+  double* As = sm + 2 * kPlane;
+  double* Br = sm + 3 * kPlane;
+  double* Bi = sm + 4 * kPlane;
+  double* Bs = sm + 5 * kPlane;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double t1[4][4], t2[4][4], t3[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += kKc) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q, r, k;
+      if (!AT) { r = idx & 63; k = idx >> 6; }
+      else { k = idx & 15; r = idx >> 4; }
+      double2 v = make_double2(0.0, 0.0);
+      if (r < Mv && k0 + k < K) v = AT ? A[(k0 + k) + lda * r] : A[r + lda * (k0 + k)];
+      Ar[k * kLd + r] = v.x;
+      Ai[k * kLd + r] = v.y;
+      As[k * kLd + r] = v.x + v.y;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q, k = idx & 15, c = idx >> 4;
+      double2 v = make_double2(0.0, 0.0);
+      if (c < Nv && k0 + k < K) v = B[(k0 + k) + ldb * c];
+      Br[k * kLd + c] = v.x;
+      Bi[k * kLd + c] = v.y;
+      Bs[k * kLd + c] = v.x + v.y;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int k = 0; k < kKc; ++k) {
+      double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ar[i] = Ar[k * kLd + tx + 16 * i];
+        ai[i] = Ai[k * kLd + tx + 16 * i];
+        as[i] = As[k * kLd + tx + 16 * i];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        br[j] = Br[k * kLd + ty + 16 * j];
+        bi[j] = Bi[k * kLd + ty + 16 * j];
+        bs[j] = Bs[k * kLd + ty + 16 * j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          t1[i][j] = fma(ar[i], br[j], t1[i][j]);
+          t2[i][j] = fma(ai[i], bi[j], t2[i][j]);
+          t3[i][j] = fma(as[i], bs[j], t3[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      acc[i][j] = make_double2(t1[i][j] - t2[i][j], (t3[i][j] - t1[i][j]) - t2[i][j]);
+}
+
+// Dispatch: complex tiles take the 3M form, real tiles the plain one.
+template <typename T, bool AT>
+__device__ __forceinline__ void gemm_any(T (&acc)[4][4], const T* A, int64_t lda, const T* B, int64_t ldb, int Mv,
+                                         int Nv, int K, double* sm);
+template <>
+__device__ __forceinline__ void gemm_any<double, false>(double (&acc)[4][4], const double* A, int64_t lda,
+                                                        const double* B, int64_t ldb, int Mv, int Nv, int K,
+                                                        double* sm) {
+  gemm_tile<double, false>(acc, A, lda, B, ldb, Mv, Nv, K, sm, sm + kPlane);
+}
+template <>
+__device__ __forceinline__ void gemm_any<double2, false>(double2 (&acc)[4][4], const double2* A, int64_t lda,
+                                                         const double2* B, int64_t ldb, int Mv, int Nv, int K,
+                                                         double* sm) {
+  gemm_tile_3m<false>(acc, A, lda, B, ldb, Mv, Nv, K, sm);
+}
+template <>
+__device__ __forceinline__ void gemm_any<double2, true>(double2 (&acc)[4][4], const double2* A, int64_t lda,
+                                                        const double2* B, int64_t ldb, int Mv, int Nv, int K,
+                                                        double* sm) {
+  gemm_tile_3m<true>(acc, A, lda, B, ldb, Mv, Nv, K, sm);
+}
+
 template <typename T>
 __device__ __forceinline__ void zero_acc(T (&acc)[4][4]) {
 #pragma unroll
@@ -374,8 +476,7 @@ __global__ void k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __res
 template <typename T>
 __global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts,
                                                      int p0, int b) {
-  __shared__ __align__(16) T As[kKc * kLd];
-  __shared__ __align__(16) T Bs[kKc * kLd];
+  extern __shared__ __align__(16) double gsm[];
   const int f = fronts[blockIdx.y];
   const int s = fr.s[f], m = fr.m[f];
   if (p0 >= s) return;
@@ -386,7 +487,7 @@ __global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFront
   const int Mv = min(kTile, mp - I0);
   T acc[4][4];
   zero_acc(acc);
-  gemm_tile<T, false>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * p0, m, Mv, bb, bb, As, Bs);
+  gemm_any<T, false>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * p0, m, Mv, bb, bb, gsm);
   // W^T into the upper triangle (rows p0.., columns q0+I0..)
   for (int idx = threadIdx.x; idx < Mv * bb; idx += blockDim.x) {
     int k = idx % bb, r = idx / bb;
@@ -407,8 +508,7 @@ __global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFront
 template <typename T>
 __global__ void __launch_bounds__(256) k_trailing(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts,
                                                   int p0, int b) {
-  __shared__ __align__(16) T As[kKc * kLd];
-  __shared__ __align__(16) T Bs[kKc * kLd];
+  extern __shared__ __align__(16) double gsm[];
   const int f = fronts[blockIdx.y];
   const int s = fr.s[f], m = fr.m[f];
   if (p0 >= s) return;
@@ -422,7 +522,7 @@ __global__ void __launch_bounds__(256) k_trailing(T* __restrict__ F, DevFronts f
   const int Mv = min(kTile, m - r0), Nv = min(kTile, m - c0);
   T acc[4][4];
   zero_acc(acc);
-  gemm_tile<T, false>(acc, Fb + r0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * c0, m, Mv, Nv, bb, As, Bs);
+  gemm_any<T, false>(acc, Fb + r0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * c0, m, Mv, Nv, bb, gsm);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -461,8 +561,7 @@ __global__ void k_gather(double2* __restrict__ Y, DevFronts fr, const int32_t* _
 
 __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y, const double2* __restrict__ F, DevFronts fr,
                                                         const int32_t* __restrict__ fronts, int p0, int b) {
-  __shared__ __align__(16) double2 As[kKc * kLd];
-  __shared__ __align__(16) double2 Bs[kKc * kLd];
+  extern __shared__ __align__(16) double gsm[];
   const int f = fronts[blockIdx.y];
   const int s = fr.s[f], m = fr.m[f];
   if (p0 >= s) return;
@@ -475,7 +574,7 @@ __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y,
   const int Mv = min(kTile, mp - I0);
   double2 acc[4][4];
   zero_acc(acc);
-  gemm_tile<double2, false>(acc, Yb + q0 + I0 + int64_t(m) * q0, m, Fb + q0 + int64_t(m) * p0, m, Mv, bb, mp, As, Bs);
+  gemm_any<double2, false>(acc, Yb + q0 + I0 + int64_t(m) * q0, m, Fb + q0 + int64_t(m) * p0, m, Mv, bb, mp, gsm);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -494,8 +593,7 @@ __global__ void __launch_bounds__(256) k_selinv_diag_partial(const double2* __re
                                                              double2* __restrict__ part, const int64_t* __restrict__ part_off,
                                                              int64_t part_stride, DevFronts fr,
                                                              const int32_t* __restrict__ fronts, int p0, int b) {
-  __shared__ __align__(16) double2 As[kKc * kLd];
-  __shared__ __align__(16) double2 Bs[kKc * kLd];
+  extern __shared__ __align__(16) double gsm[];
   const int f = fronts[blockIdx.y];
   const int s = fr.s[f], m = fr.m[f];
   if (p0 >= s) return;
@@ -509,7 +607,7 @@ __global__ void __launch_bounds__(256) k_selinv_diag_partial(const double2* __re
   double2 acc[4][4];
   zero_acc(acc);
   // partial(c1, c2) = sum_{i in tile} L[i, p0+c1] Y[i, p0+c2]
-  gemm_tile<double2, true>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Yb + q0 + I0 + int64_t(m) * p0, m, bb, bb, Kv, As, Bs);
+  gemm_any<double2, true>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Yb + q0 + I0 + int64_t(m) * p0, m, bb, bb, Kv, gsm);
   double2* out = part + int64_t(blockIdx.z) * part_stride + part_off[f] + int64_t(blockIdx.x) * b * b;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -642,7 +740,7 @@ void launch_panel_solve(T* F, const DevFronts& fr, const int32_t* fronts, int nf
                         int b, const BatchShifts& sh, cudaStream_t st) {
   if (nfronts <= 0 || max_row_tiles <= 0) return;
   dim3 grid(max_row_tiles, nfronts, sh.nb);
-  k_panel_solve<T><<<grid, 256, 0, st>>>(F, fr, fronts, p0, b);
+  k_panel_solve<T><<<grid, 256, kSmem3m, st>>>(F, fr, fronts, p0, b);
 }
 
 template <typename T>
@@ -650,7 +748,7 @@ void launch_trailing(T* F, const DevFronts& fr, const int32_t* fronts, int nfron
                      const BatchShifts& sh, cudaStream_t st) {
   if (nfronts <= 0 || max_tiles <= 0) return;
   dim3 grid(max_tiles, nfronts, sh.nb);
-  k_trailing<T><<<grid, 256, 0, st>>>(F, fr, fronts, p0, b);
+  k_trailing<T><<<grid, 256, kSmem3m, st>>>(F, fr, fronts, p0, b);
 }
 
 void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
@@ -664,7 +762,7 @@ void launch_selinv_offdiag(double2* Y, const double2* F, const DevFronts& fr, co
                            int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
   if (nfronts <= 0 || max_row_tiles <= 0) return;
   dim3 grid(max_row_tiles, nfronts, sh.nb);
-  k_selinv_offdiag<<<grid, 256, 0, st>>>(Y, F, fr, fronts, p0, b);
+  k_selinv_offdiag<<<grid, 256, kSmem3m, st>>>(Y, F, fr, fronts, p0, b);
 }
 
 void launch_selinv_diag_partial(const double2* Y, const double2* F, double2* part, const int64_t* part_off,
@@ -672,7 +770,7 @@ void launch_selinv_diag_partial(const double2* Y, const double2* F, double2* par
                                 int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
   if (nfronts <= 0 || max_row_tiles <= 0) return;
   dim3 grid(max_row_tiles, nfronts, sh.nb);
-  k_selinv_diag_partial<<<grid, 256, 0, st>>>(Y, F, part, part_off, part_stride, fr, fronts, p0, b);
+  k_selinv_diag_partial<<<grid, 256, kSmem3m, st>>>(Y, F, part, part_off, part_stride, fr, fronts, p0, b);
 }
 
 void launch_selinv_diag_reduce(double2* Y, const double2* F, const double2* part, const int64_t* part_off,
@@ -705,8 +803,17 @@ cudaError_t configure_kernels(int b) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_r));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_selinv_diag_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(sizeof(double2) * b * b));
+  e = cudaFuncSetAttribute(k_selinv_diag_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(sizeof(double2) * b * b));
+  if (e != cudaSuccess) return e;
+  const void* gemms[] = {(const void*)k_panel_solve<double>, (const void*)k_panel_solve<double2>,
+                         (const void*)k_trailing<double>, (const void*)k_trailing<double2>,
+                         (const void*)k_selinv_offdiag, (const void*)k_selinv_diag_partial};
+  for (const void* fn : gemms) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem3m));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 #define PEXSI_INSTANTIATE(T)                                                                                        \
