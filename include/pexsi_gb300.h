@@ -49,7 +49,9 @@ enum {
   PEXSI_ERR_NOMEM = -3,         /* host or device allocation failed            */
   PEXSI_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed */
   PEXSI_ERR_BREAKDOWN = -5,     /* zero / non-finite pivot in a diagonal block */
-  PEXSI_ERR_INTERNAL = -6       /* violated internal invariant (a bug)         */
+  PEXSI_ERR_INTERNAL = -6,      /* violated internal invariant (a bug)         */
+  PEXSI_ERR_CANCELLED = -7,     /* server request cancelled before completion  */
+  PEXSI_PENDING = 1             /* server request not finished yet (poll)      */
 };
 
 typedef struct pexsi_plan pexsi_plan;
@@ -98,6 +100,9 @@ typedef struct pexsi_dm_info {
   double gemm_flops;       /* algorithmic GEMM flops executed by the call       */
   int32_t n_poles;         /* poles evaluated by the call                       */
   int32_t breakdown_front; /* front of the first breakdown, -1 if none          */
+  double trace_ddm_s;      /* Tr[Gamma^d S] = N'(mu) (Sec. II.C): Gamma^d uses the
+                              weights of d f / d mu with the same poles; it is
+                              accumulated like the outputs (plan workspace)     */
 } pexsi_dm_info;
 
 /* Fill *opts with the defaults. */
@@ -193,6 +198,144 @@ int pexsi_inertia_device(pexsi_plan* plan, const double* dH, const double* dS,
  * and this call with rows == NULL, which only writes first, rptr and parent. */
 int pexsi_plan_get_supernodes(const pexsi_plan* plan, int32_t* first, int64_t* rptr, int32_t* rows,
                               int32_t* parent);
+
+/* ------------------------------------------------------------ chemical potential
+ * Sec. II.C: find mu with N_beta(mu) = Tr[DM S] = N_e (Eq. Nmu).
+ * 1. Inertia counting: N_inf(eps) = 2 x (# eigenvalues of (H,S) below eps) at
+ *    n_shifts points across [mu_lo, mu_hi]; N_beta is the linear interpolation
+ *    of those counts smoothed by -f'(eps - mu) (Eq. finiteelectronnumber). Two
+ *    roots N_beta(eps_l) = N_e - delta_n and N_beta(eps_h) = N_e + delta_n give
+ *    mu = (eps_l + eps_h)/2 (the gap rule) and a narrower bracket (the samples
+ *    enclosing the two roots, widened by 16/beta for the Fermi tail); this
+ *    repeats up to max_inertia times. A bracket that does not contain the
+ *    target count is widened by its own width (at most 8 times).
+ * 2. Newton: N(mu) = Tr[DM S] and N'(mu) = Tr[Gamma^d S] from one P-pole
+ *    evaluation each (Gamma^d shares the poles), mu <- mu - (N - N_e)/N',
+ *    bisection inside the bracket when the step leaves it, until
+ *    |N - N_e| <= tol_ne or max_newton evaluations.
+ * delta_e must cover the spectrum around every mu the search visits. dm,
+ * edm, fdm (host, nnz each, may be NULL) receive the matrices of the last
+ * evaluation. Errors as pexsi_dm; PEXSI_ERR_INVALID_ARG also when the target
+ * count cannot be bracketed. */
+typedef struct pexsi_mu_opts {
+  double mu_lo, mu_hi;   /* initial bracket                                     */
+  double n_electrons;    /* target N_e (both spins)                             */
+  double tol_ne;         /* |Tr[DM S] - N_e| tolerance (default 1e-6)            */
+  double delta_n;        /* gap-rule offset delta N (default 0.1)               */
+  int32_t n_shifts;      /* inertia shifts per counting cycle (default 16)      */
+  int32_t max_inertia;   /* counting cycles (default 3; 0 = Newton only)        */
+  int32_t max_newton;    /* P-pole evaluations (default 16)                     */
+  int32_t reserved0;
+} pexsi_mu_opts;
+
+typedef struct pexsi_mu_info {
+  double mu;             /* final chemical potential                           */
+  double n_e;            /* Tr[DM S] at mu                                      */
+  double dn_dmu;         /* Tr[Gamma^d S] at mu                                 */
+  double mu_inertia;     /* estimate after the inertia-counting cycles          */
+  double bracket_lo, bracket_hi;
+  int32_t inertia_cycles, newton_iters, converged, reserved0;
+} pexsi_mu_info;
+
+int pexsi_mu_opts_default(pexsi_mu_opts* opts);
+int pexsi_mu_solve(pexsi_plan* plan, const double* H, const double* S, double beta, int32_t n_poles,
+                   double delta_e, const pexsi_mu_opts* opts, double* dm, double* edm, double* fdm,
+                   pexsi_mu_info* info);
+
+/* ------------------------------------------------------------ DOS and LDOS
+ * Sec. II.D. pexsi_dos samples the cumulative density of states
+ * C(eps_k) = N_inf(eps_k) = 2 x #{eigenvalues of (H,S) < eps_k} (Eq. cdos; the
+ * factor 2 is spin, Eq. DOS) at n_points energies evenly spaced on
+ * [e_lo, e_hi] by inertia counting, and the DOS g(eps_k) as the derivative of
+ * the linear interpolation of C (central differences inside, one-sided at
+ * the ends). eps, cdos, dos: host arrays of n_points (n_points >= 2).
+ * pexsi_ldos writes the selected elements of the LDOS matrix
+ * (2/pi) Im [H - (eps + i eta) S]^{-1} on the pattern (Eq. LDOSGreen; its
+ * contraction with the basis functions, g(x, eps), is left to the caller).
+ * ldos: host array of nnz. eta > 0. Errors as pexsi_inertia / pexsi_selinv. */
+int pexsi_dos(pexsi_plan* plan, const double* H, const double* S, double e_lo, double e_hi, int32_t n_points,
+              double* eps, double* cdos, double* dos);
+int pexsi_ldos(pexsi_plan* plan, const double* H, const double* S, double eps, double eta, double* ldos);
+
+/* ------------------------------------------------------------ request server
+ * A continuous-batching request loop for DM and inertia solves of systems of
+ * different sizes (the serving pattern around Sec. II.C's inertia counting and
+ * Sec. II.A's pole expansion). The server owns `slots` worker threads, each
+ * with its own CUDA stream. A request waits in a FIFO queue until a slot is
+ * free AND its device footprint (fronts of `batch` poles of its plan plus
+ * staging) fits the HBM budget still unused; it is then admitted, its
+ * workspace is taken from the stream-ordered allocator, and its kernels run
+ * concurrently with those of the other admitted requests. Plans (symbolic
+ * structure and device maps) stay resident across requests; several requests
+ * may share one plan. Per request: the inertia counts at its shifts first,
+ * then the P-pole DM/EDM/FDM, copied into the caller's buffers. Results are
+ * the same as the plan calls give alone (the kernels are deterministic). */
+typedef struct pexsi_server pexsi_server;
+
+typedef struct pexsi_server_opts {
+  int32_t device;      /* CUDA device (default 0)                                 */
+  int32_t slots;       /* concurrently admitted requests (default 4)              */
+  int32_t batch;       /* poles per device batch of one request (default 8)       */
+  int32_t reserved0;
+  int64_t hbm_budget;  /* bytes all admitted workspaces may use, 0 = 60% of free  */
+} pexsi_server_opts;
+
+/* One request. H, S and shifts are copied at submit; the plan and the output
+ * buffers must stay valid until the request completes or is cancelled. */
+typedef struct pexsi_request {
+  const pexsi_plan* plan;   /* built by pexsi_setup on the server's device        */
+  const double* H;          /* nnz values (host)                                  */
+  const double* S;          /* nnz values (host), NULL = identity                 */
+  double mu, beta, delta_e; /* pole expansion parameters (Eq. polerho)            */
+  int32_t n_poles;          /* P (even); 0 = inertia only                         */
+  int32_t n_shifts;         /* number of inertia shifts, may be 0                 */
+  const double* shifts;     /* n_shifts real shifts (host)                        */
+  double* dm;               /* outputs, nnz each (host), any may be NULL          */
+  double* edm;
+  double* fdm;
+  int64_t* counts;          /* n_shifts inertia counts (host)                     */
+} pexsi_request;
+
+typedef struct pexsi_result {
+  int32_t status;           /* PEXSI_OK or a PEXSI_ERR_* code                     */
+  int32_t breakdown_front;  /* -1 if none                                         */
+  double trace_dm_s, trace_edm_s, trace_fdm_s;
+  double queue_ms;          /* submit -> admission                                */
+  double run_ms;            /* admission -> outputs in the caller's buffers       */
+  double latency_ms;        /* submit -> outputs ready                            */
+  int64_t footprint_bytes;  /* device bytes the request was admitted with         */
+  int32_t batch;            /* poles per device batch used                        */
+  int32_t max_concurrent;   /* requests running on the device at its admission    */
+} pexsi_result;
+
+typedef struct pexsi_server_stats {
+  int64_t submitted, completed, cancelled, failed;
+  int64_t queued, running;
+  int64_t bytes_in_use, peak_bytes, budget;
+  int32_t peak_concurrent, reserved0;
+} pexsi_server_stats;
+
+int pexsi_server_opts_default(pexsi_server_opts* opts);
+/* Errors: INVALID_ARG, CUDA, NOMEM. */
+int pexsi_server_create(const pexsi_server_opts* opts, pexsi_server** out);
+/* Queues a request; *ticket identifies it. Errors: INVALID_ARG (bad request,
+ * plan on another device or host-only), NOMEM (a single pole of this plan can
+ * never fit the budget). */
+int pexsi_server_submit(pexsi_server* server, const pexsi_request* req, int64_t* ticket);
+/* PEXSI_OK and *result when finished (also for failed or cancelled requests,
+ * see result->status), PEXSI_PENDING otherwise, INVALID_ARG for an unknown
+ * ticket. A finished ticket stays readable until pexsi_server_release. */
+int pexsi_server_poll(pexsi_server* server, int64_t ticket, pexsi_result* result);
+/* Blocks until the request finishes; returns as pexsi_server_poll. */
+int pexsi_server_wait(pexsi_server* server, int64_t ticket, pexsi_result* result);
+/* A queued request is removed at once; a running one stops after its current
+ * device batch. Its status becomes PEXSI_ERR_CANCELLED. */
+int pexsi_server_cancel(pexsi_server* server, int64_t ticket);
+/* Forget a finished ticket. */
+int pexsi_server_release(pexsi_server* server, int64_t ticket);
+int pexsi_server_get_stats(pexsi_server* server, pexsi_server_stats* stats);
+/* Cancels queued requests, waits for running ones, joins the workers. */
+int pexsi_server_destroy(pexsi_server* server);
 
 /* Allocation-free Tr[X S] for device-resident DM / EDM / FDM (no counterpart
  * in the paper; the traces themselves are Eq. Nmu and its energy analogues).

@@ -125,3 +125,22 @@ def trace_eig(lam, table, poles_idx):
         w = table[key][list(poles_idx)]
         out.append(float(np.sum(np.imag(w[None, :] / (lam[:, None] - z[None, :])))))
     return out
+
+
+def electron_count_poles(lam, beta, delta_e, n_poles, mu):
+    """N_P(mu) = sum_i Im sum_l w_l / (lam_i - z_l): the electron count the
+    P-pole expansion at mu gives for generalised eigenvalues lam (Eq. Nmu)."""
+    tab = poles.pole_table(beta, delta_e, n_poles, mu)
+    return float(np.sum(poles.rational_approx(lam, tab)))
+
+
+def chemical_potential(lam, beta, delta_e, n_poles, n_e, lo, hi):
+    """The mu in [lo, hi] with N_P(mu) = n_e (Sec. II.C), by bisection on the
+    non-decreasing N_P (Eq. Nmu)."""
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if electron_count_poles(lam, beta, delta_e, n_poles, mid) < n_e:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)

@@ -74,6 +74,15 @@ def free_energy_fn(x, beta):
     return -(2.0 / beta) * out
 
 
+def dfermi_dmu(x, beta):
+    """d/dmu f_beta(eps - mu) at x = eps - mu: (beta/2) f (2 - f) = -f'(x).
+
+    Weights for this function give Gamma^d, whose trace with S is N'(mu)
+    (Sec. II.C, the Newton step on the chemical potential)."""
+    f = fermi_dirac(x, beta)
+    return 0.5 * beta * f * (2.0 - f)
+
+
 def jacobi_sncndn(u, m):
     """sn, cn, dn(u | m) for complex u and real parameter 0 < m < 1.
 
@@ -133,6 +142,7 @@ def pole_table(beta, delta_e, n_poles, mu=0.0):
       ``w_rho`` -- weights for f_beta,
       ``w_E``   -- weights for (x + mu) f_beta(x),
       ``w_F``   -- weights for -(2/beta) ln(1 + exp(-beta x)),
+      ``w_d``   -- weights for d f / d mu = (beta/2) f (2 - f),
     such that  F(eps - mu) ~= Im sum_l w_l / (eps - z[l]).
     """
     x, c, _ = contour_nodes(beta, delta_e, n_poles)
@@ -141,6 +151,7 @@ def pole_table(beta, delta_e, n_poles, mu=0.0):
         "w_rho": lambda y: fermi_dirac(y, beta),
         "w_E": lambda y: energy_fn(y, beta, mu),
         "w_F": lambda y: free_energy_fn(y, beta),
+        "w_d": lambda y: dfermi_dmu(y, beta),
     }
     upper = shifts.imag > 0
     out = {"z": shifts[upper] + mu}

@@ -23,7 +23,10 @@ c_int64_p = ctypes.POINTER(ctypes.c_int64)
 c_double_p = ctypes.POINTER(ctypes.c_double)
 
 ERR_NAMES = {0: "PEXSI_OK", -1: "PEXSI_ERR_INVALID_ARG", -2: "PEXSI_ERR_NOT_SYMMETRIC", -3: "PEXSI_ERR_NOMEM",
-             -4: "PEXSI_ERR_CUDA", -5: "PEXSI_ERR_BREAKDOWN", -6: "PEXSI_ERR_INTERNAL"}
+             -4: "PEXSI_ERR_CUDA", -5: "PEXSI_ERR_BREAKDOWN", -6: "PEXSI_ERR_INTERNAL", -7: "PEXSI_ERR_CANCELLED",
+             1: "PEXSI_PENDING"}
+PEXSI_PENDING = 1
+PEXSI_ERR_CANCELLED = -7
 
 
 class PexsiError(RuntimeError):
@@ -51,7 +54,8 @@ class pexsi_dm_info(ctypes.Structure):
     _fields_ = [("trace_dm_s", ctypes.c_double), ("trace_edm_s", ctypes.c_double),
                 ("trace_fdm_s", ctypes.c_double), ("min_pivot_ratio", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("gemm_flops", ctypes.c_double),
-                ("n_poles", ctypes.c_int32), ("breakdown_front", ctypes.c_int32)]
+                ("n_poles", ctypes.c_int32), ("breakdown_front", ctypes.c_int32),
+                ("trace_ddm_s", ctypes.c_double)]
 
 
 class pexsi_kernel_profile(ctypes.Structure):
@@ -60,6 +64,45 @@ class pexsi_kernel_profile(ctypes.Structure):
 
 
 PROFILE_CLASSES = 11
+
+
+class pexsi_mu_opts(ctypes.Structure):
+    _fields_ = [("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double), ("n_electrons", ctypes.c_double),
+                ("tol_ne", ctypes.c_double), ("delta_n", ctypes.c_double), ("n_shifts", ctypes.c_int32),
+                ("max_inertia", ctypes.c_int32), ("max_newton", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
+class pexsi_mu_info(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("n_e", ctypes.c_double), ("dn_dmu", ctypes.c_double),
+                ("mu_inertia", ctypes.c_double), ("bracket_lo", ctypes.c_double), ("bracket_hi", ctypes.c_double),
+                ("inertia_cycles", ctypes.c_int32), ("newton_iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
+
+
+class pexsi_server_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("hbm_budget", ctypes.c_int64)]
+
+
+class pexsi_request(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("H", c_double_p), ("S", c_double_p), ("mu", ctypes.c_double),
+                ("beta", ctypes.c_double), ("delta_e", ctypes.c_double), ("n_poles", ctypes.c_int32),
+                ("n_shifts", ctypes.c_int32), ("shifts", c_double_p), ("dm", c_double_p), ("edm", c_double_p),
+                ("fdm", c_double_p), ("counts", c_int64_p)]
+
+
+class pexsi_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("breakdown_front", ctypes.c_int32), ("trace_dm_s", ctypes.c_double),
+                ("trace_edm_s", ctypes.c_double), ("trace_fdm_s", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
+                ("batch", ctypes.c_int32), ("max_concurrent", ctypes.c_int32)]
+
+
+class pexsi_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("peak_bytes", ctypes.c_int64), ("budget", ctypes.c_int64),
+                ("peak_concurrent", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 def _as_dict(st: ctypes.Structure) -> dict:
@@ -98,6 +141,23 @@ SIGNATURES = [
                                             ctypes.c_int32, c_int64_p, ctypes.c_void_p]),
     ("pexsi_trace_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    ("pexsi_mu_opts_default", ctypes.c_int, [ctypes.POINTER(pexsi_mu_opts)]),
+    ("pexsi_mu_solve", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double, ctypes.c_int32,
+                                      ctypes.c_double, ctypes.POINTER(pexsi_mu_opts), c_double_p, c_double_p,
+                                      c_double_p, ctypes.POINTER(pexsi_mu_info)]),
+    ("pexsi_dos", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int32, c_double_p, c_double_p, c_double_p]),
+    ("pexsi_ldos", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double, ctypes.c_double,
+                                  c_double_p]),
+    ("pexsi_server_opts_default", ctypes.c_int, [ctypes.POINTER(pexsi_server_opts)]),
+    ("pexsi_server_create", ctypes.c_int, [ctypes.POINTER(pexsi_server_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    ("pexsi_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pexsi_request), c_int64_p]),
+    ("pexsi_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(pexsi_result)]),
+    ("pexsi_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(pexsi_result)]),
+    ("pexsi_server_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("pexsi_server_release", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("pexsi_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pexsi_server_stats)]),
+    ("pexsi_server_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("pexsi_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("pexsi_last_error_detail", ctypes.c_char_p, [ctypes.c_void_p]),
 ]
@@ -311,6 +371,133 @@ def pexsi_trace_noalloc(d_dm, d_edm, d_fdm, d_S, nnz, d_out3, stream=0):
     rc = lib().pexsi_trace_noalloc(d_dm or None, d_edm or None, d_fdm or None, d_S or None, int(nnz),
                                    d_out3 or None, stream or None)
     _check(rc)
+
+
+# ---------------------------------------------------------------- mu search
+def pexsi_mu_opts_default(**overrides) -> pexsi_mu_opts:
+    o = pexsi_mu_opts()
+    _check(lib().pexsi_mu_opts_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def pexsi_mu_solve(plan, H, S, beta, n_poles, delta_e, opts: pexsi_mu_opts, want=("dm", "edm", "fdm")):
+    """Returns (dm, edm, fdm, info) at the chemical potential found."""
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _f64(H, nnz)
+    S = None if S is None else _f64(S, nnz)
+    outs = {k: (np.empty(nnz) if k in want else None) for k in ("dm", "edm", "fdm")}
+    info = pexsi_mu_info()
+    rc = lib().pexsi_mu_solve(plan, _ptr(H, ctypes.c_double), _ptr(S, ctypes.c_double), float(beta), int(n_poles),
+                              float(delta_e), ctypes.byref(opts), _ptr(outs["dm"], ctypes.c_double),
+                              _ptr(outs["edm"], ctypes.c_double), _ptr(outs["fdm"], ctypes.c_double),
+                              ctypes.byref(info))
+    _check(rc, plan)
+    return outs["dm"], outs["edm"], outs["fdm"], _as_dict(info)
+
+
+# ---------------------------------------------------------------- DOS / LDOS
+def pexsi_dos(plan, H, S, e_lo, e_hi, n_points):
+    """(eps, cdos, dos) arrays of n_points."""
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _f64(H, nnz)
+    S = None if S is None else _f64(S, nnz)
+    eps, cdos, dos = (np.empty(int(n_points)) for _ in range(3))
+    rc = lib().pexsi_dos(plan, _ptr(H, ctypes.c_double), _ptr(S, ctypes.c_double), float(e_lo), float(e_hi),
+                         int(n_points), _ptr(eps, ctypes.c_double), _ptr(cdos, ctypes.c_double),
+                         _ptr(dos, ctypes.c_double))
+    _check(rc, plan)
+    return eps, cdos, dos
+
+
+def pexsi_ldos(plan, H, S, eps, eta) -> np.ndarray:
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _f64(H, nnz)
+    S = None if S is None else _f64(S, nnz)
+    out = np.empty(nnz)
+    rc = lib().pexsi_ldos(plan, _ptr(H, ctypes.c_double), _ptr(S, ctypes.c_double), float(eps), float(eta),
+                          _ptr(out, ctypes.c_double))
+    _check(rc, plan)
+    return out
+
+
+# ---------------------------------------------------------------- server
+def pexsi_server_opts_default(**overrides) -> pexsi_server_opts:
+    o = pexsi_server_opts()
+    _check(lib().pexsi_server_opts_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def pexsi_server_create(opts: pexsi_server_opts | None = None):
+    h = ctypes.c_void_p()
+    _check(lib().pexsi_server_create(None if opts is None else ctypes.byref(opts), ctypes.byref(h)))
+    return h.value
+
+
+class ServerRequest:
+    """Keeps the numpy buffers of one submitted request alive until it is
+    collected (the server copies H, S and shifts at submit, but writes the
+    outputs into these arrays when the request completes)."""
+
+    def __init__(self, plan, H, S, mu=0.0, beta=1.0, n_poles=0, delta_e=1.0, shifts=None, want=("dm", "edm", "fdm")):
+        nnz = pexsi_plan_get_stats(plan)["nnz"]
+        self.H = _f64(H, nnz)
+        self.S = None if S is None else _f64(S, nnz)
+        self.shifts = None if shifts is None else _f64(np.atleast_1d(shifts))
+        nsh = 0 if self.shifts is None else self.shifts.shape[0]
+        self.dm = np.zeros(nnz) if (n_poles and "dm" in want) else None
+        self.edm = np.zeros(nnz) if (n_poles and "edm" in want) else None
+        self.fdm = np.zeros(nnz) if (n_poles and "fdm" in want) else None
+        self.counts = np.zeros(nsh, dtype=np.int64) if nsh else None
+        self.c = pexsi_request(plan, _ptr(self.H, ctypes.c_double), _ptr(self.S, ctypes.c_double), float(mu),
+                               float(beta), float(delta_e), int(n_poles), int(nsh), _ptr(self.shifts, ctypes.c_double),
+                               _ptr(self.dm, ctypes.c_double), _ptr(self.edm, ctypes.c_double),
+                               _ptr(self.fdm, ctypes.c_double), _ptr(self.counts, ctypes.c_int64))
+        self.ticket = None
+
+
+def pexsi_server_submit(server, request: ServerRequest) -> int:
+    t = ctypes.c_int64()
+    _check(lib().pexsi_server_submit(server, ctypes.byref(request.c), ctypes.byref(t)))
+    request.ticket = t.value
+    return t.value
+
+
+def pexsi_server_poll(server, ticket):
+    """None while pending, else the result dict."""
+    r = pexsi_result()
+    rc = lib().pexsi_server_poll(server, int(ticket), ctypes.byref(r))
+    if rc == PEXSI_PENDING:
+        return None
+    _check(rc)
+    return _as_dict(r)
+
+
+def pexsi_server_wait(server, ticket) -> dict:
+    r = pexsi_result()
+    _check(lib().pexsi_server_wait(server, int(ticket), ctypes.byref(r)))
+    return _as_dict(r)
+
+
+def pexsi_server_cancel(server, ticket):
+    _check(lib().pexsi_server_cancel(server, int(ticket)))
+
+
+def pexsi_server_release(server, ticket):
+    _check(lib().pexsi_server_release(server, int(ticket)))
+
+
+def pexsi_server_get_stats(server) -> dict:
+    st = pexsi_server_stats()
+    _check(lib().pexsi_server_get_stats(server, ctypes.byref(st)))
+    return _as_dict(st)
+
+
+def pexsi_server_destroy(server):
+    _check(lib().pexsi_server_destroy(server))
 
 
 def pexsi_strerror(code: int) -> str:

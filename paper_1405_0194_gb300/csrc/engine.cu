@@ -1,5 +1,6 @@
-// C ABI of the library: plan construction (host symbolic analysis + upload),
-// batched numeric factorisation / selected inversion / pole sum, inertia.
+// C ABI of the plan: host symbolic analysis + upload (pexsi_setup), and the
+// batched numeric drivers (pole batches through assembly, factorisation,
+// selected inversion and the pole sum; inertia shift batches).
 #include <algorithm>
 #include <cfloat>
 #include <climits>
@@ -10,29 +11,408 @@
 #include <string>
 #include <vector>
 
-#include "../../include/pexsi_gb300.h"
-#include "kernels.cuh"
-#include "symbolic.hpp"
+#include "plan.hpp"
 
 namespace pexsi {
-int pole_table(double beta, double delta_e, int P, double mu, std::vector<std::complex<double>>& z,
-               std::vector<std::complex<double>>& w_rho, std::vector<std::complex<double>>& w_E,
-               std::vector<std::complex<double>>& w_F);
+
+// ------------------------------------------------------------------ profiler
+namespace {
+const char* const kProfNames[PEXSI_PROFILE_CLASSES] = {
+    "assemble", "extend_add", "diag_inv", "panel_solve", "schur_update", "gather",
+    "selinv_offdiag", "selinv_diag_partial", "selinv_diag_reduce", "pole_sum", "trace"};
 }
 
-using pexsi::BatchShifts;
-using pexsi::DevFronts;
-using pexsi::DevStatus;
+cudaEvent_t Profiler::begin(cudaStream_t st) {
+  if (!on) return nullptr;
+  cudaEvent_t a;
+  if (!pool.empty()) { a = pool.back(); pool.pop_back(); }
+  else ck(cudaEventCreate(&a), "cudaEventCreate(profile)");
+  ck(cudaEventRecord(a, st), "cudaEventRecord(profile)");
+  return a;
+}
+
+void Profiler::end(cudaEvent_t a, int cls, cudaStream_t st, double fl, double by, int kernels) {
+  if (!on || !a) return;
+  cudaEvent_t b;
+  if (!pool.empty()) { b = pool.back(); pool.pop_back(); }
+  else ck(cudaEventCreate(&b), "cudaEventCreate(profile)");
+  ck(cudaEventRecord(b, st), "cudaEventRecord(profile)");
+  pending.push_back({cls, a, b, fl, by, kernels});
+}
+
+void Profiler::drain() {
+  for (auto& q : pending) {
+    ck(cudaEventSynchronize(q.b), "cudaEventSynchronize(profile)");
+    float t = 0;
+    ck(cudaEventElapsedTime(&t, q.a, q.b), "cudaEventElapsedTime(profile)");
+    launches[q.cls] += q.kernels;
+    ms[q.cls] += t;
+    flops[q.cls] += q.flops;
+    bytes[q.cls] += q.bytes;
+    pool.push_back(q.a);
+    pool.push_back(q.b);
+  }
+  pending.clear();
+}
+
+void Profiler::reset() {
+  drain();
+  for (int c = 0; c < PEXSI_PROFILE_CLASSES; ++c) { launches[c] = 0; ms[c] = flops[c] = bytes[c] = 0; }
+}
+
+void Profiler::destroy() {
+  for (auto& q : pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
+  for (auto e : pool) cudaEventDestroy(e);
+  pending.clear();
+  pool.clear();
+}
+
+// ------------------------------------------------------------------ workspaces
+int64_t bytes_per_pole(const pexsi_plan* p) {
+  return (2 * p->sym.front_elems + p->part_stride) * int64_t(sizeof(double2));
+}
+
+int64_t bytes_fixed(const pexsi_plan* p) {
+  return 9 * p->sym.nnz * int64_t(sizeof(double)) + 4 * p->trace_blocks * 8 + 4096;
+}
+
+namespace {
+template <typename T>
+void wsalloc(T** ptr, size_t bytes, Workspace& ws, const char* what) {
+  if (ws.async) ck(cudaMallocAsync(reinterpret_cast<void**>(ptr), bytes, ws.stream), what);
+  else ck(cudaMalloc(reinterpret_cast<void**>(ptr), bytes), what);
+  ws.bytes += int64_t(bytes);
+}
+}  // namespace
+
+void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t stream, bool async) {
+  ws.async = async;
+  ws.stream = stream;
+  ws.batch = batch;
+  ws.bytes = 0;
+  const size_t pool = size_t(p->sym.front_elems), nnz = size_t(p->sym.nnz);
+  wsalloc(&ws.F, sizeof(double2) * pool * batch, ws, "alloc(F)");
+  wsalloc(&ws.Y, sizeof(double2) * pool * batch, ws, "alloc(Y)");
+  wsalloc(&ws.part, sizeof(double2) * size_t(p->part_stride) * batch, ws, "alloc(partials)");
+  wsalloc(&ws.H, sizeof(double) * nnz, ws, "alloc(H)");
+  wsalloc(&ws.S, sizeof(double) * nnz, ws, "alloc(S)");
+  wsalloc(&ws.out, sizeof(double) * nnz * 4, ws, "alloc(outputs)");
+  wsalloc(&ws.brk, sizeof(int), ws, "alloc(status)");
+  wsalloc(&ws.minpiv, sizeof(unsigned long long), ws, "alloc(status)");
+  wsalloc(&ws.neg, sizeof(int) * kMaxBatch, ws, "alloc(status)");
+  wsalloc(&ws.partials, sizeof(double) * 4 * p->trace_blocks, ws, "alloc(trace)");
+  wsalloc(&ws.trace3, sizeof(double) * 4, ws, "alloc(trace)");
+  if (!ws.ev0) ck(cudaEventCreate(&ws.ev0), "cudaEventCreate");
+  if (!ws.ev1) ck(cudaEventCreate(&ws.ev1), "cudaEventCreate");
+}
+
+void workspace_free(Workspace& ws) {
+  void* ptrs[] = {ws.F, ws.Y, ws.part, ws.H, ws.S, ws.out, ws.brk, ws.minpiv, ws.neg, ws.partials, ws.trace3, ws.ainv};
+  for (void* q : ptrs) {
+    if (!q) continue;
+    if (ws.async) cudaFreeAsync(q, ws.stream);
+    else cudaFree(q);
+  }
+  if (ws.ev0) cudaEventDestroy(ws.ev0);
+  if (ws.ev1) cudaEventDestroy(ws.ev1);
+  cudaStream_t st = ws.stream;
+  bool async = ws.async;
+  ws = Workspace();
+  ws.stream = st;
+  ws.async = async;
+}
+
+// ------------------------------------------------------------------ drivers
+namespace {
+
+struct PanelGeom {
+  int nact = 0, row_tiles = 0, tri_tiles = 0;
+};
+
+PanelGeom panel_geom(const Level& lv, int p0, int b) {
+  PanelGeom g;
+  for (size_t t = 0; t < lv.fronts.size(); ++t) {
+    if (lv.s[t] <= p0) break;
+    ++g.nact;
+    int bb = std::min(b, lv.s[t] - p0);
+    int mp = lv.m[t] - p0 - bb;
+    int rt = (mp + kTile - 1) / kTile;
+    g.row_tiles = std::max(g.row_tiles, rt);
+    g.tri_tiles = std::max(g.tri_tiles, rt * (rt + 1) / 2);
+  }
+  return g;
+}
+
+// Algorithmic work of the fronts active at panel offset p0 (one batch member).
+struct PanelWork {
+  double diag_fl = 0, diag_by = 0, panel_fl = 0, panel_by = 0, schur_fl = 0, schur_by = 0;
+  double off_fl = 0, off_by = 0, dpart_fl = 0, dpart_by = 0, dred_by = 0;
+};
+
+PanelWork panel_work(const Level& lv, int p0, int b, double es, double fma_fl) {
+  PanelWork w;
+  for (size_t t = 0; t < lv.fronts.size(); ++t) {
+    if (lv.s[t] <= p0) break;
+    double bb = std::min(b, lv.s[t] - p0);
+    double mp = double(lv.m[t]) - p0 - bb;
+    double nt = std::ceil(mp / kTile);
+    w.diag_fl += fma_fl * bb * bb * bb;
+    w.diag_by += 2 * bb * bb * es;
+    w.panel_fl += fma_fl * mp * bb * bb;
+    w.panel_by += (3 * mp * bb + bb * bb) * es;
+    w.schur_fl += fma_fl * mp * (mp + 1) / 2 * bb;
+    w.schur_by += (mp * (mp + 1) + 2 * mp * bb) * es;
+    w.off_fl += fma_fl * mp * mp * bb;
+    w.off_by += (mp * mp + 3 * mp * bb) * es;
+    w.dpart_fl += fma_fl * bb * bb * mp;
+    w.dpart_by += (2 * mp * bb + nt * bb * bb) * es;
+    w.dred_by += (nt + 2) * bb * bb * es;
+  }
+  return w;
+}
+
+Profiler g_off;  // a profiler that is never switched on
+
+// Factor the batch in F (assembled), leaves to root.
+template <typename T>
+void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& sh, bool count, Profiler& pf) {
+  cudaStream_t st = ws.stream;
+  DevFronts fr = p->fronts();
+  DevStatus status{ws.brk, ws.minpiv, ws.neg};
+  const int b = p->b;
+  const double es = double(sizeof(T)), fl = sizeof(T) == 16 ? 8.0 : 2.0, nb = sh.nb;
+  for (size_t L = 0; L < p->levels.size(); ++L) {
+    const Level& lv = p->levels[L];
+    const int32_t* dfr = p->d_level_fronts + lv.front_off;
+    for (size_t k = 0; k < lv.ea_off.size(); ++k) {
+      cudaEvent_t a = pf.begin(st);
+      launch_extend_add<T>(F, fr, p->d_ea + lv.ea_off[k], lv.ea_count[k], lv.ea_tiles[k], sh, st);
+      pf.end(a, P_EXTEND, st, 0.0, nb * lv.ea_elems[k] * es);
+    }
+    for (int p0 = 0; p0 < lv.max_s; p0 += b) {
+      PanelGeom g = panel_geom(lv, p0, b);
+      PanelWork w = pf.on ? panel_work(lv, p0, b, es, fl) : PanelWork();
+      cudaEvent_t a = pf.begin(st);
+      launch_diag_inv<T>(F, fr, dfr, g.nact, p0, b, sh, status, count, st);
+      pf.end(a, P_DIAG, st, nb * w.diag_fl, nb * w.diag_by);
+      a = pf.begin(st);
+      launch_panel_solve<T>(F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
+      pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
+      a = pf.begin(st);
+      launch_trailing<T>(F, fr, dfr, g.nact, g.tri_tiles, p0, b, sh, st);
+      pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by);
+    }
+  }
+  ck(cudaGetLastError(), "factor kernels");
+}
+
+void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Profiler& pf) {
+  cudaStream_t st = ws.stream;
+  DevFronts fr = p->fronts();
+  const int b = p->b;
+  const double es = 16.0, nb = sh.nb;
+  for (int L = int(p->levels.size()) - 1; L >= 0; --L) {
+    const Level& lv = p->levels[L];
+    const int32_t* dfr = p->d_level_fronts + lv.front_off;
+    cudaEvent_t a = pf.begin(st);
+    launch_gather(ws.Y, fr, dfr, int(lv.fronts.size()), int(lv.gather_tiles), sh, st);
+    pf.end(a, P_GATHER, st, 0.0, nb * lv.gather_bytes);
+    int last = ((lv.max_s - 1) / b) * b;
+    for (int p0 = last; p0 >= 0; p0 -= b) {
+      PanelGeom g = panel_geom(lv, p0, b);
+      PanelWork w = pf.on ? panel_work(lv, p0, b, es, 8.0) : PanelWork();
+      a = pf.begin(st);
+      launch_selinv_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
+      pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by);
+      a = pf.begin(st);
+      launch_selinv_diag_partial(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.row_tiles,
+                                 p0, b, sh, st);
+      pf.end(a, P_DPART, st, nb * w.dpart_fl, nb * w.dpart_by);
+      a = pf.begin(st);
+      launch_selinv_diag_reduce(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, p0, b, sh, st);
+      pf.end(a, P_DRED, st, 0.0, nb * w.dred_by);
+    }
+  }
+  ck(cudaGetLastError(), "selinv kernels");
+}
+
+BatchShifts make_shifts(const std::vector<std::complex<double>>& z, const std::vector<std::complex<double>>* wr,
+                        const std::vector<std::complex<double>>* we, const std::vector<std::complex<double>>* wf,
+                        int begin, int nb, const std::vector<std::complex<double>>* wd = nullptr) {
+  BatchShifts sh;
+  std::memset(&sh, 0, sizeof(sh));
+  sh.nb = nb;
+  for (int t = 0; t < nb; ++t) {
+    sh.re[t] = z[begin + t].real();
+    sh.im[t] = z[begin + t].imag();
+    if (wr) { sh.wr_re[t] = (*wr)[begin + t].real(); sh.wr_im[t] = (*wr)[begin + t].imag(); }
+    if (we) { sh.we_re[t] = (*we)[begin + t].real(); sh.we_im[t] = (*we)[begin + t].imag(); }
+    if (wf) { sh.wf_re[t] = (*wf)[begin + t].real(); sh.wf_im[t] = (*wf)[begin + t].imag(); }
+    if (wd) { sh.wd_re[t] = (*wd)[begin + t].real(); sh.wd_im[t] = (*wd)[begin + t].imag(); }
+  }
+  return sh;
+}
+
+const int kBig = INT_MAX;
+const unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+void reset_status(Workspace& ws) {
+  ck(cudaMemcpyAsync(ws.brk, &kBig, sizeof(int), cudaMemcpyHostToDevice, ws.stream), "status");
+  ck(cudaMemcpyAsync(ws.minpiv, &kInfBits, sizeof(kInfBits), cudaMemcpyHostToDevice, ws.stream), "status");
+}
+
+// One batch of complex shifts through assembly, factorisation and selected
+// inversion; the result is left in ws.Y.
+void run_complex_batch(const pexsi_plan* p, Workspace& ws, const double* dH, const double* dS, const BatchShifts& sh,
+                       Profiler& pf) {
+  const int64_t pool = p->sym.front_elems;
+  ck(cudaMemsetAsync(ws.F, 0, sizeof(double2) * size_t(pool) * sh.nb, ws.stream), "memset(F)");
+  cudaEvent_t a = pf.begin(ws.stream);
+  launch_assemble<double2>(ws.F, dH, dS, p->d_asm_src, p->d_asm_pos, p->nlow, pool, sh, ws.stream);
+  pf.end(a, P_ASSEMBLE, ws.stream, 0.0, double(p->nlow) * (32.0 + 16.0 * sh.nb));
+  factor_batch<double2>(p, ws, ws.F, sh, false, pf);
+  selinv_batch(p, ws, sh, pf);
+}
+
+}  // namespace
+
+int dm_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* dH, const double* dS, double mu,
+             double beta, int P, double delta_e, int begin, int end, int accumulate, double* d_dm, double* d_edm,
+             double* d_fdm, pexsi_dm_info* info, std::string* err) {
+  Profiler& pf = prof ? *prof : g_off;
+  std::vector<std::complex<double>> z, wr, we, wf, wd;
+  int rc = pole_table(beta, delta_e, P, mu, z, wr, we, wf, &wd);
+  if (rc) { *err = "bad pole-expansion parameters"; return rc; }
+  const double* S = dS ? dS : p->d_ident;
+  cudaStream_t st = ws.stream;
+  double* d_ddm = ws.out + 3 * p->sym.nnz;
+  if (info) ck(cudaEventRecord(ws.ev0, st), "event");
+  reset_status(ws);
+  bool first = true;
+  for (int b0 = begin; b0 < end; b0 += ws.batch) {
+    int nb = std::min(ws.batch, end - b0);
+    BatchShifts sh = make_shifts(z, &wr, &we, &wf, b0, nb, &wd);
+    run_complex_batch(p, ws, dH, S, sh, pf);
+    int overwrite = (first && !accumulate) ? 1 : 0;
+    cudaEvent_t a = pf.begin(st);
+    launch_pole_sum(ws.Y, p->sym.front_elems, p->d_entry_pos, p->sym.nnz, sh, overwrite, d_dm, d_edm, d_fdm, d_ddm,
+                    st);
+    int nout = 1 + (d_dm ? 1 : 0) + (d_edm ? 1 : 0) + (d_fdm ? 1 : 0);
+    pf.end(a, P_POLESUM, st, 6.0 * nout * nb * double(p->sym.nnz),
+           double(p->sym.nnz) * (8.0 + 16.0 * nb + 8.0 * nout * (overwrite ? 1 : 2)));
+    first = false;
+  }
+  ck(cudaGetLastError(), "pole sum");
+  if (!info) return PEXSI_OK;
+  std::memset(info, 0, sizeof(*info));
+  cudaEvent_t a = pf.begin(st);
+  launch_traces(d_dm, d_edm, d_fdm, d_ddm, S, p->sym.nnz, ws.partials, p->trace_blocks, ws.trace3, st);
+  pf.end(a, P_TRACE, st, 8.0 * double(p->sym.nnz), 40.0 * double(p->sym.nnz), 2);
+  ck(cudaEventRecord(ws.ev1, st), "event");
+  double tr[4] = {0, 0, 0, 0};
+  int brk = INT_MAX;
+  unsigned long long mp = 0;
+  ck(cudaMemcpyAsync(tr, ws.trace3, sizeof(tr), cudaMemcpyDeviceToHost, st), "trace");
+  ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+  ck(cudaMemcpyAsync(&mp, ws.minpiv, sizeof(mp), cudaMemcpyDeviceToHost, st), "status");
+  ck(cudaStreamSynchronize(st), "sync");
+  float ms = 0;
+  ck(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1), "event");
+  info->trace_dm_s = d_dm ? tr[0] : 0.0;
+  info->trace_edm_s = d_edm ? tr[1] : 0.0;
+  info->trace_fdm_s = d_fdm ? tr[2] : 0.0;
+  info->trace_ddm_s = tr[3];
+  std::memcpy(&info->min_pivot_ratio, &mp, sizeof(double));
+  info->ms_total = ms;
+  info->gemm_flops = (p->flops.factor_gemm + p->flops.selinv_gemm) * (end - begin);
+  info->n_poles = end - begin;
+  info->breakdown_front = brk == INT_MAX ? -1 : brk;
+  if (brk != INT_MAX) {
+    *err = "zero or tiny pivot in front " + std::to_string(brk);
+    return PEXSI_ERR_BREAKDOWN;
+  }
+  return PEXSI_OK;
+}
+
+int inertia_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* dH, const double* dS,
+                  const double* shifts, int n_shifts, int64_t* counts, std::string* err) {
+  Profiler& pf = prof ? *prof : g_off;
+  const double* S = dS ? dS : p->d_ident;
+  cudaStream_t st = ws.stream;
+  const int64_t pool = p->sym.front_elems;
+  // real fronts: the complex pool holds twice as many real ones
+  const int cap = std::min(kMaxBatch, 2 * ws.batch);
+  double* F = reinterpret_cast<double*>(ws.F);
+  std::vector<std::complex<double>> z(n_shifts);
+  for (int t = 0; t < n_shifts; ++t) z[t] = {shifts[t], 0.0};
+  int brk_all = INT_MAX;
+  for (int b0 = 0; b0 < n_shifts; b0 += cap) {
+    int nb = std::min(cap, n_shifts - b0);
+    BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, b0, nb);
+    reset_status(ws);
+    ck(cudaMemsetAsync(ws.neg, 0, sizeof(int) * kMaxBatch, st), "status");
+    ck(cudaMemsetAsync(F, 0, sizeof(double) * size_t(pool) * nb, st), "memset(F)");
+    cudaEvent_t a = pf.begin(st);
+    launch_assemble<double>(F, dH, S, p->d_asm_src, p->d_asm_pos, p->nlow, pool, sh, st);
+    pf.end(a, P_ASSEMBLE, st, 0.0, double(p->nlow) * (32.0 + 8.0 * nb));
+    factor_batch<double>(p, ws, F, sh, true, pf);
+    int neg[kMaxBatch];
+    int brk = INT_MAX;
+    ck(cudaMemcpyAsync(neg, ws.neg, sizeof(int) * nb, cudaMemcpyDeviceToHost, st), "D2H(counts)");
+    ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    ck(cudaStreamSynchronize(st), "sync");
+    for (int t = 0; t < nb; ++t) counts[b0 + t] = neg[t];
+    brk_all = std::min(brk_all, brk);
+  }
+  if (brk_all != INT_MAX) {
+    *err = "zero or tiny pivot in front " + std::to_string(brk_all);
+    return PEXSI_ERR_BREAKDOWN;
+  }
+  return PEXSI_OK;
+}
+
+int selinv_one(const pexsi_plan* p, Workspace& ws, const double* dH, const double* dS, double z_re, double z_im,
+               double2* d_ainv, std::string* err) {
+  std::vector<std::complex<double>> z{{z_re, z_im}};
+  BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, 0, 1);
+  reset_status(ws);
+  run_complex_batch(p, ws, dH, dS ? dS : p->d_ident, sh, g_off);
+  launch_extract(ws.Y, p->d_entry_pos, p->sym.nnz, d_ainv, ws.stream);
+  ck(cudaGetLastError(), "extract");
+  int brk = INT_MAX;
+  ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, ws.stream), "status");
+  ck(cudaStreamSynchronize(ws.stream), "sync");
+  if (brk != INT_MAX) {
+    *err = "zero or tiny pivot in front " + std::to_string(brk);
+    return PEXSI_ERR_BREAKDOWN;
+  }
+  return PEXSI_OK;
+}
+
+}  // namespace pexsi
+
+using namespace pexsi;
 
 namespace {
 
-struct CudaError {
-  cudaError_t e;
-  const char* what;
-};
+void free_plan_device(pexsi_plan* p) {
+  void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
+                  p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_ident};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  cudaStream_t st = p->ws.stream;
+  workspace_free(p->ws);
+  p->prof.destroy();
+  if (st) cudaStreamDestroy(st);
+}
 
-inline void ck(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) throw CudaError{e, what};
+int fail(pexsi_plan* p, int code, const std::string& msg) {
+  if (p) p->last_error = msg;
+  return code;
+}
+
+int map_cuda(pexsi_plan* p, const CudaError& ce) {
+  return fail(p, PEXSI_ERR_CUDA, std::string(ce.what) + ": " + cudaGetErrorString(ce.e));
 }
 
 template <typename T>
@@ -44,151 +424,13 @@ T* dev_upload(const std::vector<T>& h) {
   return d;
 }
 
-// Host-side launch geometry of one level: fronts sorted by width descending,
-// so the fronts still active at panel offset p0 (s > p0) are a prefix.
-struct Level {
-  int64_t front_off = 0;  // into d_level_fronts
-  std::vector<int32_t> fronts, s, m;
-  // extend-add: children of this level's fronts grouped by child rank
-  std::vector<int64_t> ea_off;
-  std::vector<int32_t> ea_count, ea_tiles;
-  std::vector<double> ea_bytes;  // elements moved by each extend-add launch (read U, read+write parent)
-  int64_t gather_tiles = 0;
-  double gather_bytes = 0;       // bytes of the gathers of this level (one batch member)
-  int32_t max_s = 0;
-};
-
-const char* const kProfNames[PEXSI_PROFILE_CLASSES] = {
-    "assemble", "extend_add", "diag_inv", "panel_solve", "schur_update", "gather",
-    "selinv_offdiag", "selinv_diag_partial", "selinv_diag_reduce", "pole_sum", "trace"};
-enum ProfClass { P_ASSEMBLE, P_EXTEND, P_DIAG, P_PANEL, P_SCHUR, P_GATHER, P_OFFDIAG, P_DPART, P_DRED, P_POLESUM, P_TRACE };
-
-// CUDA-event bracketing of kernel launches, per class; elapsed times are read
-// back only when the caller asks, after the stream has drained.
-struct Profiler {
-  bool on = false;
-  struct Pending { int cls; cudaEvent_t a, b; double flops, bytes; };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> pool;
-  int64_t launches[PEXSI_PROFILE_CLASSES] = {};
-  double ms[PEXSI_PROFILE_CLASSES] = {}, flops[PEXSI_PROFILE_CLASSES] = {}, bytes[PEXSI_PROFILE_CLASSES] = {};
-  cudaEvent_t take() {
-    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
-    cudaEvent_t e;
-    ck(cudaEventCreate(&e), "cudaEventCreate(profile)");
-    return e;
-  }
-  cudaEvent_t begin(cudaStream_t st) {
-    if (!on) return nullptr;
-    cudaEvent_t a = take();
-    ck(cudaEventRecord(a, st), "cudaEventRecord(profile)");
-    return a;
-  }
-  void end(cudaEvent_t a, int cls, cudaStream_t st, double fl, double by) {
-    if (!on || !a) return;
-    cudaEvent_t b = take();
-    ck(cudaEventRecord(b, st), "cudaEventRecord(profile)");
-    pending.push_back({cls, a, b, fl, by});
-  }
-  void drain() {
-    for (auto& q : pending) {
-      ck(cudaEventSynchronize(q.b), "cudaEventSynchronize(profile)");
-      float t = 0;
-      ck(cudaEventElapsedTime(&t, q.a, q.b), "cudaEventElapsedTime(profile)");
-      launches[q.cls] += 1;
-      ms[q.cls] += t;
-      flops[q.cls] += q.flops;
-      bytes[q.cls] += q.bytes;
-      pool.push_back(q.a);
-      pool.push_back(q.b);
-    }
-    pending.clear();
-  }
-  void reset() {
-    drain();
-    for (int c = 0; c < PEXSI_PROFILE_CLASSES; ++c) { launches[c] = 0; ms[c] = flops[c] = bytes[c] = 0; }
-  }
-  void destroy() {
-    for (auto& q : pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
-    for (auto e : pool) cudaEventDestroy(e);
-    pending.clear();
-    pool.clear();
-  }
-};
-
-}  // namespace
-
-struct pexsi_plan {
-  pexsi::Symbolic sym;
-  pexsi_opts opts{};
-  std::string last_error;
-  int b = 64;
-  // device plan
-  int64_t* d_front_off = nullptr;
-  int32_t *d_s = nullptr, *d_m = nullptr, *d_parent = nullptr, *d_rel = nullptr;
-  int64_t* d_rptr = nullptr;
-  int64_t *d_asm_src = nullptr, *d_asm_pos = nullptr;
-  int64_t nlow = 0;
-  int64_t* d_entry_pos = nullptr;
-  int32_t* d_level_fronts = nullptr;
-  int32_t* d_ea = nullptr;
-  int64_t* d_part_off = nullptr;
-  int64_t part_stride = 0;  // elements of partial scratch per batch member
-  std::vector<Level> levels;
-  // workspace
-  int batch = 0;
-  double2 *d_F = nullptr, *d_Y = nullptr, *d_part = nullptr;
-  double *d_H = nullptr, *d_S = nullptr, *d_ident = nullptr;
-  double *d_dm = nullptr, *d_edm = nullptr, *d_fdm = nullptr;
-  double2* d_ainv = nullptr;
-  int* d_break = nullptr;
-  unsigned long long* d_minpiv = nullptr;
-  int* d_neg = nullptr;
-  double* d_partials = nullptr;
-  double* d_trace3 = nullptr;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  pexsi::FlopCounts flops;
-  int trace_blocks = 256;
-  Profiler prof;
-
-  DevFronts fronts() const {
-    DevFronts f;
-    f.off = d_front_off; f.s = d_s; f.m = d_m; f.parent = d_parent; f.rptr = d_rptr; f.rel = d_rel;
-    f.pool = sym.front_elems;
-    return f;
-  }
-};
-
-namespace {
-
-void free_plan_device(pexsi_plan* p) {
-  // d_edm and d_fdm point into the d_dm allocation and are not freed separately
-  void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
-                  p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_F, p->d_Y, p->d_part, p->d_H,
-                  p->d_S, p->d_ident, p->d_dm, p->d_ainv, p->d_break, p->d_minpiv, p->d_neg, p->d_partials,
-                  p->d_trace3};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
-  p->prof.destroy();
-  if (p->stream) cudaStreamDestroy(p->stream);
-  if (p->ev0) cudaEventDestroy(p->ev0);
-  if (p->ev1) cudaEventDestroy(p->ev1);
-}
-
-int fail(pexsi_plan* p, int code, const std::string& msg) {
-  if (p) p->last_error = msg;
-  return code;
-}
-
 void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector<int32_t>& ea,
                   std::vector<int64_t>& part_off) {
-  const pexsi::Symbolic& S = p->sym;
+  const Symbolic& S = p->sym;
   const int b = p->b;
   p->levels.assign(S.nlevels, Level());
   part_off.assign(S.nsuper, 0);
   p->part_stride = 0;
-  // children per front, in index order
   std::vector<std::vector<int32_t>> kids(S.nsuper);
   for (int32_t K = 0; K < S.nsuper; ++K)
     if (S.parent[K] >= 0) kids[S.parent[K]].push_back(K);
@@ -209,10 +451,9 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
       if (S.parent[K] >= 0) lv.gather_bytes += 2.0 * 16.0 * double(r) * double(r);
       int64_t first_mp = S.m(K) - std::min(b, S.s(K));
       part_off[K] = slots * int64_t(b) * b;
-      slots += (first_mp + pexsi::kTile - 1) / pexsi::kTile;
+      slots += (first_mp + kTile - 1) / kTile;
     }
     p->part_stride = std::max<int64_t>(p->part_stride, slots * int64_t(b) * b);
-    // extend-add groups: rank k = k-th child of each parent
     size_t maxk = 0;
     for (int32_t K : fr) maxk = std::max(maxk, kids[K].size());
     for (size_t k = 0; k < maxk; ++k) {
@@ -228,7 +469,7 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
         tiles = std::max(tiles, T * (T + 1) / 2);
         elems += 3.0 * double(r) * (r + 1) / 2;
       }
-      lv.ea_bytes.push_back(elems);
+      lv.ea_elems.push_back(elems);
       lv.ea_count.push_back(cnt);
       lv.ea_tiles.push_back(tiles);
     }
@@ -236,194 +477,40 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
   if (p->part_stride == 0) p->part_stride = int64_t(b) * b;
 }
 
-// Number of active fronts at p0 and the grid extents the kernels need.
-struct PanelGeom {
-  int nact = 0, row_tiles = 0, tri_tiles = 0;
-};
-
-PanelGeom panel_geom(const Level& lv, int p0, int b) {
-  PanelGeom g;
-  for (size_t t = 0; t < lv.fronts.size(); ++t) {
-    if (lv.s[t] <= p0) break;
-    ++g.nact;
-    int bb = std::min(b, lv.s[t] - p0);
-    int mp = lv.m[t] - p0 - bb;
-    int rt = (mp + pexsi::kTile - 1) / pexsi::kTile;
-    g.row_tiles = std::max(g.row_tiles, rt);
-    g.tri_tiles = std::max(g.tri_tiles, rt * (rt + 1) / 2);
-  }
-  return g;
-}
-
+// The plan's own workspace: the largest batch that fits the budget.
 int ensure_workspace(pexsi_plan* p) {
-  if (p->batch > 0) return PEXSI_OK;
-  const int64_t pool = p->sym.front_elems;
+  if (p->ws.batch > 0) return PEXSI_OK;
   size_t free_b = 0, total_b = 0;
   ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
   int64_t budget = p->opts.hbm_budget > 0 ? p->opts.hbm_budget : int64_t(0.6 * double(free_b));
-  int64_t per = 2 * pool * int64_t(sizeof(double2)) + p->part_stride * int64_t(sizeof(double2));
-  int64_t nb = budget / std::max<int64_t>(per, 1);
+  int64_t nb = (budget - bytes_fixed(p)) / std::max<int64_t>(bytes_per_pole(p), 1);
   if (p->opts.max_batch > 0) nb = std::min<int64_t>(nb, p->opts.max_batch);
-  nb = std::min<int64_t>(nb, pexsi::kMaxBatch);
+  nb = std::min<int64_t>(nb, kMaxBatch);
   if (nb < 1) return fail(p, PEXSI_ERR_NOMEM, "device workspace for one pole exceeds the HBM budget");
-  size_t nnz = size_t(p->sym.nnz);
-  ck(cudaMalloc(&p->d_F, sizeof(double2) * size_t(pool) * nb), "cudaMalloc(F)");
-  ck(cudaMalloc(&p->d_Y, sizeof(double2) * size_t(pool) * nb), "cudaMalloc(Y)");
-  ck(cudaMalloc(&p->d_part, sizeof(double2) * size_t(p->part_stride) * nb), "cudaMalloc(partials)");
-  ck(cudaMalloc(&p->d_H, sizeof(double) * nnz), "cudaMalloc(H)");
-  ck(cudaMalloc(&p->d_S, sizeof(double) * nnz), "cudaMalloc(S)");
-  ck(cudaMalloc(&p->d_dm, sizeof(double) * nnz * 3), "cudaMalloc(dm)");
-  p->d_edm = p->d_dm + nnz;
-  p->d_fdm = p->d_dm + 2 * nnz;
-  p->batch = int(nb);
+  workspace_alloc(p, p->ws, int(nb), p->ws.stream, false);
   return PEXSI_OK;
 }
 
-void reset_status(pexsi_plan* p) {
-  int big = INT_MAX;
-  unsigned long long one = 0x7FF0000000000000ull;  // +inf
-  ck(cudaMemcpyAsync(p->d_break, &big, sizeof(int), cudaMemcpyHostToDevice, p->stream), "status");
-  ck(cudaMemcpyAsync(p->d_minpiv, &one, sizeof(one), cudaMemcpyHostToDevice, p->stream), "status");
-}
+}  // namespace
 
-// Algorithmic work of the fronts active at panel offset p0 (one batch member).
-struct PanelWork {
-  double diag_fl = 0, diag_by = 0, panel_fl = 0, panel_by = 0, schur_fl = 0, schur_by = 0;
-  double off_fl = 0, off_by = 0, dpart_fl = 0, dpart_by = 0, dred_by = 0;
-};
+int pexsi::plan_workspace(pexsi_plan* p) { return ensure_workspace(p); }
 
-PanelWork panel_work(const Level& lv, int p0, int b, double es, double fma_fl) {
-  PanelWork w;
-  for (size_t t = 0; t < lv.fronts.size(); ++t) {
-    if (lv.s[t] <= p0) break;
-    double bb = std::min(b, lv.s[t] - p0);
-    double mp = double(lv.m[t]) - p0 - bb;
-    double nt = std::ceil(mp / pexsi::kTile);
-    w.diag_fl += fma_fl * bb * bb * bb;
-    w.diag_by += 2 * bb * bb * es;
-    w.panel_fl += fma_fl * mp * bb * bb;
-    w.panel_by += (3 * mp * bb + bb * bb) * es;
-    w.schur_fl += fma_fl * mp * (mp + 1) / 2 * bb;
-    w.schur_by += (mp * (mp + 1) + 2 * mp * bb) * es;
-    w.off_fl += fma_fl * mp * mp * bb;
-    w.off_by += (mp * mp + 3 * mp * bb) * es;
-    w.dpart_fl += fma_fl * bb * bb * mp;
-    w.dpart_by += (2 * mp * bb + nt * bb * bb) * es;
-    w.dred_by += (nt + 2) * bb * bb * es;
+namespace {
+
+// Runs fn with the plan's workspace temporarily on `stream` (NULL = its own).
+template <typename Fn>
+int on_stream(pexsi_plan* p, void* stream, Fn fn) {
+  cudaStream_t own = p->ws.stream;
+  if (stream) p->ws.stream = static_cast<cudaStream_t>(stream);
+  int rc;
+  try {
+    rc = fn();
+  } catch (...) {
+    p->ws.stream = own;
+    throw;
   }
-  return w;
-}
-
-// Factor the batch in F (assembled), leaves to root.
-template <typename T>
-void factor_batch(pexsi_plan* p, T* F, const BatchShifts& sh, bool count, cudaStream_t st) {
-  DevFronts fr = p->fronts();
-  DevStatus status{p->d_break, p->d_minpiv, p->d_neg};
-  const int b = p->b;
-  const double es = double(sizeof(T)), fl = sizeof(T) == 16 ? 8.0 : 2.0, nb = sh.nb;
-  Profiler& pf = p->prof;
-  for (size_t L = 0; L < p->levels.size(); ++L) {
-    const Level& lv = p->levels[L];
-    const int32_t* dfr = p->d_level_fronts + lv.front_off;
-    for (size_t k = 0; k < lv.ea_off.size(); ++k) {
-      cudaEvent_t a = pf.begin(st);
-      pexsi::launch_extend_add<T>(F, fr, p->d_ea + lv.ea_off[k], lv.ea_count[k], lv.ea_tiles[k], sh, st);
-      pf.end(a, P_EXTEND, st, 0.0, nb * lv.ea_bytes[k] * es);
-    }
-    for (int p0 = 0; p0 < lv.max_s; p0 += b) {
-      PanelGeom g = panel_geom(lv, p0, b);
-      PanelWork w = pf.on ? panel_work(lv, p0, b, es, fl) : PanelWork();
-      cudaEvent_t a = pf.begin(st);
-      pexsi::launch_diag_inv<T>(F, fr, dfr, g.nact, p0, b, sh, status, count, st);
-      pf.end(a, P_DIAG, st, nb * w.diag_fl, nb * w.diag_by);
-      a = pf.begin(st);
-      pexsi::launch_panel_solve<T>(F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
-      pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
-      a = pf.begin(st);
-      pexsi::launch_trailing<T>(F, fr, dfr, g.nact, g.tri_tiles, p0, b, sh, st);
-      pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by);
-    }
-  }
-  ck(cudaGetLastError(), "factor kernels");
-}
-
-void selinv_batch(pexsi_plan* p, const BatchShifts& sh, cudaStream_t st) {
-  DevFronts fr = p->fronts();
-  const int b = p->b;
-  const double es = 16.0, nb = sh.nb;
-  Profiler& pf = p->prof;
-  for (int L = int(p->levels.size()) - 1; L >= 0; --L) {
-    const Level& lv = p->levels[L];
-    const int32_t* dfr = p->d_level_fronts + lv.front_off;
-    cudaEvent_t a = pf.begin(st);
-    pexsi::launch_gather(p->d_Y, fr, dfr, int(lv.fronts.size()), int(lv.gather_tiles), sh, st);
-    pf.end(a, P_GATHER, st, 0.0, nb * lv.gather_bytes);
-    int last = ((lv.max_s - 1) / b) * b;
-    for (int p0 = last; p0 >= 0; p0 -= b) {
-      PanelGeom g = panel_geom(lv, p0, b);
-      PanelWork w = pf.on ? panel_work(lv, p0, b, es, 8.0) : PanelWork();
-      a = pf.begin(st);
-      pexsi::launch_selinv_offdiag(p->d_Y, p->d_F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
-      pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by);
-      a = pf.begin(st);
-      pexsi::launch_selinv_diag_partial(p->d_Y, p->d_F, p->d_part, p->d_part_off, p->part_stride, fr, dfr, g.nact,
-                                        g.row_tiles, p0, b, sh, st);
-      pf.end(a, P_DPART, st, nb * w.dpart_fl, nb * w.dpart_by);
-      a = pf.begin(st);
-      pexsi::launch_selinv_diag_reduce(p->d_Y, p->d_F, p->d_part, p->d_part_off, p->part_stride, fr, dfr, g.nact,
-                                       p0, b, sh, st);
-      pf.end(a, P_DRED, st, 0.0, nb * w.dred_by);
-    }
-  }
-  ck(cudaGetLastError(), "selinv kernels");
-}
-
-BatchShifts make_shifts(const std::vector<std::complex<double>>& z, const std::vector<std::complex<double>>* wr,
-                        const std::vector<std::complex<double>>* we, const std::vector<std::complex<double>>* wf,
-                        int begin, int nb) {
-  BatchShifts sh;
-  std::memset(&sh, 0, sizeof(sh));
-  sh.nb = nb;
-  for (int t = 0; t < nb; ++t) {
-    sh.re[t] = z[begin + t].real();
-    sh.im[t] = z[begin + t].imag();
-    if (wr) { sh.wr_re[t] = (*wr)[begin + t].real(); sh.wr_im[t] = (*wr)[begin + t].imag(); }
-    if (we) { sh.we_re[t] = (*we)[begin + t].real(); sh.we_im[t] = (*we)[begin + t].imag(); }
-    if (wf) { sh.wf_re[t] = (*wf)[begin + t].real(); sh.wf_im[t] = (*wf)[begin + t].imag(); }
-  }
-  return sh;
-}
-
-// One batch of complex shifts through assembly, factorisation and selected
-// inversion; the result is left in p->d_Y.
-void run_complex_batch(pexsi_plan* p, const double* dH, const double* dS, const BatchShifts& sh, cudaStream_t st) {
-  const int64_t pool = p->sym.front_elems;
-  ck(cudaMemsetAsync(p->d_F, 0, sizeof(double2) * size_t(pool) * sh.nb, st), "memset(F)");
-  cudaEvent_t a = p->prof.begin(st);
-  pexsi::launch_assemble<double2>(p->d_F, dH, dS, p->d_asm_src, p->d_asm_pos, p->nlow, pool, sh, st);
-  p->prof.end(a, P_ASSEMBLE, st, 0.0, double(p->nlow) * (32.0 + 16.0 * sh.nb));
-  factor_batch<double2>(p, p->d_F, sh, false, st);
-  selinv_batch(p, sh, st);
-}
-
-int map_cuda(pexsi_plan* p, const CudaError& ce) {
-  return fail(p, PEXSI_ERR_CUDA, std::string(ce.what) + ": " + cudaGetErrorString(ce.e));
-}
-
-int check_breakdown(pexsi_plan* p, pexsi_dm_info* info) {
-  int brk = INT_MAX;
-  unsigned long long mp = 0;
-  ck(cudaMemcpyAsync(&brk, p->d_break, sizeof(int), cudaMemcpyDeviceToHost, p->stream), "status");
-  ck(cudaMemcpyAsync(&mp, p->d_minpiv, sizeof(mp), cudaMemcpyDeviceToHost, p->stream), "status");
-  ck(cudaStreamSynchronize(p->stream), "sync");
-  double ratio;
-  std::memcpy(&ratio, &mp, sizeof(ratio));
-  if (info) {
-    info->min_pivot_ratio = ratio;
-    info->breakdown_front = brk == INT_MAX ? -1 : brk;
-  }
-  if (brk != INT_MAX) return fail(p, PEXSI_ERR_BREAKDOWN, "zero or tiny pivot in front " + std::to_string(brk));
-  return PEXSI_OK;
+  p->ws.stream = own;
+  return rc;
 }
 
 }  // namespace
@@ -437,8 +524,6 @@ int pexsi_opts_default(pexsi_opts* o) {
   o->panel = 64;
   o->leaf_cols = 96;
   o->amalgamate = 1;
-  o->max_batch = 0;
-  o->hbm_budget = 0;
   return PEXSI_OK;
 }
 
@@ -490,6 +575,8 @@ const char* pexsi_strerror(int code) {
     case PEXSI_ERR_CUDA: return "CUDA error";
     case PEXSI_ERR_BREAKDOWN: return "factorisation breakdown (zero or tiny pivot)";
     case PEXSI_ERR_INTERNAL: return "internal error";
+    case PEXSI_ERR_CANCELLED: return "request cancelled";
+    case PEXSI_PENDING: return "request pending";
     default: return "unknown error";
   }
 }
@@ -500,7 +587,7 @@ int pexsi_pole_table(double beta, double delta_e, int32_t n_poles, double mu, do
                      double* w_F) {
   if (!z) return PEXSI_ERR_INVALID_ARG;
   std::vector<std::complex<double>> zz, wr, we, wf;
-  int rc = pexsi::pole_table(beta, delta_e, n_poles, mu, zz, wr, we, wf);
+  int rc = pole_table(beta, delta_e, n_poles, mu, zz, wr, we, wf);
   if (rc) return rc;
   for (int l = 0; l < n_poles; ++l) {
     z[2 * l] = zz[l].real(); z[2 * l + 1] = zz[l].imag();
@@ -532,24 +619,29 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
     }
     p->b = p->opts.panel;
     std::string err;
-    int rc = pexsi::analyse(n, colptr, rowind, perm_or_null, p->opts.leaf_cols, p->opts.amalgamate != 0, p->sym, err);
+    int rc = analyse(n, colptr, rowind, perm_or_null, p->opts.leaf_cols, p->opts.amalgamate != 0, p->sym, err);
     if (rc) {
       delete p;
       return rc;
     }
-    p->flops = pexsi::count_flops(p->sym, p->b);
+    p->flops = count_flops(p->sym, p->b);
     if (p->opts.device < 0) {  // host-only plan: symbolic analysis only
       *out = p;
       return PEXSI_OK;
     }
     ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
-    ck(pexsi::configure_kernels(p->b), "cudaFuncSetAttribute");
-    const pexsi::Symbolic& S = p->sym;
+    ck(configure_kernels(p->b), "cudaFuncSetAttribute");
+    const Symbolic& S = p->sym;
     std::vector<int32_t> hs(S.nsuper), hm(S.nsuper);
     for (int32_t K = 0; K < S.nsuper; ++K) { hs[K] = S.s(K); hm[K] = S.m(K); }
     std::vector<int32_t> level_fronts, ea;
     std::vector<int64_t> part_off;
     build_levels(p, level_fronts, ea, part_off);
+    for (const Level& lv : p->levels)
+      if (lv.fronts.size() > 65535) {  // grid.y limit of the per-level launches
+        delete p;
+        return PEXSI_ERR_INTERNAL;
+      }
     std::vector<int64_t> asm_src, asm_pos;
     for (int64_t e = 0; e < S.nnz; ++e)
       if (S.entry_lower[e]) { asm_src.push_back(e); asm_pos.push_back(S.entry_pos[e]); }
@@ -566,25 +658,17 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
     p->d_level_fronts = dev_upload(level_fronts);
     p->d_ea = dev_upload(ea);
     p->d_part_off = dev_upload(part_off);
-    // S = I on the pattern: 1 where the entry is diagonal
     {
-      std::vector<double> ident(S.nnz, 0.0);
+      std::vector<double> ident(S.nnz, 0.0);  // S = I on the pattern
       for (int64_t j = 0; j < n; ++j)
         for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e)
           if (rowind[e] == j) ident[e] = 1.0;
       p->d_ident = dev_upload(ident);
     }
-    ck(cudaMalloc(&p->d_break, sizeof(int)), "cudaMalloc(status)");
-    ck(cudaMalloc(&p->d_minpiv, sizeof(unsigned long long)), "cudaMalloc(status)");
-    ck(cudaMalloc(&p->d_neg, sizeof(int) * pexsi::kMaxBatch), "cudaMalloc(status)");
-    ck(cudaMalloc(&p->d_partials, sizeof(double) * 3 * p->trace_blocks), "cudaMalloc(trace)");
-    ck(cudaMalloc(&p->d_trace3, sizeof(double) * 3), "cudaMalloc(trace)");
-    ck(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking), "cudaStreamCreate");
-    ck(cudaEventCreate(&p->ev0), "cudaEventCreate");
-    ck(cudaEventCreate(&p->ev1), "cudaEventCreate");
+    ck(cudaStreamCreateWithFlags(&p->ws.stream, cudaStreamNonBlocking), "cudaStreamCreate");
     *out = p;
     return PEXSI_OK;
-  } catch (const CudaError& ce) {
+  } catch (const CudaError&) {
     if (p) { free_plan_device(p); delete p; }
     return PEXSI_ERR_CUDA;
   } catch (const std::bad_alloc&) {
@@ -605,7 +689,7 @@ int pexsi_plan_destroy(pexsi_plan* p) {
 
 int pexsi_plan_get_stats(const pexsi_plan* p, pexsi_plan_stats* st) {
   if (!p || !st) return PEXSI_ERR_INVALID_ARG;
-  const pexsi::Symbolic& S = p->sym;
+  const Symbolic& S = p->sym;
   st->n = S.n;
   st->nnz = S.nnz;
   st->nsuper = S.nsuper;
@@ -618,14 +702,14 @@ int pexsi_plan_get_stats(const pexsi_plan* p, pexsi_plan_stats* st) {
   st->selinv_gemm_flops = p->flops.selinv_gemm;
   st->diag_flops = p->flops.diag;
   st->gather_bytes = p->flops.gather_bytes;
-  st->batch = p->batch;
-  st->workspace_bytes = int64_t(p->batch) * (2 * S.front_elems + p->part_stride) * int64_t(sizeof(double2));
+  st->batch = p->ws.batch;
+  st->workspace_bytes = p->ws.bytes;
   return PEXSI_OK;
 }
 
 int pexsi_plan_get_supernodes(const pexsi_plan* p, int32_t* first, int64_t* rptr, int32_t* rows, int32_t* parent) {
   if (!p || !first || !rptr || !parent) return PEXSI_ERR_INVALID_ARG;
-  const pexsi::Symbolic& S = p->sym;
+  const Symbolic& S = p->sym;
   std::memcpy(first, S.first.data(), sizeof(int32_t) * (S.nsuper + 1));
   std::memcpy(rptr, S.rptr.data(), sizeof(int64_t) * (S.nsuper + 1));
   std::memcpy(parent, S.parent.data(), sizeof(int32_t) * S.nsuper);
@@ -648,61 +732,14 @@ int pexsi_dm_device(pexsi_plan* p, const double* dH, const double* dS, double mu
     return fail(p, PEXSI_ERR_INVALID_ARG, "bad pole range");
   try {
     ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
-    std::vector<std::complex<double>> z, wr, we, wf;
-    int rc = pexsi::pole_table(beta, delta_e, n_poles, mu, z, wr, we, wf);
-    if (rc) return fail(p, rc, "bad pole-expansion parameters");
-    rc = ensure_workspace(p);
+    int rc = ensure_workspace(p);
     if (rc) return rc;
-    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : p->stream;
-    const double* S = dS ? dS : p->d_ident;
-    if (info) ck(cudaEventRecord(p->ev0, st), "event");
-    {
-      int big = INT_MAX;
-      unsigned long long inf = 0x7FF0000000000000ull;
-      ck(cudaMemcpyAsync(p->d_break, &big, sizeof(int), cudaMemcpyHostToDevice, st), "status");
-      ck(cudaMemcpyAsync(p->d_minpiv, &inf, sizeof(inf), cudaMemcpyHostToDevice, st), "status");
-    }
-    bool first = true;
-    for (int b0 = pole_begin; b0 < pole_end; b0 += p->batch) {
-      int nb = std::min(p->batch, pole_end - b0);
-      BatchShifts sh = make_shifts(z, &wr, &we, &wf, b0, nb);
-      run_complex_batch(p, dH, S, sh, st);
-      int overwrite = (first && !accumulate) ? 1 : 0;
-      cudaEvent_t a = p->prof.begin(st);
-      pexsi::launch_pole_sum(p->d_Y, p->sym.front_elems, p->d_entry_pos, p->sym.nnz, sh, overwrite, d_dm, d_edm, d_fdm,
-                             st);
-      int nout = (d_dm ? 1 : 0) + (d_edm ? 1 : 0) + (d_fdm ? 1 : 0);
-      p->prof.end(a, P_POLESUM, st, 6.0 * nout * nb * double(p->sym.nnz),
-                  double(p->sym.nnz) * (8.0 + 16.0 * nb + 8.0 * nout * (overwrite ? 1 : 2)));
-      first = false;
-    }
-    ck(cudaGetLastError(), "pole sum");
-    if (info) {
-      std::memset(info, 0, sizeof(*info));
-      cudaEvent_t a = p->prof.begin(st);
-      pexsi::launch_traces(d_dm, d_edm, d_fdm, S, p->sym.nnz, p->d_partials, p->trace_blocks, p->d_trace3, st);
-      p->prof.end(a, P_TRACE, st, 6.0 * double(p->sym.nnz), 32.0 * double(p->sym.nnz));
-      ck(cudaEventRecord(p->ev1, st), "event");
-      double tr[3] = {0, 0, 0};
-      int brk = INT_MAX;
-      unsigned long long mp = 0;
-      ck(cudaMemcpyAsync(tr, p->d_trace3, sizeof(tr), cudaMemcpyDeviceToHost, st), "trace");
-      ck(cudaMemcpyAsync(&brk, p->d_break, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
-      ck(cudaMemcpyAsync(&mp, p->d_minpiv, sizeof(mp), cudaMemcpyDeviceToHost, st), "status");
-      ck(cudaStreamSynchronize(st), "sync");
-      float ms = 0;
-      ck(cudaEventElapsedTime(&ms, p->ev0, p->ev1), "event");
-      info->trace_dm_s = d_dm ? tr[0] : 0.0;
-      info->trace_edm_s = d_edm ? tr[1] : 0.0;
-      info->trace_fdm_s = d_fdm ? tr[2] : 0.0;
-      std::memcpy(&info->min_pivot_ratio, &mp, sizeof(double));
-      info->ms_total = ms;
-      info->gemm_flops = (p->flops.factor_gemm + p->flops.selinv_gemm) * (pole_end - pole_begin);
-      info->n_poles = pole_end - pole_begin;
-      info->breakdown_front = brk == INT_MAX ? -1 : brk;
-      if (brk != INT_MAX) return fail(p, PEXSI_ERR_BREAKDOWN, "zero or tiny pivot in front " + std::to_string(brk));
-    }
-    return PEXSI_OK;
+    std::string err;
+    rc = on_stream(p, stream, [&] {
+      return dm_range(p, p->ws, &p->prof, dH, dS, mu, beta, n_poles, delta_e, pole_begin, pole_end, accumulate, d_dm,
+                      d_edm, d_fdm, info, &err);
+    });
+    return rc ? fail(p, rc, err) : PEXSI_OK;
   } catch (const CudaError& ce) {
     return map_cuda(p, ce);
   } catch (const std::bad_alloc&) {
@@ -720,31 +757,32 @@ int pexsi_dm_poles(pexsi_plan* p, const double* H, const double* S, double mu, d
                    double* fdm, pexsi_dm_info* info) {
   if (p && p->opts.device < 0) return fail(p, PEXSI_ERR_INVALID_ARG, "host-only plan has no device");
   if (!p || !H) return fail(p, PEXSI_ERR_INVALID_ARG, "NULL plan or H");
+  if (pole_begin < 0 || pole_end > n_poles || pole_begin >= pole_end)
+    return fail(p, PEXSI_ERR_INVALID_ARG, "bad pole range");
   try {
     ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
     int rc = ensure_workspace(p);
     if (rc) return rc;
+    Workspace& ws = p->ws;
     const size_t nnz = size_t(p->sym.nnz);
-    ck(cudaMemcpyAsync(p->d_H, H, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->stream), "H2D(H)");
-    if (S) ck(cudaMemcpyAsync(p->d_S, S, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->stream), "H2D(S)");
-    pexsi_dm_info local;
+    double *o_dm = ws.out, *o_edm = ws.out + nnz, *o_fdm = ws.out + 2 * nnz;
+    ck(cudaMemcpyAsync(ws.H, H, sizeof(double) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(H)");
+    if (S) ck(cudaMemcpyAsync(ws.S, S, sizeof(double) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(S)");
     if (accumulate) {
-      if (dm) ck(cudaMemcpyAsync(p->d_dm, dm, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->stream), "H2D(dm)");
-      if (edm) ck(cudaMemcpyAsync(p->d_edm, edm, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->stream), "H2D(edm)");
-      if (fdm) ck(cudaMemcpyAsync(p->d_fdm, fdm, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->stream), "H2D(fdm)");
+      if (dm) ck(cudaMemcpyAsync(o_dm, dm, sizeof(double) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(dm)");
+      if (edm) ck(cudaMemcpyAsync(o_edm, edm, sizeof(double) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(edm)");
+      if (fdm) ck(cudaMemcpyAsync(o_fdm, fdm, sizeof(double) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(fdm)");
     }
-    rc = pexsi_dm_device(p, p->d_H, S ? p->d_S : nullptr, mu, beta, n_poles, delta_e, pole_begin, pole_end,
-                         accumulate, dm ? p->d_dm : nullptr, edm ? p->d_edm : nullptr, fdm ? p->d_fdm : nullptr,
-                         p->stream, &local);
-    if (rc) {
-      if (info) *info = local;
-      return rc;
-    }
-    if (dm) ck(cudaMemcpyAsync(dm, p->d_dm, sizeof(double) * nnz, cudaMemcpyDeviceToHost, p->stream), "D2H(dm)");
-    if (edm) ck(cudaMemcpyAsync(edm, p->d_edm, sizeof(double) * nnz, cudaMemcpyDeviceToHost, p->stream), "D2H(edm)");
-    if (fdm) ck(cudaMemcpyAsync(fdm, p->d_fdm, sizeof(double) * nnz, cudaMemcpyDeviceToHost, p->stream), "D2H(fdm)");
-    ck(cudaStreamSynchronize(p->stream), "sync");
+    pexsi_dm_info local;
+    std::string err;
+    rc = dm_range(p, ws, &p->prof, ws.H, S ? ws.S : nullptr, mu, beta, n_poles, delta_e, pole_begin, pole_end,
+                  accumulate, dm ? o_dm : nullptr, edm ? o_edm : nullptr, fdm ? o_fdm : nullptr, &local, &err);
     if (info) *info = local;
+    if (rc) return fail(p, rc, err);
+    if (dm) ck(cudaMemcpyAsync(dm, o_dm, sizeof(double) * nnz, cudaMemcpyDeviceToHost, ws.stream), "D2H(dm)");
+    if (edm) ck(cudaMemcpyAsync(edm, o_edm, sizeof(double) * nnz, cudaMemcpyDeviceToHost, ws.stream), "D2H(edm)");
+    if (fdm) ck(cudaMemcpyAsync(fdm, o_fdm, sizeof(double) * nnz, cudaMemcpyDeviceToHost, ws.stream), "D2H(fdm)");
+    ck(cudaStreamSynchronize(ws.stream), "sync");
     return PEXSI_OK;
   } catch (const CudaError& ce) {
     return map_cuda(p, ce);
@@ -759,19 +797,16 @@ int pexsi_selinv(pexsi_plan* p, const double* H, const double* S, double z_re, d
     ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
     int rc = ensure_workspace(p);
     if (rc) return rc;
+    Workspace& ws = p->ws;
     const size_t nnz = size_t(p->sym.nnz);
-    cudaStream_t st = p->stream;
-    ck(cudaMemcpyAsync(p->d_H, H, sizeof(double) * nnz, cudaMemcpyHostToDevice, st), "H2D(H)");
-    if (S) ck(cudaMemcpyAsync(p->d_S, S, sizeof(double) * nnz, cudaMemcpyHostToDevice, st), "H2D(S)");
-    std::vector<std::complex<double>> z{{z_re, z_im}};
-    BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, 0, 1);
-    reset_status(p);
-    run_complex_batch(p, p->d_H, S ? p->d_S : p->d_ident, sh, st);
-    if (!p->d_ainv) ck(cudaMalloc(&p->d_ainv, sizeof(double2) * nnz), "cudaMalloc(ainv)");
-    pexsi::launch_extract(p->d_Y, p->d_entry_pos, p->sym.nnz, p->d_ainv, st);
-    ck(cudaGetLastError(), "extract");
-    ck(cudaMemcpyAsync(ainv, p->d_ainv, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, st), "D2H(ainv)");
-    return check_breakdown(p, nullptr);
+    ck(cudaMemcpyAsync(ws.H, H, sizeof(double) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(H)");
+    if (S) ck(cudaMemcpyAsync(ws.S, S, sizeof(double) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(S)");
+    if (!ws.ainv) ck(cudaMalloc(&ws.ainv, sizeof(double2) * nnz), "cudaMalloc(ainv)");
+    std::string err;
+    rc = selinv_one(p, ws, ws.H, S ? ws.S : nullptr, z_re, z_im, ws.ainv, &err);
+    if (rc) return fail(p, rc, err);
+    ck(cudaMemcpy(ainv, ws.ainv, sizeof(double2) * nnz, cudaMemcpyDeviceToHost), "D2H(ainv)");
+    return PEXSI_OK;
   } catch (const CudaError& ce) {
     return map_cuda(p, ce);
   }
@@ -785,39 +820,9 @@ int pexsi_inertia_device(pexsi_plan* p, const double* dH, const double* dS, cons
     ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
     int rc = ensure_workspace(p);
     if (rc) return rc;
-    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : p->stream;
-    const double* S = dS ? dS : p->d_ident;
-    const int64_t pool = p->sym.front_elems;
-    // real fronts: the complex pool holds twice as many real ones
-    const int cap = std::min(pexsi::kMaxBatch, 2 * p->batch);
-    double* F = reinterpret_cast<double*>(p->d_F);
-    std::vector<std::complex<double>> z(n_shifts);
-    for (int t = 0; t < n_shifts; ++t) z[t] = {shifts[t], 0.0};
-    int brk_all = INT_MAX;
-    for (int b0 = 0; b0 < n_shifts; b0 += cap) {
-      int nb = std::min(cap, n_shifts - b0);
-      BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, b0, nb);
-      int big = INT_MAX;
-      ck(cudaMemcpyAsync(p->d_break, &big, sizeof(int), cudaMemcpyHostToDevice, st), "status");
-      ck(cudaMemsetAsync(p->d_neg, 0, sizeof(int) * pexsi::kMaxBatch, st), "status");
-      unsigned long long inf = 0x7FF0000000000000ull;
-      ck(cudaMemcpyAsync(p->d_minpiv, &inf, sizeof(inf), cudaMemcpyHostToDevice, st), "status");
-      ck(cudaMemsetAsync(F, 0, sizeof(double) * size_t(pool) * nb, st), "memset(F)");
-      cudaEvent_t a = p->prof.begin(st);
-      pexsi::launch_assemble<double>(F, dH, S, p->d_asm_src, p->d_asm_pos, p->nlow, pool, sh, st);
-      p->prof.end(a, P_ASSEMBLE, st, 0.0, double(p->nlow) * (32.0 + 8.0 * nb));
-      factor_batch<double>(p, F, sh, true, st);
-      int neg[pexsi::kMaxBatch];
-      int brk = INT_MAX;
-      ck(cudaMemcpyAsync(neg, p->d_neg, sizeof(int) * nb, cudaMemcpyDeviceToHost, st), "D2H(counts)");
-      ck(cudaMemcpyAsync(&brk, p->d_break, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
-      ck(cudaStreamSynchronize(st), "sync");
-      for (int t = 0; t < nb; ++t) counts[b0 + t] = neg[t];
-      brk_all = std::min(brk_all, brk);
-    }
-    if (brk_all != INT_MAX)
-      return fail(p, PEXSI_ERR_BREAKDOWN, "zero or tiny pivot in front " + std::to_string(brk_all));
-    return PEXSI_OK;
+    std::string err;
+    rc = on_stream(p, stream, [&] { return inertia_range(p, p->ws, &p->prof, dH, dS, shifts, n_shifts, counts, &err); });
+    return rc ? fail(p, rc, err) : PEXSI_OK;
   } catch (const CudaError& ce) {
     return map_cuda(p, ce);
   }
@@ -832,9 +837,9 @@ int pexsi_inertia(pexsi_plan* p, const double* H, const double* S, const double*
     int rc = ensure_workspace(p);
     if (rc) return rc;
     const size_t nnz = size_t(p->sym.nnz);
-    ck(cudaMemcpyAsync(p->d_H, H, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->stream), "H2D(H)");
-    if (S) ck(cudaMemcpyAsync(p->d_S, S, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->stream), "H2D(S)");
-    return pexsi_inertia_device(p, p->d_H, S ? p->d_S : nullptr, shifts, n_shifts, counts, p->stream);
+    ck(cudaMemcpyAsync(p->ws.H, H, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->ws.stream), "H2D(H)");
+    if (S) ck(cudaMemcpyAsync(p->ws.S, S, sizeof(double) * nnz, cudaMemcpyHostToDevice, p->ws.stream), "H2D(S)");
+    return pexsi_inertia_device(p, p->ws.H, S ? p->ws.S : nullptr, shifts, n_shifts, counts, p->ws.stream);
   } catch (const CudaError& ce) {
     return map_cuda(p, ce);
   }

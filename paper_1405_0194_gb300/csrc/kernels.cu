@@ -650,20 +650,22 @@ __global__ void k_selinv_diag_reduce(double2* __restrict__ Y, const double2* __r
 // ------------------------------------------------------------ pole sum
 __global__ void k_pole_sum(const double2* __restrict__ Y, int64_t pool, const int64_t* __restrict__ entry_pos,
                            int64_t nnz, BatchShifts sh, int overwrite, double* __restrict__ dm,
-                           double* __restrict__ edm, double* __restrict__ fdm) {
+                           double* __restrict__ edm, double* __restrict__ fdm, double* __restrict__ ddm) {
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t p = entry_pos[e];
-    double a = 0.0, ae = 0.0, af = 0.0;
+    double a = 0.0, ae = 0.0, af = 0.0, ad = 0.0;
     for (int b = 0; b < sh.nb; ++b) {
       double2 v = Y[b * pool + p];
       // Im(w v) = w.re v.im + w.im v.re
       a = fma(sh.wr_re[b], v.y, fma(sh.wr_im[b], v.x, a));
       ae = fma(sh.we_re[b], v.y, fma(sh.we_im[b], v.x, ae));
       af = fma(sh.wf_re[b], v.y, fma(sh.wf_im[b], v.x, af));
+      ad = fma(sh.wd_re[b], v.y, fma(sh.wd_im[b], v.x, ad));
     }
     if (dm) dm[e] = overwrite ? a : dm[e] + a;
     if (edm) edm[e] = overwrite ? ae : edm[e] + ae;
     if (fdm) fdm[e] = overwrite ? af : fdm[e] + af;
+    if (ddm) ddm[e] = overwrite ? ad : ddm[e] + ad;
   }
 }
 
@@ -673,34 +675,41 @@ __global__ void k_extract(const double2* __restrict__ Y, const int64_t* __restri
     out[e] = Y[entry_pos[e]];
 }
 
-__global__ void k_trace_partial(const double* dm, const double* edm, const double* fdm, const double* __restrict__ S,
-                                int64_t nnz, double* partials) {
-  __shared__ double red[3][256];
+__global__ void k_scaled_imag(const double2* __restrict__ Y, const int64_t* __restrict__ entry_pos, int64_t nnz,
+                              double scale, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x)
+    out[e] = scale * Y[entry_pos[e]].y;
+}
+
+__global__ void k_trace_partial(const double* dm, const double* edm, const double* fdm, const double* ddm,
+                                const double* __restrict__ S, int64_t nnz, double* partials) {
+  __shared__ double red[4][256];
   const int64_t chunk = (nnz + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk, hi = min(nnz, lo + chunk);
-  double a = 0, b = 0, c = 0;
+  double a = 0, b = 0, c = 0, d = 0;
   for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
     double sv = S[e];
     if (dm) a = fma(dm[e], sv, a);
     if (edm) b = fma(edm[e], sv, b);
     if (fdm) c = fma(fdm[e], sv, c);
+    if (ddm) d = fma(ddm[e], sv, d);
   }
-  red[0][threadIdx.x] = a; red[1][threadIdx.x] = b; red[2][threadIdx.x] = c;
+  red[0][threadIdx.x] = a; red[1][threadIdx.x] = b; red[2][threadIdx.x] = c; red[3][threadIdx.x] = d;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (int(threadIdx.x) < w)
-      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int q = 0; q < 3; ++q) partials[3 * blockIdx.x + q] = red[q][0];
+    for (int q = 0; q < 4; ++q) partials[4 * blockIdx.x + q] = red[q][0];
 }
 
-__global__ void k_trace_final(const double* partials, int nblocks, double* out3) {
-  if (threadIdx.x < 3) {
+__global__ void k_trace_final(const double* partials, int nblocks, double* out4) {
+  if (threadIdx.x < 4) {
     double s = 0;
-    for (int t = 0; t < nblocks; ++t) s += partials[3 * t + threadIdx.x];
-    out3[threadIdx.x] = s;
+    for (int t = 0; t < nblocks; ++t) s += partials[4 * t + threadIdx.x];
+    out4[threadIdx.x] = s;
   }
 }
 
@@ -782,18 +791,23 @@ void launch_selinv_diag_reduce(double2* Y, const double2* F, const double2* part
 }
 
 void launch_pole_sum(const double2* Y, int64_t pool, const int64_t* entry_pos, int64_t nnz, const BatchShifts& sh,
-                     int overwrite, double* dm, double* edm, double* fdm, cudaStream_t st) {
-  k_pole_sum<<<grid_for(nnz, 256), 256, 0, st>>>(Y, pool, entry_pos, nnz, sh, overwrite, dm, edm, fdm);
+                     int overwrite, double* dm, double* edm, double* fdm, double* ddm, cudaStream_t st) {
+  k_pole_sum<<<grid_for(nnz, 256), 256, 0, st>>>(Y, pool, entry_pos, nnz, sh, overwrite, dm, edm, fdm, ddm);
 }
 
 void launch_extract(const double2* Y, const int64_t* entry_pos, int64_t nnz, double2* out, cudaStream_t st) {
   k_extract<<<grid_for(nnz, 256), 256, 0, st>>>(Y, entry_pos, nnz, out);
 }
 
-void launch_traces(const double* dm, const double* edm, const double* fdm, const double* S, int64_t nnz,
-                   double* partials, int nblocks, double* out3, cudaStream_t st) {
-  k_trace_partial<<<nblocks, 256, 0, st>>>(dm, edm, fdm, S, nnz, partials);
-  k_trace_final<<<1, 32, 0, st>>>(partials, nblocks, out3);
+void launch_scaled_imag(const double2* Y, const int64_t* entry_pos, int64_t nnz, double scale, double* out,
+                        cudaStream_t st) {
+  k_scaled_imag<<<grid_for(nnz, 256), 256, 0, st>>>(Y, entry_pos, nnz, scale, out);
+}
+
+void launch_traces(const double* dm, const double* edm, const double* fdm, const double* ddm, const double* S,
+                   int64_t nnz, double* partials, int nblocks, double* out4, cudaStream_t st) {
+  k_trace_partial<<<nblocks, 256, 0, st>>>(dm, edm, fdm, ddm, S, nnz, partials);
+  k_trace_final<<<1, 32, 0, st>>>(partials, nblocks, out4);
 }
 
 cudaError_t configure_kernels(int b) {

@@ -18,6 +18,7 @@ struct BatchShifts {
   double wr_re[kMaxBatch], wr_im[kMaxBatch];  // w^rho
   double we_re[kMaxBatch], we_im[kMaxBatch];  // w^E
   double wf_re[kMaxBatch], wf_im[kMaxBatch];  // w^F
+  double wd_re[kMaxBatch], wd_im[kMaxBatch];  // w^d (mu-derivative of the Fermi function)
 };
 
 // Front geometry on the device.
@@ -74,16 +75,20 @@ void launch_selinv_diag_reduce(double2* Y, const double2* F, const double2* part
                                int b, const BatchShifts& sh, cudaStream_t st);
 
 void launch_pole_sum(const double2* Y, int64_t pool, const int64_t* entry_pos, int64_t nnz, const BatchShifts& sh,
-                     int overwrite, double* dm, double* edm, double* fdm, cudaStream_t st);
+                     int overwrite, double* dm, double* edm, double* fdm, double* ddm, cudaStream_t st);
 
 void launch_extract(const double2* Y, const int64_t* entry_pos, int64_t nnz, double2* out, cudaStream_t st);
+
+// out[e] = scale * Im Y[entry_pos[e]] (the LDOS matrix from one selected inverse).
+void launch_scaled_imag(const double2* Y, const int64_t* entry_pos, int64_t nnz, double scale, double* out,
+                        cudaStream_t st);
 
 // Raises the dynamic shared-memory limits the kernels need for panel width b.
 cudaError_t configure_kernels(int b);
 
-// Deterministic Tr[X S] for up to three X (NULL entries skipped): partial sums
-// of fixed ranges in `partials` (3 * nblocks doubles), then one ordered sum.
-void launch_traces(const double* dm, const double* edm, const double* fdm, const double* S, int64_t nnz,
-                   double* partials, int nblocks, double* out3, cudaStream_t st);
+// Deterministic Tr[X S] for up to four X (NULL entries give 0): partial sums
+// of fixed ranges in `partials` (4 * nblocks doubles), then one ordered sum.
+void launch_traces(const double* dm, const double* edm, const double* fdm, const double* ddm, const double* S,
+                   int64_t nnz, double* partials, int nblocks, double* out4, cudaStream_t st);
 
 }  // namespace pexsi

@@ -1,0 +1,157 @@
+// Internal definitions shared by the plan API (engine.cu) and the request
+// server (server.cu): the device plan, per-computation workspaces and the
+// batched numeric drivers.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pexsi_gb300.h"
+#include "kernels.cuh"
+#include "symbolic.hpp"
+
+namespace pexsi {
+
+int pole_table(double beta, double delta_e, int P, double mu, std::vector<std::complex<double>>& z,
+               std::vector<std::complex<double>>& w_rho, std::vector<std::complex<double>>& w_E,
+               std::vector<std::complex<double>>& w_F, std::vector<std::complex<double>>* w_d = nullptr);
+
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw CudaError{e, what};
+}
+
+// Host-side launch geometry of one level of the supernodal tree: fronts sorted
+// by width descending, so the fronts still active at panel offset p0 (s > p0)
+// are a prefix.
+struct Level {
+  int64_t front_off = 0;  // into the device list of level fronts
+  std::vector<int32_t> fronts, s, m;
+  std::vector<int64_t> ea_off;   // extend-add groups: rank k = k-th child of each parent
+  std::vector<int32_t> ea_count, ea_tiles;
+  std::vector<double> ea_elems;  // elements moved by each extend-add launch
+  int64_t gather_tiles = 0;
+  double gather_bytes = 0;
+  int32_t max_s = 0;
+};
+
+// CUDA-event bracketing of kernel launches, per launch class.
+struct Profiler {
+  bool on = false;
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+    double flops, bytes;
+    int kernels;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[PEXSI_PROFILE_CLASSES] = {};
+  double ms[PEXSI_PROFILE_CLASSES] = {}, flops[PEXSI_PROFILE_CLASSES] = {}, bytes[PEXSI_PROFILE_CLASSES] = {};
+  cudaEvent_t begin(cudaStream_t st);
+  void end(cudaEvent_t a, int cls, cudaStream_t st, double fl, double by, int kernels = 1);
+  void drain();
+  void reset();
+  void destroy();
+};
+
+enum ProfClass { P_ASSEMBLE, P_EXTEND, P_DIAG, P_PANEL, P_SCHUR, P_GATHER, P_OFFDIAG, P_DPART, P_DRED, P_POLESUM, P_TRACE };
+
+// Device buffers of one in-flight computation: fronts for `batch` poles (or
+// 2 x batch real shifts), split-K partials, status words, trace scratch, and
+// staging for host-buffer calls; plus the stream the work runs on.
+struct Workspace {
+  int batch = 0;
+  double2 *F = nullptr, *Y = nullptr, *part = nullptr;
+  int* brk = nullptr;
+  unsigned long long* minpiv = nullptr;
+  int* neg = nullptr;
+  double* partials = nullptr;
+  double* trace3 = nullptr;
+  double *H = nullptr, *S = nullptr, *out = nullptr;  // nnz, nnz, 4 nnz (DM, EDM, FDM, Gamma^d)
+  double2* ainv = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool async = false;  // buffers from cudaMallocAsync on `stream`
+  int64_t bytes = 0;
+};
+
+}  // namespace pexsi
+
+struct pexsi_plan {
+  pexsi::Symbolic sym;
+  pexsi_opts opts{};
+  std::string last_error;
+  int b = 64;
+  int64_t* d_front_off = nullptr;
+  int32_t *d_s = nullptr, *d_m = nullptr, *d_parent = nullptr, *d_rel = nullptr;
+  int64_t* d_rptr = nullptr;
+  int64_t *d_asm_src = nullptr, *d_asm_pos = nullptr;
+  int64_t nlow = 0;
+  int64_t* d_entry_pos = nullptr;
+  int32_t* d_level_fronts = nullptr;
+  int32_t* d_ea = nullptr;
+  int64_t* d_part_off = nullptr;
+  int64_t part_stride = 0;  // partial-scratch elements per batch member
+  double* d_ident = nullptr;
+  std::vector<pexsi::Level> levels;
+  pexsi::FlopCounts flops;
+  int trace_blocks = 256;
+  pexsi::Profiler prof;
+  pexsi::Workspace ws;  // the plan's own workspace (plan API calls)
+
+  pexsi::DevFronts fronts() const {
+    pexsi::DevFronts f;
+    f.off = d_front_off;
+    f.s = d_s;
+    f.m = d_m;
+    f.parent = d_parent;
+    f.rptr = d_rptr;
+    f.rel = d_rel;
+    f.pool = sym.front_elems;
+    return f;
+  }
+};
+
+namespace pexsi {
+
+// Bytes of workspace one pole adds (F and Y fronts + partials).
+int64_t bytes_per_pole(const pexsi_plan* p);
+// Fixed bytes of a workspace (staging + status + trace scratch).
+int64_t bytes_fixed(const pexsi_plan* p);
+
+// Allocates ws for `batch` poles on `stream` (cudaMallocAsync when async).
+void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t stream, bool async);
+void workspace_free(Workspace& ws);
+
+// Poles [begin, end) of the P-pole table into d_dm/d_edm/d_fdm (device, any
+// may be NULL), accumulating when `accumulate`; traces and status into info
+// when info != NULL (synchronises ws.stream). Returns a PEXSI code; message
+// in *err.
+// Gamma^d (for N'(mu), Sec. II.C) accumulates into ws.out + 3 nnz with the
+// same `accumulate` rule, and its trace goes to info->trace_ddm_s.
+int dm_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* dH, const double* dS, double mu,
+             double beta, int P, double delta_e, int begin, int end, int accumulate, double* d_dm, double* d_edm,
+             double* d_fdm, pexsi_dm_info* info, std::string* err);
+
+// Inertia counts of H - shifts[m] S (host shifts and counts); synchronises.
+int inertia_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* dH, const double* dS,
+                  const double* shifts, int n_shifts, int64_t* counts, std::string* err);
+
+// The plan's own workspace (created on first use); PEXSI code.
+int plan_workspace(pexsi_plan* p);
+
+// Selected inverse of one complex shift into d_ainv (device, nnz complex);
+// synchronises ws.stream.
+int selinv_one(const pexsi_plan* p, Workspace& ws, const double* dH, const double* dS, double z_re, double z_im,
+               double2* d_ainv, std::string* err);
+
+}  // namespace pexsi

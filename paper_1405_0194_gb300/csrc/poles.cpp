@@ -99,10 +99,17 @@ cd grand(cd x, double beta) {
   return -(2.0 / beta) * l;
 }
 
+// d/dmu of f(eps - mu) at x = eps - mu: (beta/2) f (2 - f); its weights give
+// Gamma^d, whose trace with S is N'(mu) (Sec. II.C).
+cd dfermi(cd x, double beta) {
+  cd f = fermi(x, beta);
+  return 0.5 * beta * f * (2.0 - f);
+}
+
 }  // namespace
 
 int pole_table(double beta, double delta_e, int P, double mu, std::vector<cd>& z, std::vector<cd>& w_rho,
-               std::vector<cd>& w_E, std::vector<cd>& w_F) {
+               std::vector<cd>& w_E, std::vector<cd>& w_F, std::vector<cd>* w_d) {
   if (!(beta > 0) || !(delta_e > 0) || P < 2 || (P & 1)) return PEXSI_ERR_INVALID_ARG;
   const int N = P;
   const double m = (kPi / beta) * (kPi / beta);
@@ -129,6 +136,7 @@ int pole_table(double beta, double delta_e, int P, double mu, std::vector<cd>& z
     cs[j] = -h * dxi / (cd(0.0, 4.0 * kPi) * x);
   }
   z.clear(); w_rho.clear(); w_E.clear(); w_F.clear();
+  if (w_d) w_d->clear();
   // poles at +x_j (residue -c_j F(x_j)) then at -x_j (residue +c_j F(-x_j));
   // keep the upper half-plane member of each conjugate pair, weight 2 i r
   for (int side = 0; side < 2; ++side) {
@@ -142,6 +150,7 @@ int pole_table(double beta, double delta_e, int P, double mu, std::vector<cd>& z
       w_rho.push_back(two_i * sgn * cs[j] * f);
       w_E.push_back(two_i * sgn * cs[j] * (y + mu) * f);
       w_F.push_back(two_i * sgn * cs[j] * grand(y, beta));
+      if (w_d) w_d->push_back(two_i * sgn * cs[j] * dfermi(y, beta));
     }
   }
   if (int(z.size()) != P) return PEXSI_ERR_INTERNAL;
