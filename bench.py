@@ -15,6 +15,12 @@ with H and S resident on the device; e2e = the same through the host-buffer
 call (H, S copied in and DM/EDM/FDM copied out every step, from pinned host
 memory).
 
+By default (--split 6) the two large complex supernode GEMMs (the Schur
+update and the Takahashi step) run as exact 6-slice bf16 products on the
+tcgen05 tensor cores with FP64 in and out; everything else is FP64. The
+plain FP64 path is timed after it on the same workload ("fp64_path"), with
+the largest difference between the two on one identical pole batch.
+
 With --impl reference the CPU oracle is timed instead on the same workload
 (a bounded sample per step: the dense LU of one shifted matrix plus a
 sample of its columns, extrapolated to one full pole-solve).
@@ -122,6 +128,86 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def roofline_of(dom: dict, total_kernel_ms: float, peaks: dict, split: int) -> dict:
+    """Roofline entry of the dominant launch class. A class that runs on the
+    tensor cores (the split-precision GEMMs) is measured by the bf16 flops its
+    MMAs execute against the measured sustained bf16 peak (the class is timed
+    inside a seconds-long step); an FP64 class by its algorithmic flops against
+    the FP64 DFMA peak (no measured FP64 peak exists)."""
+    secs = dom["ms"] / 1e3
+    r = {"kernel": dom["name"], "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(1, dom["launches"]),
+         "time_share": dom["ms"] / total_kernel_ms if total_kernel_ms else None}
+    if dom.get("tensor_flops", 0) > 0 and secs > 0:
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        ach = dom["tensor_flops"] / secs / 1e12
+        r.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                  "peak_source": "bf16_tflops_sustained of MEASURED_PEAKS.json (of measured)",
+                  "fp64_equivalent_tflops": dom["flops"] / secs / 1e12,
+                  "note": f"achieved = bf16 flops the tcgen05 MMAs execute: {split * (split + 1) // 2} slice pairs "
+                          "x 4 real products x 2 flops per complex multiply-add; fp64_equivalent_tflops counts "
+                          "8 flops per complex multiply-add of the FP64 product it replaces"})
+    else:
+        ach = dom["flops"] / secs / 1e12 if secs > 0 else 0.0
+        r.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": ach / FP64_PEAK_TFLOPS,
+                  "peak_source": "derived: FP64 DFMA 2/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                  "executed_frac": ach * 6.0 / 8.0 / FP64_PEAK_TFLOPS,
+                  "note": "achieved counts 8 real flops per complex multiply-add; the tiles execute 3 DFMA "
+                          "(6 flops) per complex multiply-add (Gauss form), executed_frac is their DFMA rate"})
+    return r
+
+
+def gemm_rate(kernels: dict) -> dict:
+    """FP64-equivalent rate of the four supernode GEMM classes together (and
+    the split-precision slicing that feeds them, when present)."""
+    names = ["panel_solve", "schur_update", "selinv_offdiag", "selinv_diag_partial", "split_slice"]
+    ks = [kernels[k] for k in names if k in kernels]
+    ms = sum(k["ms"] for k in ks)
+    tf = sum(k["flops"] for k in ks) / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    return {"fp64_equivalent_tflops": tf, "fp64_peak_tflops": FP64_PEAK_TFLOPS, "vs_fp64_peak": tf / FP64_PEAK_TFLOPS}
+
+
+def fp64_path(px, s, mu, dE, device, dH, dS, stream, args, B, Q, all_shifts, split_dm):
+    """The plain FP64 path on the same workload and step (fewer timed steps),
+    and the split path's deviation from it on one identical pole batch."""
+    import torch
+    P = s.n_poles
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind,
+                          opts=px.pexsi_opts_default(device=device, max_batch=B, split_slices=0))
+    o = torch.zeros(3, s.nnz, dtype=torch.float64, device=dH.device)
+    px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, 0, B, 0,
+                       o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
+    ref = o.cpu().numpy()
+    px.pexsi_profile_reset(plan)
+    px.pexsi_profile_enable(plan, True)
+    torch.cuda.synchronize(dH.device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.fp64_steps):
+        b0 = ((1 + i) * B) % P
+        px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, b0, min(P, b0 + B), 1,
+                           o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
+        sh = all_shifts[(i * Q) % 16:(i * Q) % 16 + Q]
+        px.pexsi_inertia_device(plan, dH.data_ptr(), dS.data_ptr(), sh, stream)
+    e1.record()
+    torch.cuda.synchronize(dH.device)
+    ms = e0.elapsed_time(e1)
+    prof = px.pexsi_profile_read(plan)
+    px.pexsi_plan_destroy(plan)
+    kern = {p["name"]: p for p in prof}
+    dom = max(prof, key=lambda p: p["ms"])
+    scale = [float(np.max(np.abs(ref[k]))) for k in range(3)]
+    dev = [float(np.max(np.abs(ref[k] - split_dm[k]))) for k in range(3)]
+    return {"value": B * args.fp64_steps / (ms / 1e3), "unit": "pole-solves/s", "steps": args.fp64_steps,
+            "ms_per_step": ms / args.fp64_steps, "dominant": roofline_of(dom, sum(p["ms"] for p in prof), {}, 0),
+            "gemm_rate": gemm_rate(kern),
+            "split_vs_fp64_same_batch": {"max_abs": {"dm": dev[0], "edm": dev[1], "fdm": dev[2]},
+                                         "max_abs_over_max_entry": {"dm": dev[0] / scale[0], "edm": dev[1] / scale[1],
+                                                                    "fdm": dev[2] / scale[2]},
+                                         "batch": f"poles 0..{B - 1}"}}
+
+
 def prepare(workload: str, seed: int):
     w = WORKLOADS[workload]
     s = w["make"](seed)
@@ -192,7 +278,8 @@ def run_ours(args):
     s, mu, dE = prepare(args.workload, args.seed)
     P = s.n_poles
     plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=local,
-                                                                              max_batch=args.poles_per_step))
+                                                                              max_batch=args.poles_per_step,
+                                                                              split_slices=args.split))
     st = px.pexsi_plan_get_stats(plan)
     dev = torch.device("cuda", local)
     dH = torch.from_numpy(s.H).to(dev)
@@ -276,40 +363,45 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (live CUDA-event timings)
+    # ---- roofline of the dominant launch class (live CUDA-event timings)
     kernels = {p["name"]: p for p in prof}
     dom = max(prof, key=lambda p: p["ms"])
     launches = sum(p["launches"] for p in prof) + kernels["trace"]["launches"]  # trace = 2 kernels
-    achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12 if dom["ms"] > 0 else 0.0
-    gemm = [kernels[k] for k in ("panel_solve", "schur_update", "selinv_offdiag", "selinv_diag_partial")]
-    gemm_tf = sum(k["flops"] for k in gemm) / (sum(k["ms"] for k in gemm) / 1e3) / 1e12
     total_kernel_ms = sum(p["ms"] for p in prof)
     peaks, peak_src = load_peaks()
-    traffic = None
+    roofline = roofline_of(dom, total_kernel_ms, peaks, args.split)
+    roofline["traffic"] = None
     tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
-        if tj.get("kernel") == dom["name"]:
-            traffic = tj.get("dram_bytes_per_launch")
+        if tj.get("kernel") == dom["name"] and tj.get("split_slices", 0) == args.split:
+            roofline["traffic"] = tj.get("dram_bytes_per_launch")
+
+    # split-precision result against the FP64 path on one identical pole batch
+    split_dm = None
+    if args.split and args.fp64_steps > 0:
+        o = torch.zeros(3, s.nnz, dtype=torch.float64, device=dev)
+        px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, 0, B, 0,
+                           o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
+        split_dm = o.cpu().numpy()
+        del o
 
     line = {
         "metric": "pole-solves/sec", "value": value, "unit": "pole-solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload]["desc"], "poles_per_step": B,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": (f"f64 in/out; supernode GEMMs as bf16x{args.split} slices on tcgen05 (exact fp32 / int64 "
+                  f"accumulation)" if args.split else "f64"),
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "poles_per_step": B, "split_slices": args.split,
                    "inertia_shifts_per_step": Q, "seed": args.seed, "ordering": "own nested dissection",
                    "nsuper": st["nsuper"], "nnz_L": st["nnz_L"],
                    "gemm_flops_per_pole": st["factor_gemm_flops"] + st["selinv_gemm_flops"],
                    "l2": f"no flush: each step streams {st['front_elems'] * 32 * B / 1e9:.1f} GB of fronts "
                          f"(> 129 MB L2)", "parallelism": "replicas" if world == 1 else f"poles sharded x{world}"},
-        "roofline": {"bound": "alu", "kernel": dom["name"], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "derived: FP64 DFMA 2/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                     "launches": dom["launches"], "avg_launch_ms": dom["ms"] / max(1, dom["launches"]),
-                     "time_share": dom["ms"] / total_kernel_ms if total_kernel_ms else None},
-        "gemm_fraction_fp64": {"achieved_tflops": gemm_tf, "peak_tflops": FP64_PEAK_TFLOPS,
-                               "frac": gemm_tf / FP64_PEAK_TFLOPS},
+        "roofline": roofline,
+        "gemm_rate": gemm_rate(kernels),
         "kernel_ms": {p["name"]: round(p["ms"], 3) for p in prof},
         "e2e": {"value": e2e_value, "unit": "pole-solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
@@ -318,6 +410,10 @@ def run_ours(args):
         "peaks_source": peak_src,
     }
     px.pexsi_plan_destroy(plan)
+    if args.split and args.fp64_steps > 0:
+        line["fp64_path"] = fp64_path(px, s, mu, dE, local, dH, dS, stream, args, B, Q, all_shifts, split_dm)
+    if world == 1 and args.serve_requests > 0:
+        line["serving"] = serve_trace(px, local, args.serve_rate, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(1)
         est, wall = oracle_pole_sample(s, mu, dE, 0, args.oracle_cols, rng)
@@ -329,6 +425,67 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------------ serving trace
+SERVE_SYSTEMS = [
+    ("sheet8x8", lambda: ns.make_sheet(ncell=8, seed=11)),
+    ("fluid64", lambda: ns.make_fluid(nmol=64, seed=12)),
+    ("chain256", lambda: ns.make_chain(natoms=256, seed=13, norb=4)),
+]
+
+
+def serve_trace(px, device, rate, n_req, seed=0):
+    """Seeded Poisson trace of mu-search-shaped requests (8 inertia shifts then
+    one 60-pole DM) over three system sizes with per-request mu and beta
+    jitter, through the request server twice: continuous batching (4 slots,
+    8-pole device batches) and the plain per-pole path (1 slot, 1 pole per
+    batch). Returns p50 / p99 latency and throughput of both."""
+    rng = np.random.default_rng(seed)
+    systems = []
+    for name, make in SERVE_SYSTEMS:
+        s = make()
+        mu, dE = ns.mu_and_delta_e(s)
+        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=device))
+        systems.append((name, s, mu, dE, plan))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    picks = rng.integers(0, len(systems), n_req)
+    jit_mu = rng.uniform(-0.05, 0.05, n_req)
+    jit_beta = rng.uniform(0.9, 1.1, n_req)
+
+    def run(slots, batch):
+        server = px.pexsi_server_create(px.pexsi_server_opts_default(device=device, slots=slots, batch=batch))
+        reqs = []
+        t0 = time.perf_counter()
+        for k in range(n_req):
+            while time.perf_counter() - t0 < arrivals[k]:
+                time.sleep(0.0005)
+            name, s, mu, dE, plan = systems[picks[k]]
+            m = mu + jit_mu[k]
+            r = px.ServerRequest(plan, s.H, s.S, mu=m, beta=s.beta * jit_beta[k], n_poles=60, delta_e=dE + 0.05,
+                                 shifts=m + np.linspace(-0.2, 0.2, 8) + 1.0e-4)
+            px.pexsi_server_submit(server, r)
+            reqs.append(r)
+        res = [px.pexsi_server_wait(server, r.ticket) for r in reqs]
+        wall = time.perf_counter() - t0
+        st = px.pexsi_server_get_stats(server)
+        px.pexsi_server_destroy(server)
+        lat = np.array([x["latency_ms"] for x in res])
+        ok = all(x["status"] == 0 for x in res)
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "throughput_req_s": n_req / wall, "pole_solves_s": 60 * n_req / wall,
+                "peak_concurrent": st["peak_concurrent"], "all_ok": ok}, reqs
+
+    cont, r1 = run(4, 8)
+    plain, r2 = run(1, 1)
+    same = max(float(np.max(np.abs(a.dm - b.dm))) for a, b in zip(r1, r2))
+    for *_, plan in systems:
+        px.pexsi_plan_destroy(plan)
+    return {"workload": "Poisson arrivals, requests = 8 inertia shifts + one 60-pole DM over "
+                        + ", ".join(f"{n} (n={s.n})" for n, s, *_ in systems)
+                        + "; mu jitter +-0.05 Ha, beta jitter +-10% (sizes scaled down from 4k-50k)",
+            "rate_req_s": rate, "requests": n_req, "continuous": cont, "plain_per_pole": plain,
+            "max_abs_dm_diff_between_modes": same}
 
 
 def main():
@@ -343,6 +500,12 @@ def main():
     ap.add_argument("--oracle-cols", type=int, default=64)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split", type=int, default=6,
+                    help="bf16 slices of the split-precision supernode GEMMs (0 = FP64 everywhere)")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the plain FP64 path reported beside a split-precision run (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving trace (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=3.0, help="Poisson arrival rate of the serving trace")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

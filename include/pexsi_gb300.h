@@ -67,7 +67,11 @@ typedef struct pexsi_opts {
   int32_t leaf_cols;       /* nested-dissection leaf size in columns (default 96)    */
   int32_t amalgamate;      /* 1: relaxed supernode amalgamation (default), 0: off    */
   int32_t max_batch;       /* poles / shifts per device batch, 0 = automatic         */
-  int32_t reserved0;
+  int32_t split_slices;    /* 0: FP64 GEMMs (default). 2..6: split-precision
+                              Takahashi GEMM Y[S,P] = -Y[S,S] L[S,P] on the tcgen05
+                              tensor cores with this many bf16 slices per operand
+                              (Ozaki scheme; 6 slices ~ 43 bits); the diagonal-block
+                              inverses, the Schur updates and the pole sum stay FP64 */
   int64_t hbm_budget;      /* bytes of device workspace the batch may use, 0 = auto  */
 } pexsi_opts;
 
@@ -369,19 +373,23 @@ int pexsi_trace_noalloc(const double* d_dm, const double* d_edm, const double* d
  * the work has completed. Classes (index: name):
  *   0 assemble, 1 extend_add, 2 diag_inv, 3 panel_solve, 4 schur_update,
  *   5 gather, 6 selinv_offdiag, 7 selinv_diag_partial, 8 selinv_diag_reduce,
- *   9 pole_sum, 10 trace
+ *   9 pole_sum, 10 trace, 11 split_slice (the bf16 slicing kernels of the
+ *   split-precision path; its GEMMs stay in classes 4 and 6)
  * flops / bytes are the algorithmic counts of the launches (complex
  * multiply-add = 8 flops, real = 2; bytes = one read of each input element and
- * one write of each output element). */
+ * one write of each output element). tensor_flops: the bf16 tensor-core flops
+ * the split-precision GEMMs execute (2 per multiply-add of every slice
+ * product), 0 elsewhere. */
 typedef struct pexsi_kernel_profile {
   char name[24];
   int64_t launches;
   double ms;
   double flops;
   double bytes;
+  double tensor_flops;
 } pexsi_kernel_profile;
 
-#define PEXSI_PROFILE_CLASSES 11
+#define PEXSI_PROFILE_CLASSES 12
 
 int pexsi_profile_enable(pexsi_plan* plan, int32_t on);
 /* Synchronises the plan's pending work, then writes PEXSI_PROFILE_CLASSES

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ffp-contract=off: host arithmetic (the ordering's Lanczos runs) must give
 # bit-identical results on x86-64 and aarch64 hosts
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-lineinfo", "-I" + os.path.join(HERE, "..", "include")]
-SOURCES = ["symbolic.cpp", "poles.cpp", "kernels.cu", "engine.cu", "server.cu", "mu.cu", "spectral.cu", "noalloc.cu"]
+SOURCES = ["symbolic.cpp", "poles.cpp", "kernels.cu", "ozaki.cu", "engine.cu", "server.cu", "mu.cu", "spectral.cu", "noalloc.cu"]
 HEADERS = ["symbolic.hpp", "kernels.cuh", "plan.hpp"]
 
 

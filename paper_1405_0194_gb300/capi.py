@@ -37,7 +37,7 @@ class PexsiError(RuntimeError):
 
 class pexsi_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("panel", ctypes.c_int32), ("leaf_cols", ctypes.c_int32),
-                ("amalgamate", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("amalgamate", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("split_slices", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64)]
 
 
@@ -60,10 +60,10 @@ class pexsi_dm_info(ctypes.Structure):
 
 class pexsi_kernel_profile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("tensor_flops", ctypes.c_double)]
 
 
-PROFILE_CLASSES = 11
+PROFILE_CLASSES = 12
 
 
 class pexsi_mu_opts(ctypes.Structure):
@@ -317,8 +317,8 @@ def pexsi_profile_read(plan) -> list:
     """Per-kernel-class totals: list of dicts (name, launches, ms, flops, bytes)."""
     arr = (pexsi_kernel_profile * PROFILE_CLASSES)()
     _check(lib().pexsi_profile_read(plan, arr), plan)
-    return [{"name": a.name.decode(), "launches": a.launches, "ms": a.ms, "flops": a.flops, "bytes": a.bytes}
-            for a in arr]
+    return [{"name": a.name.decode(), "launches": a.launches, "ms": a.ms, "flops": a.flops, "bytes": a.bytes,
+             "tensor_flops": a.tensor_flops} for a in arr]
 
 
 def pexsi_dm_device(plan, dH, dS, mu, beta, n_poles, delta_e, pole_begin, pole_end, accumulate, d_dm, d_edm, d_fdm,

@@ -19,7 +19,7 @@ namespace pexsi {
 namespace {
 const char* const kProfNames[PEXSI_PROFILE_CLASSES] = {
     "assemble", "extend_add", "diag_inv", "panel_solve", "schur_update", "gather",
-    "selinv_offdiag", "selinv_diag_partial", "selinv_diag_reduce", "pole_sum", "trace"};
+    "selinv_offdiag", "selinv_diag_partial", "selinv_diag_reduce", "pole_sum", "trace", "split_slice"};
 }
 
 cudaEvent_t Profiler::begin(cudaStream_t st) {
@@ -31,13 +31,13 @@ cudaEvent_t Profiler::begin(cudaStream_t st) {
   return a;
 }
 
-void Profiler::end(cudaEvent_t a, int cls, cudaStream_t st, double fl, double by, int kernels) {
+void Profiler::end(cudaEvent_t a, int cls, cudaStream_t st, double fl, double by, int kernels, double tensor_fl) {
   if (!on || !a) return;
   cudaEvent_t b;
   if (!pool.empty()) { b = pool.back(); pool.pop_back(); }
   else ck(cudaEventCreate(&b), "cudaEventCreate(profile)");
   ck(cudaEventRecord(b, st), "cudaEventRecord(profile)");
-  pending.push_back({cls, a, b, fl, by, kernels});
+  pending.push_back({cls, a, b, fl, by, kernels, tensor_fl});
 }
 
 void Profiler::drain() {
@@ -49,6 +49,7 @@ void Profiler::drain() {
     ms[q.cls] += t;
     flops[q.cls] += q.flops;
     bytes[q.cls] += q.bytes;
+    tensor[q.cls] += q.tensor;
     pool.push_back(q.a);
     pool.push_back(q.b);
   }
@@ -57,7 +58,7 @@ void Profiler::drain() {
 
 void Profiler::reset() {
   drain();
-  for (int c = 0; c < PEXSI_PROFILE_CLASSES; ++c) { launches[c] = 0; ms[c] = flops[c] = bytes[c] = 0; }
+  for (int c = 0; c < PEXSI_PROFILE_CLASSES; ++c) { launches[c] = 0; ms[c] = flops[c] = bytes[c] = tensor[c] = 0; }
 }
 
 void Profiler::destroy() {
@@ -69,7 +70,8 @@ void Profiler::destroy() {
 
 // ------------------------------------------------------------------ workspaces
 int64_t bytes_per_pole(const pexsi_plan* p) {
-  return (2 * p->sym.front_elems + p->part_stride) * int64_t(sizeof(double2));
+  return (2 * p->sym.front_elems + p->part_stride) * int64_t(sizeof(double2)) + p->ozA_stride + p->ozB_stride +
+         4 * (p->exA_stride + p->exB_stride);
 }
 
 int64_t bytes_fixed(const pexsi_plan* p) {
@@ -102,12 +104,20 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
   wsalloc(&ws.neg, sizeof(int) * kMaxBatch, ws, "alloc(status)");
   wsalloc(&ws.partials, sizeof(double) * 4 * p->trace_blocks, ws, "alloc(trace)");
   wsalloc(&ws.trace3, sizeof(double) * 4, ws, "alloc(trace)");
+  if (p->oz_slices > 0) {
+    wsalloc(&ws.ozA, size_t(p->ozA_stride) * batch, ws, "alloc(split A)");
+    wsalloc(&ws.ozB, size_t(p->ozB_stride) * batch, ws, "alloc(split B)");
+    wsalloc(&ws.exA, sizeof(int) * size_t(p->exA_stride) * batch, ws, "alloc(split exponents)");
+    wsalloc(&ws.exB, sizeof(int) * size_t(p->exB_stride) * batch, ws, "alloc(split exponents)");
+    wsalloc(&ws.ozfail, sizeof(int), ws, "alloc(status)");
+  }
   if (!ws.ev0) ck(cudaEventCreate(&ws.ev0), "cudaEventCreate");
   if (!ws.ev1) ck(cudaEventCreate(&ws.ev1), "cudaEventCreate");
 }
 
 void workspace_free(Workspace& ws) {
-  void* ptrs[] = {ws.F, ws.Y, ws.part, ws.H, ws.S, ws.out, ws.brk, ws.minpiv, ws.neg, ws.partials, ws.trace3, ws.ainv};
+  void* ptrs[] = {ws.F,  ws.Y,        ws.part,  ws.H,    ws.S,   ws.out, ws.brk, ws.minpiv, ws.neg,
+                  ws.partials, ws.trace3, ws.ainv, ws.ozA, ws.ozB, ws.exA, ws.exB, ws.ozfail};
   for (void* q : ptrs) {
     if (!q) continue;
     if (ws.async) cudaFreeAsync(q, ws.stream);
@@ -126,7 +136,7 @@ void workspace_free(Workspace& ws) {
 namespace {
 
 struct PanelGeom {
-  int nact = 0, row_tiles = 0, tri_tiles = 0;
+  int nact = 0, row_tiles = 0, tri_tiles = 0, max_mp = 0, oz_tiles = 0, oz_schur = 0;
 };
 
 PanelGeom panel_geom(const Level& lv, int p0, int b) {
@@ -139,6 +149,9 @@ PanelGeom panel_geom(const Level& lv, int p0, int b) {
     int rt = (mp + kTile - 1) / kTile;
     g.row_tiles = std::max(g.row_tiles, rt);
     g.tri_tiles = std::max(g.tri_tiles, rt * (rt + 1) / 2);
+    g.max_mp = std::max(g.max_mp, mp);
+    g.oz_tiles = std::max(g.oz_tiles, ((mp + 127) / 128) * ((bb + 31) / 32));
+    g.oz_schur = std::max(g.oz_schur, oz_schur_tiles(mp));
   }
   return g;
 }
@@ -147,6 +160,7 @@ PanelGeom panel_geom(const Level& lv, int p0, int b) {
 struct PanelWork {
   double diag_fl = 0, diag_by = 0, panel_fl = 0, panel_by = 0, schur_fl = 0, schur_by = 0;
   double off_fl = 0, off_by = 0, dpart_fl = 0, dpart_by = 0, dred_by = 0;
+  double slice_off_by = 0, slice_schur_by = 0;  // split path: read FP64, write bf16 planes (10 B / element / slice)
 };
 
 PanelWork panel_work(const Level& lv, int p0, int b, double es, double fma_fl) {
@@ -167,6 +181,8 @@ PanelWork panel_work(const Level& lv, int p0, int b, double es, double fma_fl) {
     w.dpart_fl += fma_fl * bb * bb * mp;
     w.dpart_by += (2 * mp * bb + nt * bb * bb) * es;
     w.dred_by += (nt + 2) * bb * bb * es;
+    w.slice_off_by += (mp * mp + mp * bb) * (es + 4.0 * 6);
+    w.slice_schur_by += 2 * mp * bb * (es + 4.0 * 6);
   }
   return w;
 }
@@ -199,8 +215,20 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
       launch_panel_solve<T>(F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
       pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
       a = pf.begin(st);
-      launch_trailing<T>(F, fr, dfr, g.nact, g.tri_tiles, p0, b, sh, st);
-      pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by);
+      if (sizeof(T) == sizeof(double2) && p->oz_slices > 0) {
+        OzScratch oz{ws.ozA, p->d_ozA_off, p->ozA_stride, ws.ozB, p->d_ozB_off, p->ozB_stride,
+                     ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+        double2* Fz = reinterpret_cast<double2*>(F);
+        const int S = p->oz_slices;
+        launch_oz_slice_schur(Fz, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
+        pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by);
+        a = pf.begin(st);
+        launch_oz_gemm_schur(Fz, fr, dfr, g.nact, g.oz_schur, p0, b, S, oz, sh.nb, st);
+        pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by, 1, nb * w.schur_fl * 4.0 * S * (S + 1) / 2 / 8.0 * 2.0);
+      } else {
+        launch_trailing<T>(F, fr, dfr, g.nact, g.tri_tiles, p0, b, sh, st);
+        pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by);
+      }
     }
   }
   ck(cudaGetLastError(), "factor kernels");
@@ -222,8 +250,19 @@ void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Pro
       PanelGeom g = panel_geom(lv, p0, b);
       PanelWork w = pf.on ? panel_work(lv, p0, b, es, 8.0) : PanelWork();
       a = pf.begin(st);
-      launch_selinv_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
-      pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by);
+      if (p->oz_slices > 0) {
+        OzScratch oz{ws.ozA, p->d_ozA_off, p->ozA_stride, ws.ozB, p->d_ozB_off, p->ozB_stride,
+                     ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+        const int S = p->oz_slices;
+        launch_oz_slice_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
+        pf.end(a, P_SLICE, st, 0.0, nb * w.slice_off_by);
+        a = pf.begin(st);
+        launch_oz_gemm_offdiag(ws.Y, fr, dfr, g.nact, g.oz_tiles, p0, b, S, oz, sh.nb, st);
+        pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by, 1, nb * w.off_fl * 4.0 * S * (S + 1) / 2 / 8.0 * 2.0);
+      } else {
+        launch_selinv_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
+        pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by);
+      }
       a = pf.begin(st);
       launch_selinv_diag_partial(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.row_tiles,
                                  p0, b, sh, st);
@@ -259,6 +298,16 @@ const unsigned long long kInfBits = 0x7FF0000000000000ull;
 void reset_status(Workspace& ws) {
   ck(cudaMemcpyAsync(ws.brk, &kBig, sizeof(int), cudaMemcpyHostToDevice, ws.stream), "status");
   ck(cudaMemcpyAsync(ws.minpiv, &kInfBits, sizeof(kInfBits), cudaMemcpyHostToDevice, ws.stream), "status");
+  if (ws.ozfail) ck(cudaMemsetAsync(ws.ozfail, 0, sizeof(int), ws.stream), "status");
+}
+
+// A bounded wait inside the split-precision GEMM ran out (never expected).
+int split_failed(Workspace& ws) {
+  if (!ws.ozfail) return 0;
+  int f = 0;
+  ck(cudaMemcpyAsync(&f, ws.ozfail, sizeof(int), cudaMemcpyDeviceToHost, ws.stream), "status");
+  ck(cudaStreamSynchronize(ws.stream), "sync");
+  return f;
 }
 
 // One batch of complex shifts through assembly, factorisation and selected
@@ -331,6 +380,12 @@ int dm_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* d
     *err = "zero or tiny pivot in front " + std::to_string(brk);
     return PEXSI_ERR_BREAKDOWN;
   }
+  if (int f = split_failed(ws)) {
+    *err = "split-precision GEMM: a bounded wait ran out (mode " + std::to_string((f >> 30) & 1) + ", wait " +
+           std::to_string(((f >> 20) & 1023) & 15) + ", K tile " + std::to_string(((f >> 20) & 1023) >> 4) +
+           ", tile " + std::to_string((f - 1) & ((1 << 20) - 1)) + ")";
+    return PEXSI_ERR_INTERNAL;
+  }
   return PEXSI_OK;
 }
 
@@ -386,6 +441,12 @@ int selinv_one(const pexsi_plan* p, Workspace& ws, const double* dH, const doubl
     *err = "zero or tiny pivot in front " + std::to_string(brk);
     return PEXSI_ERR_BREAKDOWN;
   }
+  if (int f = split_failed(ws)) {
+    *err = "split-precision GEMM: a bounded wait ran out (mode " + std::to_string((f >> 30) & 1) + ", wait " +
+           std::to_string(((f >> 20) & 1023) & 15) + ", K tile " + std::to_string(((f >> 20) & 1023) >> 4) +
+           ", tile " + std::to_string((f - 1) & ((1 << 20) - 1)) + ")";
+    return PEXSI_ERR_INTERNAL;
+  }
   return PEXSI_OK;
 }
 
@@ -397,7 +458,8 @@ namespace {
 
 void free_plan_device(pexsi_plan* p) {
   void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
-                  p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_ident};
+                  p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_ident,
+                  p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   cudaStream_t st = p->ws.stream;
@@ -475,6 +537,41 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
     }
   }
   if (p->part_stride == 0) p->part_stride = int64_t(b) * b;
+}
+
+// Split-precision scratch layout: per level, the fronts' slice tiles are laid
+// out one after another (only one level is active at a time).
+void build_split_layout(pexsi_plan* p, std::vector<int64_t>& a_off, std::vector<int64_t>& b_off,
+                        std::vector<int64_t>& ea_off, std::vector<int64_t>& eb_off) {
+  const Symbolic& S = p->sym;
+  const int b = p->b, planes = 2 * p->oz_slices;
+  a_off.assign(S.nsuper, 0);
+  b_off.assign(S.nsuper, 0);
+  ea_off.assign(S.nsuper, 0);
+  eb_off.assign(S.nsuper, 0);
+  for (const Level& lv : p->levels) {
+    int64_t sa = 0, sb = 0, xa = 0, xb = 0;
+    for (int32_t K : lv.fronts) {
+      int64_t mp = S.m(K) - std::min(b, S.s(K));
+      int64_t nmt = (mp + 127) / 128, nkt = (mp + 63) / 64, nnt = (b + 31) / 32;
+      a_off[K] = sa;
+      b_off[K] = sb;
+      ea_off[K] = xa;
+      eb_off[K] = xb;
+      sa += nmt * nkt * planes * oz_tile_bytes_A();
+      sb += std::max(nnt * nkt, (mp + 31) / 32) * planes * oz_tile_bytes_B();
+      xa += mp;
+      xb += std::max<int64_t>(b, mp);
+    }
+    p->ozA_stride = std::max(p->ozA_stride, sa);
+    p->ozB_stride = std::max(p->ozB_stride, sb);
+    p->exA_stride = std::max(p->exA_stride, xa);
+    p->exB_stride = std::max(p->exB_stride, xb);
+  }
+  p->ozA_stride = std::max<int64_t>(p->ozA_stride, 16);
+  p->ozB_stride = std::max<int64_t>(p->ozB_stride, 16);
+  p->exA_stride = std::max<int64_t>(p->exA_stride, 1);
+  p->exB_stride = std::max<int64_t>(p->exB_stride, 1);
 }
 
 // The plan's own workspace: the largest batch that fits the budget.
@@ -562,6 +659,7 @@ int pexsi_profile_read(pexsi_plan* p, pexsi_kernel_profile* out) {
     out[c].ms = p->prof.ms[c];
     out[c].flops = p->prof.flops[c];
     out[c].bytes = p->prof.bytes[c];
+    out[c].tensor_flops = p->prof.tensor[c];
   }
   return PEXSI_OK;
 }
@@ -613,10 +711,12 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
       if (p->opts.panel <= 0) p->opts.panel = def.panel;
       if (p->opts.leaf_cols <= 0) p->opts.leaf_cols = def.leaf_cols;
     }
-    if (p->opts.panel < 16 || p->opts.panel > 64) {
+    if (p->opts.panel < 16 || p->opts.panel > 64 || p->opts.split_slices < 0 || p->opts.split_slices > 6 ||
+        p->opts.split_slices == 1) {
       delete p;
       return PEXSI_ERR_INVALID_ARG;
     }
+    p->oz_slices = p->opts.split_slices;
     p->b = p->opts.panel;
     std::string err;
     int rc = analyse(n, colptr, rowind, perm_or_null, p->opts.leaf_cols, p->opts.amalgamate != 0, p->sym, err);
@@ -631,6 +731,7 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
     }
     ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
     ck(configure_kernels(p->b), "cudaFuncSetAttribute");
+    if (p->oz_slices > 0) ck(oz_configure(p->oz_slices), "cudaFuncSetAttribute(split)");
     const Symbolic& S = p->sym;
     std::vector<int32_t> hs(S.nsuper), hm(S.nsuper);
     for (int32_t K = 0; K < S.nsuper; ++K) { hs[K] = S.s(K); hm[K] = S.m(K); }
@@ -658,6 +759,14 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
     p->d_level_fronts = dev_upload(level_fronts);
     p->d_ea = dev_upload(ea);
     p->d_part_off = dev_upload(part_off);
+    if (p->oz_slices > 0) {
+      std::vector<int64_t> oa, ob, xa, xb;
+      build_split_layout(p, oa, ob, xa, xb);
+      p->d_ozA_off = dev_upload(oa);
+      p->d_ozB_off = dev_upload(ob);
+      p->d_exA_off = dev_upload(xa);
+      p->d_exB_off = dev_upload(xb);
+    }
     {
       std::vector<double> ident(S.nnz, 0.0);  // S = I on the pattern
       for (int64_t j = 0; j < n; ++j)

@@ -39,6 +39,26 @@ struct DevStatus {
   int* neg_count;                    // per batch member: negative eigenvalues of D (inertia)
 };
 
+// Scratch of the split-precision GEMM: bf16 slice tiles of A = Y[S,S] and
+// B = L[S,P], their power-of-two exponents (per row / column), per front
+// offsets within one batch member, strides between batch members, and a
+// failure flag (a bounded wait ran out).
+struct OzScratch {
+  uint8_t* A;
+  const int64_t* A_off;
+  int64_t A_stride;
+  uint8_t* B;
+  const int64_t* B_off;
+  int64_t B_stride;
+  int* exA;
+  const int64_t* exA_off;
+  int64_t exA_stride;
+  int* exB;
+  const int64_t* exB_off;
+  int64_t exB_stride;
+  int* fail;
+};
+
 // ---- launchers (T = double for real inertia, double2 for complex poles) ----
 template <typename T>
 void launch_assemble(T* F, const double* H, const double* S, const int64_t* src, const int64_t* pos, int64_t nlow,
@@ -82,6 +102,27 @@ void launch_extract(const double2* Y, const int64_t* entry_pos, int64_t nnz, dou
 // out[e] = scale * Im Y[entry_pos[e]] (the LDOS matrix from one selected inverse).
 void launch_scaled_imag(const double2* Y, const int64_t* entry_pos, int64_t nnz, double scale, double* out,
                         cudaStream_t st);
+
+// Split-precision Y[S,P] = -Y[S,S] L[S,P] and its mirror: slicing of A and
+// B (max_rows = max m_p), then the tcgen05 GEMM (max_tiles = max over fronts
+// of the 128 x 32 output tiles).
+void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts,
+                             int nfronts, int max_rows, int p0, int b, int S, const OzScratch& oz, int nb,
+                             cudaStream_t st);
+void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
+                            int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+// Split-precision Schur update F[S,S] -= L[S,P] W[S,P]^T (lower triangle):
+// slicing of L rows and W rows, then the tcgen05 GEMM with an FP64
+// read-modify-write (max_tiles = max over fronts of oz_schur_tiles(m_p)).
+void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
+                           int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
+                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+int oz_schur_tiles(int mp);
+size_t oz_smem_bytes(int S);
+int oz_tile_bytes_A();
+int oz_tile_bytes_B();
+cudaError_t oz_configure(int S);
 
 // Raises the dynamic shared-memory limits the kernels need for panel width b.
 cudaError_t configure_kernels(int b);

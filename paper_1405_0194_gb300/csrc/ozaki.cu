@@ -1,0 +1,646 @@
+// Split-precision (Ozaki-scheme) complex GEMMs on the tcgen05 tensor cores:
+// the Takahashi step Y[S,P] = -Y[S,S] L[S,P] of selected inversion and the
+// Schur update F[S,S] -= L[S,P] W[S,P]^T of the factorisation.
+//
+// Error-free splitting (Ozaki, Ogita, Oishi and Rump 2012): each row i of A
+// and each row j of B (both stored K-major) is scaled by a power of two
+// 2^e > max |entry| and cut into S slices of small integers,
+//   x = A_ik / 2^e_i = sum_s a_s 2^(-7 s) + r,  |a_1| <= 128, |a_s| <= 64 (s > 1),
+// |r| <= 2^(-7 S - 1), each slice exact in bfloat16. The cut works on the
+// bit pattern of the double (round to a 7S-bit fixed-point integer, then
+// balanced base-128 digits), so no FP64 instruction is spent on it. A
+// product of two slices is exact in FP32; the tensor core adds them in FP32
+// accumulators in TMEM, one accumulator per "diagonal" D = s + t (products
+// of equal scale 2^(-7 D)) and per real / imaginary part. With S <= 6 and K
+// chunks of 256 every accumulator holds an integer of magnitude at most 2^24
+// (for S = 6 the last diagonal holds 6 pairs: 2 (2 * 2^13 + 4 * 2^12) per k),
+// so the accumulation is exact. After each chunk the epilogue warps convert
+// the accumulators to integers and combine them exactly in 64-bit integers,
+// sum_D acc_D 2^(7 (S + 1 - D)) (magnitude below 2^58.1 per chunk, so eight
+// chunks stay below 2^61), moving the sum into FP64 every eight chunks; the
+// result is finally scaled by 2^(e_i + f_j - 7 (S + 1)). Pairs with
+// s + t > S + 1 are dropped (their contribution is below 2^(-7 (S + 2)) of
+// |A_i| |B_j|).
+//
+// Operands are pre-tiled by the slicing kernel into the no-swizzle K-major
+// core-matrix layout the MMA descriptors read: an R x 64 tile of one slice
+// plane stores element (r, k) at byte (r/8)*1024 + (k/8)*128 + (r%8)*16 +
+// (k%8)*2; the 2S planes of one (row tile, K tile) are contiguous, re and im
+// of a slice adjacent, so one bulk async copy stages a slice of A (32 KiB) or
+// all planes of B (2S x 4 KiB).
+//
+// The GEMM CTA is warp-specialised: a producer warp streams slices of A
+// through a ring of four shared-memory slots and B through two slots
+// (cp.async.bulk, mbarrier transaction counts); an MMA warp issues
+// tcgen05.mma from one thread and releases each slot with tcgen05.commit;
+// eight epilogue warps drain TMEM after every K chunk while the producer
+// keeps loading. Every wait is bounded (1 s of wall time); a wait that runs
+// out records where in a status word, lets the other roles stop, waits
+// (bounded) for its own copies and MMAs in flight, frees TMEM and returns,
+// and CTAs that start after a failure return at once.
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace pexsi {
+namespace {
+
+constexpr int kOzM = 128;     // rows of A per CTA (TMEM lanes)
+constexpr int kOzN = 32;      // rows of B (output columns) per CTA
+constexpr int kOzK = 64;      // K per staged tile
+constexpr int kOzChunk = 4;   // K tiles per exact FP32 accumulation (256)
+constexpr int kOzFlush = 8;   // chunks per 64-bit integer partial sum
+constexpr int kTileA = kOzM * kOzK * 2;  // bytes of one A slice plane tile (16 KiB)
+constexpr int kTileB = kOzN * kOzK * 2;  // bytes of one B slice plane tile (4 KiB)
+constexpr int kSlotsA = 4;    // A ring: one slice (re + im planes) of one K tile per slot
+constexpr int kSlotsB = 2;    // B ring: all 2S planes of one K tile per slot
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, 16 columns each
+constexpr int kGemmThreads = (kEpiWarps + 2) * 32;  // + producer warp + MMA warp
+constexpr int kNanExp = 0x7FFF;                     // exponent marker of a row holding Inf or NaN
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: LBO = 128 B between
+// core matrices along K, SBO = 1024 B between 8-row groups, version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46);
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major,
+// N = 32, M = 128; optionally B negated.
+__device__ __forceinline__ uint32_t idesc(bool negate_b) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_b ? (1u << 14) : 0u) | (uint32_t(kOzN >> 3) << 17) |
+         (uint32_t(kOzM >> 4) << 24);
+}
+
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (kWaitNs of wall time) for the completion of the barrier
+// phase of the given parity; gives up early once another role has recorded a
+// failure.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, const volatile int* fail) {
+  if (bar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (bar_try(bar, parity)) return true;
+    if (*fail) return false;
+    if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// Bounded wait that ignores failures (draining own copies / MMAs in flight).
+__device__ __forceinline__ bool bar_wait_all(uint32_t bar, uint32_t parity) {
+  if (bar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (bar_try(bar, parity)) return true;
+    if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate));
+}
+
+// Arrives on `bar` once every tcgen05.mma this thread issued so far is done.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Balanced base-2^7 digits of x 2^(-e), |x| < 2^e: X = the integer nearest to
+// x 2^(7 S - e), taken from the bit pattern (mantissa shifted right by
+// n >= 10 with rounding, no floating-point arithmetic); then d[S-1] ... d[1]
+// in [-64, 63] from the low end, d[0] = the rest, |d[0]| <= 128.
+__device__ __forceinline__ void digits(double x, int e, int S, int (&d)[6]) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = int((bits >> 52) & 0x7FF);
+  unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+  int Ee = 1;  // subnormals: exponent of the smallest normal, no hidden bit
+  if (E != 0) {
+    mant |= 1ull << 52;
+    Ee = E;
+  }
+  const int n = 1075 - Ee - 7 * S + e;
+  long long X = 0;
+  if (n > 0 && n < 54) X = static_cast<long long>((mant + (1ull << (n - 1))) >> n);
+  if (bits >> 63) X = -X;
+#pragma unroll
+  for (int s = 5; s >= 1; --s) {
+    if (s < S) {
+      const int dd = int((X + 64) & 127) - 64;
+      d[s] = dd;
+      X = (X - dd) >> 7;
+    } else {
+      d[s] = 0;
+    }
+  }
+  d[0] = int(X);
+}
+
+// bfloat16 bit pattern of a small integer (|d| <= 2^8, exact): the float
+// 1.5 * 2^23 + d has d in its low mantissa bits, and subtracting 1.5 * 2^23
+// gives d exactly.
+__device__ __forceinline__ uint32_t bf16_bits(int d) {
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+}
+
+// Per-(front, pole) geometry of the active panel.
+struct PanelDims {
+  int f, s, m, bb, q0, mp;
+};
+
+__device__ __forceinline__ bool panel_dims(const DevFronts& fr, const int32_t* fronts, int fi, int p0, int b,
+                                           PanelDims& d) {
+  d.f = fronts[fi];
+  d.s = fr.s[d.f];
+  d.m = fr.m[d.f];
+  if (p0 >= d.s) return false;
+  d.bb = min(b, d.s - p0);
+  d.q0 = p0 + d.bb;
+  d.mp = d.m - d.q0;
+  return d.mp > 0;
+}
+
+// ---------------------------------------------------------------- slicing
+// PHASE 0 (Takahashi): A = Y[S,S] (row i = column q0 + i of the symmetric
+//   trailing block, K = m_p), B = L[S,P] (row j = panel column p0 + j).
+// PHASE 1 (Schur): A = L[S,P] (row i = front row q0 + i, K = the panel's bb
+//   columns), B = W[S,P] (row j = column q0 + j of the stored W^T).
+// One block of 256 threads per group of 8 operand rows; grid (groups of A,
+// then groups of B; fronts; poles). Pass 1: warp w finds the exponent of row
+// 8g + w. Pass 2: thread (r, o) cuts the 8 entries of row 8g + r at K octet
+// o into 2S 16-byte words, one per slice plane, at the place the MMA
+// descriptors read them. Rows past the operand (inside the last group) and K
+// past its end are written as zeros.
+template <int PHASE>
+__global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y, const double2* __restrict__ F,
+                                                  DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
+                                                  int S, int groupsA, OzScratch oz) {
+  PanelDims d;
+  if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
+  const int pole = blockIdx.z;
+  const bool isA = int(blockIdx.x) < groupsA;
+  const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
+  const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
+  const double2* src;
+  int64_t si, sk;
+  int rows, K, nkt;
+  if (PHASE == 0) {
+    K = d.mp;
+    nkt = (d.mp + kOzK - 1) / kOzK;
+    si = d.m;
+    sk = 1;
+    if (isA) {
+      src = Y + fo + int64_t(d.q0) * d.m + d.q0;
+      rows = d.mp;
+    } else {
+      src = F + fo + int64_t(p0) * d.m + d.q0;
+      rows = d.bb;
+    }
+  } else {
+    K = d.bb;
+    nkt = 1;
+    rows = d.mp;
+    if (isA) {
+      src = F + fo + d.q0 + int64_t(d.m) * p0;
+      si = 1;
+      sk = d.m;
+    } else {
+      src = F + fo + p0 + int64_t(d.m) * d.q0;
+      si = d.m;
+      sk = 1;
+    }
+  }
+  const int R = isA ? kOzM : kOzN;
+  const int TB = isA ? kTileA : kTileB;
+  uint8_t* dst = isA ? oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f]
+                     : oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f];
+  int* ex = isA ? oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f]
+                : oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];
+  if (g * 8 >= rows) return;
+
+  __shared__ int s_e[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const int i = g * 8 + warp;
+    uint32_t mx = 0;  // largest high word of |re|, |im|: carries the largest exponent
+    if (i < rows)
+      for (int k = lane; k < K; k += 32) {
+        const double2 v = src[int64_t(i) * si + int64_t(k) * sk];
+        mx = max(mx, max(uint32_t(__double2hiint(v.x)) & 0x7FFFFFFFu, uint32_t(__double2hiint(v.y)) & 0x7FFFFFFFu));
+      }
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    int e = 0;  // 2^e > max |entry|
+    if (mx >= 0x7FF00000u)
+      e = kNanExp;
+    else if (mx != 0)
+      e = int(mx >> 20) - 1022;
+    if (lane == 0) {
+      s_e[warp] = e;
+      if (i < rows) ex[i] = e;
+    }
+  }
+  __syncthreads();
+
+  const int r = threadIdx.x & 7;
+  const int i = g * 8 + r;
+  const int e = s_e[r];
+  const int planes = 2 * S;
+  uint8_t* rowbase = dst + int64_t(i / R) * nkt * planes * TB + ((i % R) >> 3) * 1024 + r * 16;
+  const double2* row = src + int64_t(i) * si;
+  for (int o = threadIdx.x >> 3; o < nkt * 8; o += 32) {
+    uint32_t w[12][4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const int k0 = o * 8 + u;
+      double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
+      if (i < rows) {
+        if (k0 < K) v0 = row[int64_t(k0) * sk];
+        if (k0 + 1 < K) v1 = row[int64_t(k0 + 1) * sk];
+      }
+      int r0[6], i0[6], r1[6], i1[6];
+      digits(v0.x, e, S, r0);
+      digits(v0.y, e, S, i0);
+      digits(v1.x, e, S, r1);
+      digits(v1.y, e, S, i1);
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        w[2 * s][u / 2] = bf16_bits(r0[s]) | (bf16_bits(r1[s]) << 16);
+        w[2 * s + 1][u / 2] = bf16_bits(i0[s]) | (bf16_bits(i1[s]) << 16);
+      }
+    }
+    uint8_t* p = rowbase + int64_t(o >> 3) * planes * TB + (o & 7) * 128;
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+      if (q < planes) *reinterpret_cast<uint4*>(p + q * TB) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  }
+}
+
+// Output tiles of the Schur update that touch the lower triangle of the
+// m_p x m_p trailing block: for row tile mt, column tiles 0 .. 4 mt + 3.
+__host__ __device__ inline int schur_tiles(int mp) {
+  const int nmt = (mp + kOzM - 1) / kOzM, nnt = (mp + kOzN - 1) / kOzN;
+  int t = 0;
+  for (int mt = 0; mt < nmt; ++mt) t += min(4 * mt + 4, nnt);
+  return t;
+}
+
+// Where a wait ran out: site (1..8) + 16 * (K tile mod 64).
+__device__ __forceinline__ void record_fail(int* s_fail, int site, int kt) {
+  atomicCAS(s_fail, 0, site + 16 * (kt & 63));
+}
+
+// ---------------------------------------------------------------- GEMM
+// MODE 0, Takahashi: one CTA per (128-row tile of S, 32-column tile of P,
+//   front, pole); Y[S,P] = -A B^T with A = Y[S,S], B = L[S,P]^T, and mirror.
+// MODE 1, Schur: one CTA per lower-triangle output tile (128 x 32) of the
+//   trailing block; F[S,S] -= A B^T with A = L[S,P], B = W[S,P] (K = bb).
+// Warps 0-7 epilogue, warp 8 producer, warp 9 MMA issuer (and TMEM owner).
+template <int MODE>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict__ Y, DevFronts fr,
+                                                             const int32_t* __restrict__ fronts, int p0, int b,
+                                                             int S, OzScratch oz) {
+  extern __shared__ __align__(128) uint8_t osm[];
+  __shared__ __align__(8) uint64_t full_a[kSlotsA], empty_a[kSlotsA], full_b[kSlotsB], empty_b[kSlotsB];
+  __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  PanelDims d;
+  if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
+  if (*static_cast<volatile int*>(oz.fail)) return;  // an earlier CTA gave up: the result is void anyway
+  int mt, nt, nkt;
+  if (MODE == 0) {
+    const int nmt = (d.mp + kOzM - 1) / kOzM, nnt = (d.bb + kOzN - 1) / kOzN;
+    if (int(blockIdx.x) >= nmt * nnt) return;
+    mt = blockIdx.x / nnt;
+    nt = blockIdx.x % nnt;
+    nkt = (d.mp + kOzK - 1) / kOzK;
+  } else {
+    const int nmt = (d.mp + kOzM - 1) / kOzM, nnt = (d.mp + kOzN - 1) / kOzN;
+    int t = blockIdx.x;
+    mt = -1;
+    for (int q = 0; q < nmt; ++q) {
+      const int c = min(4 * q + 4, nnt);
+      if (t < c) {
+        mt = q;
+        break;
+      }
+      t -= c;
+    }
+    if (mt < 0) return;
+    nt = t;
+    nkt = 1;
+  }
+  const int pole = blockIdx.z;
+  const int planes = 2 * S;
+  const int nchunks = (nkt + kOzChunk - 1) / kOzChunk;
+  uint8_t* sA = osm;                          // kSlotsA x (re, im) planes of one A slice
+  uint8_t* sB = osm + kSlotsA * 2 * kTileA;   // kSlotsB x 2S planes of B
+  const uint8_t* gA = oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f] + int64_t(mt) * nkt * planes * kTileA;
+  const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + int64_t(nt) * nkt * planes * kTileB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* fail = &s_fail;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int j = 0; j < kSlotsA; ++j) {
+      bar_init(smem_u32(&full_a[j]), 1);
+      bar_init(smem_u32(&empty_a[j]), 1);
+    }
+    for (int j = 0; j < kSlotsB; ++j) {
+      bar_init(smem_u32(&full_b[j]), 1);
+      bar_init(smem_u32(&empty_b[j]), 1);
+    }
+    bar_init(smem_u32(&acc_full), 1);
+    bar_init(smem_u32(&acc_empty), kEpiWarps);
+    bar_init(smem_u32(&mma_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == kEpiWarps + 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  // epilogue state: rows of TMEM lane quarter q, columns 16 h .. 16 h + 15
+  const int q = warp & 3, h = (warp >> 2) & 1;
+  double dre[16], dim[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) dre[c] = dim[c] = 0.0;
+
+  if (warp == kEpiWarps) {
+    if (lane == 0) {  // ---- producer
+      int na = 0, nbf = 0;
+      for (int kt = 0; kt < nkt && !*fail; ++kt) {
+        const int sb = kt % kSlotsB, ub = kt / kSlotsB;
+        if (ub > 0 && !bar_wait(smem_u32(&empty_b[sb]), (ub - 1) & 1, fail)) {
+          record_fail(&s_fail, 1, kt);
+          break;
+        }
+        bar_expect(smem_u32(&full_b[sb]), uint32_t(planes * kTileB));
+        bulk_load(smem_u32(sB + sb * planes * kTileB), gB + int64_t(kt) * planes * kTileB, uint32_t(planes * kTileB),
+                  smem_u32(&full_b[sb]));
+        ++nbf;
+        bool ok = true;
+        for (int s = 0; s < S; ++s) {
+          const int sa = na % kSlotsA, ua = na / kSlotsA;
+          if (ua > 0 && !bar_wait(smem_u32(&empty_a[sa]), (ua - 1) & 1, fail)) {
+            record_fail(&s_fail, 2, kt);
+            ok = false;
+            break;
+          }
+          bar_expect(smem_u32(&full_a[sa]), uint32_t(2 * kTileA));
+          bulk_load(smem_u32(sA + sa * 2 * kTileA), gA + (int64_t(kt) * planes + 2 * s) * kTileA, uint32_t(2 * kTileA),
+                    smem_u32(&full_a[sa]));
+          ++na;
+        }
+        if (!ok) break;
+      }
+      // every copy issued has landed before the CTA leaves (bounded)
+      for (int j = 0; j < kSlotsA; ++j)
+        if (na > j && !bar_wait_all(smem_u32(&full_a[j]), ((na - 1 - j) / kSlotsA) & 1)) record_fail(&s_fail, 3, 0);
+      for (int j = 0; j < kSlotsB; ++j)
+        if (nbf > j && !bar_wait_all(smem_u32(&full_b[j]), ((nbf - 1 - j) / kSlotsB) & 1)) record_fail(&s_fail, 3, 1);
+    }
+  } else if (warp == kEpiWarps + 1) {
+    if (lane == 0) {  // ---- MMA issuer
+      const uint32_t id_pos = idesc(false), id_neg = idesc(true);
+      int na = 0;
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int c = kt / kOzChunk, in_chunk = kt % kOzChunk;
+        if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail)) {
+          record_fail(&s_fail, 4, kt);
+          break;
+        }
+        const int sb = kt % kSlotsB;
+        if (!bar_wait(smem_u32(&full_b[sb]), (kt / kSlotsB) & 1, fail)) {
+          record_fail(&s_fail, 5, kt);
+          break;
+        }
+        bool ok = true;
+        for (int s = 1; s <= S; ++s) {
+          const int sa = na % kSlotsA;
+          if (!bar_wait(smem_u32(&full_a[sa]), (na / kSlotsA) & 1, fail)) {
+            record_fail(&s_fail, 6, kt);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t aR = smem_u32(sA + sa * 2 * kTileA), aI = aR + kTileA;
+          // accumulators: (diagonal D = s + t, part) at column ((D - 2) * 2 + part) * 32
+          for (int t = 1; s + t <= S + 1; ++t) {
+            const uint32_t acc_re = tmem + uint32_t(((s + t - 2) * 2 + 0) * kOzN);
+            const uint32_t acc_im = tmem + uint32_t(((s + t - 2) * 2 + 1) * kOzN);
+            const uint32_t bR = smem_u32(sB + sb * planes * kTileB + (2 * (t - 1)) * kTileB), bI = bR + kTileB;
+#pragma unroll
+            for (int ks = 0; ks < kOzK / 16; ++ks) {
+              const uint32_t ko = uint32_t(ks * 256);  // two core matrices along K
+              // the first product into each accumulator of a chunk overwrites
+              // it: for diagonal D that is the pair (1, D - 1) at ks = 0
+              const uint32_t acc = (in_chunk == 0 && ks == 0 && s == 1) ? 0u : 1u;
+              mma(acc_re, sdesc(aR + ko), sdesc(bR + ko), id_pos, acc);
+              mma(acc_re, sdesc(aI + ko), sdesc(bI + ko), id_neg, 1u);
+              mma(acc_im, sdesc(aR + ko), sdesc(bI + ko), id_pos, acc);
+              mma(acc_im, sdesc(aI + ko), sdesc(bR + ko), id_pos, 1u);
+            }
+          }
+          mma_commit(smem_u32(&empty_a[sa]));
+          ++na;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&empty_b[sb]));
+        if (in_chunk == kOzChunk - 1 || kt == nkt - 1) mma_commit(smem_u32(&acc_full));
+      }
+      // every MMA issued has completed before TMEM is read for the last time or freed
+      mma_commit(smem_u32(&mma_done));
+      if (!bar_wait_all(smem_u32(&mma_done), 0)) record_fail(&s_fail, 7, 0);
+    }
+  } else {  // ---- epilogue: exact FP32 integers -> 64-bit integers -> FP64
+    unsigned long long pre[16], pim[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) pre[c] = pim[c] = 0ull;
+    int pending = 0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      bool ok = true;
+      if (lane == 0) ok = bar_wait(smem_u32(&acc_full), ch & 1, fail);
+      ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+      if (!ok) {
+        if (lane == 0) record_fail(&s_fail, 8, ch * kOzChunk);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int D = 2; D <= S + 1; ++D) {
+        const int sh = 7 * (S + 1 - D);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          uint32_t v[16];
+          const uint32_t addr = tmem + (uint32_t(q * 32) << 16) + uint32_t(((D - 2) * 2 + part) * kOzN + h * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15])
+              : "r"(addr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const unsigned long long t =
+                static_cast<unsigned long long>(static_cast<long long>(__float2int_rn(__uint_as_float(v[c])))) << sh;
+            if (part == 0)
+              pre[c] += t;
+            else
+              pim[c] += t;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) bar_arrive(smem_u32(&acc_empty));
+      if (++pending == kOzFlush || ch == nchunks - 1) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          dre[c] += double(static_cast<long long>(pre[c]));
+          dim[c] += double(static_cast<long long>(pim[c]));
+          pre[c] = pim[c] = 0ull;
+        }
+        pending = 0;
+      }
+    }
+  }
+
+  __syncthreads();
+  if (s_fail) {
+    if (threadIdx.x == 0)  // where the wait gave up: mode, site + 16 * K tile, tile
+      atomicMax(oz.fail, 1 + (MODE << 30) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
+  } else if (warp < kEpiWarps) {
+    const int i = mt * kOzM + q * 32 + lane;  // row of the trailing block
+    if (i < d.mp) {
+      const int ea = oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i];
+      double2* Yb = Y + int64_t(pole) * fr.pool + fr.off[d.f];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int j = nt * kOzN + h * 16 + c;
+        const bool in = MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb);
+        if (in) {
+          const int eb = oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + j];
+          double2 v;
+          if (ea == kNanExp || eb == kNanExp) {
+            v = make_double2(__longlong_as_double(0x7FF8000000000000LL), __longlong_as_double(0x7FF8000000000000LL));
+          } else {
+            const int sc = ea + eb - 7 * (S + 1);
+            v = make_double2(ldexp(dre[c], sc), ldexp(dim[c], sc));
+          }
+          if (MODE == 1) {
+            double2* dst = Yb + (d.q0 + i) + int64_t(d.m) * (d.q0 + j);
+            double2 o = *dst;
+            o.x -= v.x;
+            o.y -= v.y;
+            *dst = o;
+          } else {
+            const double2 nv = make_double2(-v.x, -v.y);
+            Yb[(d.q0 + i) + int64_t(d.m) * (p0 + j)] = nv;
+            Yb[(p0 + j) + int64_t(d.m) * (d.q0 + i)] = nv;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == kEpiWarps + 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+}  // namespace
+
+size_t oz_smem_bytes(int S) { return size_t(kSlotsA) * 2 * kTileA + size_t(kSlotsB) * 2 * S * kTileB; }
+
+int oz_tile_bytes_A() { return kTileA; }
+int oz_tile_bytes_B() { return kTileB; }
+
+cudaError_t oz_configure(int S) {
+  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(oz_smem_bytes(S)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(oz_smem_bytes(S)));
+}
+
+int oz_schur_tiles(int mp) { return schur_tiles(mp); }
+
+void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
+                           int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
+  if (nfronts <= 0 || max_mp <= 0) return;
+  const int groups = (max_mp + 7) / 8;
+  dim3 g(2 * groups, nfronts, nb);
+  k_oz_slice<1><<<g, 256, 0, st>>>(F, F, fr, fronts, p0, b, S, groups, oz);
+}
+
+void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
+                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
+  if (nfronts <= 0 || max_tiles <= 0) return;
+  dim3 gg(max_tiles, nfronts, nb);
+  k_oz_gemm<1><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
+}
+
+void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts,
+                             int nfronts, int max_rows, int p0, int b, int S, const OzScratch& oz, int nb,
+                             cudaStream_t st) {
+  if (nfronts <= 0 || max_rows <= 0) return;
+  const int groupsA = (max_rows + 7) / 8, groupsB = (b + 7) / 8;
+  dim3 g(groupsA + groupsB, nfronts, nb);
+  k_oz_slice<0><<<g, 256, 0, st>>>(Y, F, fr, fronts, p0, b, S, groupsA, oz);
+}
+
+void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
+                            int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
+  if (nfronts <= 0 || max_tiles <= 0) return;
+  dim3 gg(max_tiles, nfronts, nb);
+  k_oz_gemm<0><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(Y, fr, fronts, p0, b, S, oz);
+}
+
+}  // namespace pexsi

@@ -51,19 +51,23 @@ struct Profiler {
     cudaEvent_t a, b;
     double flops, bytes;
     int kernels;
+    double tensor;
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   int64_t launches[PEXSI_PROFILE_CLASSES] = {};
   double ms[PEXSI_PROFILE_CLASSES] = {}, flops[PEXSI_PROFILE_CLASSES] = {}, bytes[PEXSI_PROFILE_CLASSES] = {};
+  double tensor[PEXSI_PROFILE_CLASSES] = {};
   cudaEvent_t begin(cudaStream_t st);
-  void end(cudaEvent_t a, int cls, cudaStream_t st, double fl, double by, int kernels = 1);
+  void end(cudaEvent_t a, int cls, cudaStream_t st, double fl, double by, int kernels = 1, double tensor_fl = 0.0);
   void drain();
   void reset();
   void destroy();
 };
 
-enum ProfClass { P_ASSEMBLE, P_EXTEND, P_DIAG, P_PANEL, P_SCHUR, P_GATHER, P_OFFDIAG, P_DPART, P_DRED, P_POLESUM, P_TRACE };
+enum ProfClass {
+  P_ASSEMBLE, P_EXTEND, P_DIAG, P_PANEL, P_SCHUR, P_GATHER, P_OFFDIAG, P_DPART, P_DRED, P_POLESUM, P_TRACE, P_SLICE
+};
 
 // Device buffers of one in-flight computation: fronts for `batch` poles (or
 // 2 x batch real shifts), split-K partials, status words, trace scratch, and
@@ -78,6 +82,8 @@ struct Workspace {
   double* trace3 = nullptr;
   double *H = nullptr, *S = nullptr, *out = nullptr;  // nnz, nnz, 4 nnz (DM, EDM, FDM, Gamma^d)
   double2* ainv = nullptr;
+  uint8_t *ozA = nullptr, *ozB = nullptr;  // split-precision slice tiles
+  int *exA = nullptr, *exB = nullptr, *ozfail = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool async = false;  // buffers from cudaMallocAsync on `stream`
@@ -102,6 +108,11 @@ struct pexsi_plan {
   int64_t* d_part_off = nullptr;
   int64_t part_stride = 0;  // partial-scratch elements per batch member
   double* d_ident = nullptr;
+  // split-precision scratch layout (per front offsets within a level; strides
+  // per batch member): slice tiles of A and B, exponents of A rows, B columns
+  int oz_slices = 0;
+  int64_t *d_ozA_off = nullptr, *d_ozB_off = nullptr, *d_exA_off = nullptr, *d_exB_off = nullptr;
+  int64_t ozA_stride = 0, ozB_stride = 0, exA_stride = 0, exB_stride = 0;
   std::vector<pexsi::Level> levels;
   pexsi::FlopCounts flops;
   int trace_blocks = 256;

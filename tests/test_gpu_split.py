@@ -1,0 +1,84 @@
+"""Split-precision path (bf16 Ozaki slices on the tcgen05 tensor cores for the
+Takahashi GEMM) against the FP64 oracle: max |Delta DM| <= 1e-7, the stated
+tolerance of the split path; errors printed per slice count."""
+import numpy as np
+import pytest
+
+import nao_synth as ns
+from oracle import dense
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1405_0194_gb300 as px  # noqa: E402
+
+TOL_SPLIT = 1e-7
+
+
+@pytest.fixture(scope="module")
+def cases():
+    from paper_1405_0194_gb300 import build
+    build.build()
+    out = {}
+    for name, s in (("chain64", ns.make_chain()), ("fluid24", ns.make_fluid(nmol=24, seed=1)),
+                    ("sheet8", ns.make_sheet(ncell=8, seed=2))):
+        mu, dE = ns.mu_and_delta_e(s)
+        out[name] = (s, mu, dE)
+    return out
+
+
+@pytest.mark.parametrize("name", ["chain64", "fluid24", "sheet8"])
+def test_split_dm_within_tolerance(cases, name):
+    s, mu, dE = cases[name]
+    P = s.n_poles if name == "chain64" else 16
+    dm0, edm0, fdm0, _ = dense.density_matrices(s.n, s.colptr, s.rowind, s.H, s.S, mu, s.beta, P, dE)
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(split_slices=6))
+    dm, edm, fdm, info = px.pexsi_dm(plan, s.H, s.S, mu, s.beta, P, dE)
+    px.pexsi_plan_destroy(plan)
+    err = np.max(np.abs(dm - dm0))
+    dtr = abs(info["trace_dm_s"] - dense.trace_with_s(dm0, s.S))
+    print(f"{name}: split(6) max|dDM| = {err:.3e}, |dTr| = {dtr:.3e}")
+    assert err <= TOL_SPLIT
+    assert dtr <= 1e-8
+    assert np.max(np.abs(edm - edm0)) <= TOL_SPLIT * max(1.0, np.max(np.abs(edm0)))
+    assert np.max(np.abs(fdm - fdm0)) <= TOL_SPLIT * max(1.0, np.max(np.abs(fdm0)))
+
+
+def test_split_selinv_error_falls_with_slices(cases):
+    s, mu, dE = cases["sheet8"]
+    z = mu + 0.13 + 0.002j
+    ref = dense.selected_inverse(s.n, s.colptr, s.rowind, s.H, s.S, z)
+    errs = []
+    for slices in (3, 4, 5, 6):
+        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(split_slices=slices))
+        got = px.pexsi_selinv(plan, s.H, s.S, z)
+        px.pexsi_plan_destroy(plan)
+        errs.append(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        print(f"sheet8 selinv split({slices}) max rel err {errs[-1]:.3e}")
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[3] <= 1e-7
+
+
+def test_split_matches_fp64_gpu_path_at_full_size():
+    """fluid512 (n = 11,776) in the benchmark's launch configuration (a
+    10-pole batch): split-precision DM against the FP64 GPU path."""
+    s = ns.make_fluid(nmol=512, seed=0)
+    mu, dE = 0.0, 2.5
+    dH = torch.from_numpy(s.H).cuda(); dS = torch.from_numpy(s.S).cuda()
+    outs = []
+    for k in (0, 6):
+        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(max_batch=10, split_slices=k))
+        out = torch.zeros(3, s.nnz, dtype=torch.float64, device="cuda")
+        st = torch.cuda.current_stream().cuda_stream
+        info = px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, 60, dE, 0, 10, 0,
+                                  out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), st, want_info=True)
+        px.pexsi_plan_destroy(plan)
+        outs.append((out.cpu().numpy(), info))
+    (a, ia), (b, ib) = outs
+    err = np.max(np.abs(a[0] - b[0]))
+    print(f"fluid512 split(6) vs FP64: max|dDM| = {err:.3e}, dTr = {abs(ia['trace_dm_s'] - ib['trace_dm_s']):.3e}, "
+          f"ms {ia['ms_total']:.0f} -> {ib['ms_total']:.0f}")
+    assert err <= TOL_SPLIT
