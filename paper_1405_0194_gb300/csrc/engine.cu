@@ -70,8 +70,9 @@ void Profiler::destroy() {
 
 // ------------------------------------------------------------------ workspaces
 int64_t bytes_per_pole(const pexsi_plan* p) {
-  return (2 * p->sym.front_elems + p->part_stride) * int64_t(sizeof(double2)) + p->ozA_stride + p->ozB_stride +
-         4 * (p->exA_stride + p->exB_stride);
+  return (2 * p->sym.front_elems + p->part_stride) * int64_t(sizeof(double2)) +
+         std::max(p->ozA_stride, 2 * p->ozA_stride_r) + std::max(p->ozB_stride, 2 * p->ozB_stride_r) +
+         8 * (p->exA_stride + p->exB_stride);
 }
 
 int64_t bytes_fixed(const pexsi_plan* p) {
@@ -105,10 +106,11 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
   wsalloc(&ws.partials, sizeof(double) * 4 * p->trace_blocks, ws, "alloc(trace)");
   wsalloc(&ws.trace3, sizeof(double) * 4, ws, "alloc(trace)");
   if (p->oz_slices > 0) {
-    wsalloc(&ws.ozA, size_t(p->ozA_stride) * batch, ws, "alloc(split A)");
-    wsalloc(&ws.ozB, size_t(p->ozB_stride) * batch, ws, "alloc(split B)");
-    wsalloc(&ws.exA, sizeof(int) * size_t(p->exA_stride) * batch, ws, "alloc(split exponents)");
-    wsalloc(&ws.exB, sizeof(int) * size_t(p->exB_stride) * batch, ws, "alloc(split exponents)");
+    // complex poles use `batch` members, the real inertia shifts up to 2 batch
+    wsalloc(&ws.ozA, size_t(std::max(p->ozA_stride, 2 * p->ozA_stride_r)) * batch, ws, "alloc(split A)");
+    wsalloc(&ws.ozB, size_t(std::max(p->ozB_stride, 2 * p->ozB_stride_r)) * batch, ws, "alloc(split B)");
+    wsalloc(&ws.exA, sizeof(int) * size_t(p->exA_stride) * 2 * batch, ws, "alloc(split exponents)");
+    wsalloc(&ws.exB, sizeof(int) * size_t(p->exB_stride) * 2 * batch, ws, "alloc(split exponents)");
     wsalloc(&ws.ozfail, sizeof(int), ws, "alloc(status)");
   }
   if (!ws.ev0) ck(cudaEventCreate(&ws.ev0), "cudaEventCreate");
@@ -136,7 +138,7 @@ void workspace_free(Workspace& ws) {
 namespace {
 
 struct PanelGeom {
-  int nact = 0, row_tiles = 0, tri_tiles = 0, max_mp = 0, oz_tiles = 0, oz_schur = 0;
+  int nact = 0, row_tiles = 0, tri_tiles = 0, max_mp = 0, oz_tiles = 0, oz_schur = 0, oz_schur_r = 0;
 };
 
 PanelGeom panel_geom(const Level& lv, int p0, int b) {
@@ -150,8 +152,9 @@ PanelGeom panel_geom(const Level& lv, int p0, int b) {
     g.row_tiles = std::max(g.row_tiles, rt);
     g.tri_tiles = std::max(g.tri_tiles, rt * (rt + 1) / 2);
     g.max_mp = std::max(g.max_mp, mp);
-    g.oz_tiles = std::max(g.oz_tiles, ((mp + 127) / 128) * ((bb + 31) / 32));
+    g.oz_tiles = std::max(g.oz_tiles, oz_offdiag_tiles(mp));
     g.oz_schur = std::max(g.oz_schur, oz_schur_tiles(mp));
+    g.oz_schur_r = std::max(g.oz_schur_r, oz_schur_tiles_real(mp));
   }
   return g;
 }
@@ -225,6 +228,17 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
         a = pf.begin(st);
         launch_oz_gemm_schur(Fz, fr, dfr, g.nact, g.oz_schur, p0, b, S, oz, sh.nb, st);
         pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by, 1, nb * w.schur_fl * 4.0 * S * (S + 1) / 2 / 8.0 * 2.0);
+      } else if (sizeof(T) == sizeof(double) && p->oz_slices > 0) {
+        OzScratch oz{ws.ozA, p->d_ozA_off_r, p->ozA_stride_r, ws.ozB, p->d_ozB_off_r, p->ozB_stride_r,
+                     ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+        double* Fr = reinterpret_cast<double*>(F);
+        const int S = p->oz_slices;
+        launch_oz_slice_schur_real(Fr, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
+        pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by);
+        a = pf.begin(st);
+        launch_oz_gemm_schur_real(Fr, fr, dfr, g.nact, g.oz_schur_r, p0, b, S, oz, sh.nb, st);
+        // real: one product per slice pair instead of four (fl counts 2 flops per real multiply-add)
+        pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by, 1, nb * w.schur_fl * S * (S + 1) / 2.0);
       } else {
         launch_trailing<T>(F, fr, dfr, g.nact, g.tri_tiles, p0, b, sh, st);
         pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by);
@@ -418,6 +432,11 @@ int inertia_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const doub
     ck(cudaStreamSynchronize(st), "sync");
     for (int t = 0; t < nb; ++t) counts[b0 + t] = neg[t];
     brk_all = std::min(brk_all, brk);
+    if (int f = split_failed(ws)) {
+      *err = "split-precision GEMM (inertia): a bounded wait ran out (wait " + std::to_string(((f >> 20) & 1023) & 15) +
+             ", tile " + std::to_string((f - 1) & ((1 << 20) - 1)) + ")";
+      return PEXSI_ERR_INTERNAL;
+    }
   }
   if (brk_all != INT_MAX) {
     *err = "zero or tiny pivot in front " + std::to_string(brk_all);
@@ -459,7 +478,7 @@ namespace {
 void free_plan_device(pexsi_plan* p) {
   void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
                   p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_ident,
-                  p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off};
+                  p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off, p->d_ozA_off_r, p->d_ozB_off_r};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   cudaStream_t st = p->ws.stream;
@@ -542,34 +561,44 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
 // Split-precision scratch layout: per level, the fronts' slice tiles are laid
 // out one after another (only one level is active at a time).
 void build_split_layout(pexsi_plan* p, std::vector<int64_t>& a_off, std::vector<int64_t>& b_off,
-                        std::vector<int64_t>& ea_off, std::vector<int64_t>& eb_off) {
+                        std::vector<int64_t>& ea_off, std::vector<int64_t>& eb_off, std::vector<int64_t>& ar,
+                        std::vector<int64_t>& br) {
   const Symbolic& S = p->sym;
-  const int b = p->b, planes = 2 * p->oz_slices;
+  const int b = p->b;
+  ar.assign(S.nsuper, 0);
+  br.assign(S.nsuper, 0);
   a_off.assign(S.nsuper, 0);
   b_off.assign(S.nsuper, 0);
   ea_off.assign(S.nsuper, 0);
   eb_off.assign(S.nsuper, 0);
   for (const Level& lv : p->levels) {
-    int64_t sa = 0, sb = 0, xa = 0, xb = 0;
+    int64_t sa = 0, sb = 0, xa = 0, xb = 0, sar = 0, sbr = 0;
     for (int32_t K : lv.fronts) {
       int64_t mp = S.m(K) - std::min(b, S.s(K));
-      int64_t nmt = (mp + 127) / 128, nkt = (mp + 63) / 64, nnt = (b + 31) / 32;
       a_off[K] = sa;
       b_off[K] = sb;
       ea_off[K] = xa;
       eb_off[K] = xb;
-      sa += nmt * nkt * planes * oz_tile_bytes_A();
-      sb += std::max(nnt * nkt, (mp + 31) / 32) * planes * oz_tile_bytes_B();
+      ar[K] = sar;
+      br[K] = sbr;
+      sa += oz_front_bytes_A(mp, b, p->oz_slices);
+      sb += oz_front_bytes_B(mp, b, p->oz_slices);
+      sar += oz_front_bytes_A_real(mp, b, p->oz_slices);
+      sbr += oz_front_bytes_B_real(mp, b, p->oz_slices);
       xa += mp;
       xb += std::max<int64_t>(b, mp);
     }
     p->ozA_stride = std::max(p->ozA_stride, sa);
     p->ozB_stride = std::max(p->ozB_stride, sb);
+    p->ozA_stride_r = std::max(p->ozA_stride_r, sar);
+    p->ozB_stride_r = std::max(p->ozB_stride_r, sbr);
     p->exA_stride = std::max(p->exA_stride, xa);
     p->exB_stride = std::max(p->exB_stride, xb);
   }
   p->ozA_stride = std::max<int64_t>(p->ozA_stride, 16);
   p->ozB_stride = std::max<int64_t>(p->ozB_stride, 16);
+  p->ozA_stride_r = std::max<int64_t>(p->ozA_stride_r, 16);
+  p->ozB_stride_r = std::max<int64_t>(p->ozB_stride_r, 16);
   p->exA_stride = std::max<int64_t>(p->exA_stride, 1);
   p->exB_stride = std::max<int64_t>(p->exB_stride, 1);
 }
@@ -760,10 +789,12 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
     p->d_ea = dev_upload(ea);
     p->d_part_off = dev_upload(part_off);
     if (p->oz_slices > 0) {
-      std::vector<int64_t> oa, ob, xa, xb;
-      build_split_layout(p, oa, ob, xa, xb);
+      std::vector<int64_t> oa, ob, xa, xb, ra, rb;
+      build_split_layout(p, oa, ob, xa, xb, ra, rb);
       p->d_ozA_off = dev_upload(oa);
       p->d_ozB_off = dev_upload(ob);
+      p->d_ozA_off_r = dev_upload(ra);
+      p->d_ozB_off_r = dev_upload(rb);
       p->d_exA_off = dev_upload(xa);
       p->d_exB_off = dev_upload(xb);
     }

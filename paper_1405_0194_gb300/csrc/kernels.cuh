@@ -105,7 +105,7 @@ void launch_scaled_imag(const double2* Y, const int64_t* entry_pos, int64_t nnz,
 
 // Split-precision Y[S,P] = -Y[S,S] L[S,P] and its mirror: slicing of A and
 // B (max_rows = max m_p), then the tcgen05 GEMM (max_tiles = max over fronts
-// of the 128 x 32 output tiles).
+// of oz_offdiag_tiles(m_p), the 64-row output tiles).
 void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts,
                              int nfronts, int max_rows, int p0, int b, int S, const OzScratch& oz, int nb,
                              cudaStream_t st);
@@ -119,9 +119,21 @@ void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t*
 void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
                           int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
 int oz_schur_tiles(int mp);
+int oz_offdiag_tiles(int mp);
 size_t oz_smem_bytes(int S);
-int oz_tile_bytes_A();
-int oz_tile_bytes_B();
+// Slice-tile scratch of one front per pole (both phases), for its largest m_p.
+int64_t oz_front_bytes_A(int64_t mp, int b, int S);
+int64_t oz_front_bytes_B(int64_t mp, int b, int S);
+int64_t oz_front_bytes_A_real(int64_t mp, int b, int S);
+int64_t oz_front_bytes_B_real(int64_t mp, int b, int S);
+// Split-precision real Schur update of the inertia factorisation (LDL^T of
+// H - sigma S): slicing of L rows and W rows, then the tcgen05 GEMM on
+// 128 x 64 lower-triangle tiles (max_tiles = max of oz_schur_tiles_real).
+int oz_schur_tiles_real(int mp);
+void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
+                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
+                               int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
 cudaError_t oz_configure(int S);
 
 // Raises the dynamic shared-memory limits the kernels need for panel width b.

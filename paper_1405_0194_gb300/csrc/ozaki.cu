@@ -8,29 +8,38 @@
 //   x = A_ik / 2^e_i = sum_s a_s 2^(-7 s) + r,  |a_1| <= 128, |a_s| <= 64 (s > 1),
 // |r| <= 2^(-7 S - 1), each slice exact in bfloat16. The cut works on the
 // bit pattern of the double (round to a 7S-bit fixed-point integer, then
-// balanced base-128 digits), so no FP64 instruction is spent on it. A
-// product of two slices is exact in FP32; the tensor core adds them in FP32
-// accumulators in TMEM, one accumulator per "diagonal" D = s + t (products
-// of equal scale 2^(-7 D)) and per real / imaginary part. With S <= 6 and K
-// chunks of 256 every accumulator holds an integer of magnitude at most 2^24
-// (for S = 6 the last diagonal holds 6 pairs: 2 (2 * 2^13 + 4 * 2^12) per k),
-// so the accumulation is exact. After each chunk the epilogue warps convert
-// the accumulators to integers and combine them exactly in 64-bit integers,
+// balanced base-128 digits), so no FP64 instruction is spent on it.
+//
+// Complex products as real MMAs: a tile of 64 complex rows of A becomes the
+// 128 x K real operand [Ar; Ai] (P1) and, one slice block further on,
+// [Ai; -Ar] (P2); with B = Br + i Bi (64 complex columns as 64 real rows),
+//   P1 Br^T + P2 (-Bi)^T = [Ar Br - Ai Bi; Ai Br + Ar Bi] = [Re; Im],
+// the -Bi coming from the MMA's negate-B bit. So each slice pair (s, t) is
+// two M = 128, N = 64 MMAs per 16-deep K step into ONE accumulator, and the
+// slice tile of A stores the three 64-row blocks Ar, Ai, -Ar back to back.
+//
+// A product of two slices is exact in FP32; the tensor core adds them in FP32
+// accumulators in TMEM, one accumulator (64 columns) per "diagonal"
+// D = s + t (products of equal scale 2^(-7 D)). With S <= 6 and K chunks of
+// 256 every accumulator holds an integer of magnitude at most 2^24 (for
+// S = 6 the last diagonal holds 6 pairs: 2 (2 * 2^13 + 4 * 2^12) per k), so
+// the accumulation is exact. After each chunk the epilogue warps convert the
+// accumulators to integers and combine them exactly in 64-bit integers,
 // sum_D acc_D 2^(7 (S + 1 - D)) (magnitude below 2^58.1 per chunk, so eight
-// chunks stay below 2^61), moving the sum into FP64 every eight chunks; the
-// result is finally scaled by 2^(e_i + f_j - 7 (S + 1)). Pairs with
+// chunks stay below 2^61); the final scaling by 2^(e_i + f_j - 7 (S + 1)) is
+// folded into an integer-only int64 -> double conversion. Pairs with
 // s + t > S + 1 are dropped (their contribution is below 2^(-7 (S + 2)) of
 // |A_i| |B_j|).
 //
 // Operands are pre-tiled by the slicing kernel into the no-swizzle K-major
-// core-matrix layout the MMA descriptors read: an R x 64 tile of one slice
-// plane stores element (r, k) at byte (r/8)*1024 + (k/8)*128 + (r%8)*16 +
-// (k%8)*2; the 2S planes of one (row tile, K tile) are contiguous, re and im
-// of a slice adjacent, so one bulk async copy stages a slice of A (32 KiB) or
-// all planes of B (2S x 4 KiB).
+// core-matrix layout the MMA descriptors read: a block of R rows x 32 k of
+// one slice stores element (r, k) at byte (r/8)*512 + (k/8)*128 + (r%8)*16 +
+// (k%8)*2 (LBO 128 B, SBO 512 B). One (row tile, K tile) holds the S slices
+// one after another: 12 KiB each for A (Ar, Ai, -Ar), 8 KiB each for B
+// (Br, Bi); so one bulk async copy stages a slice of A or all slices of B.
 //
 // The GEMM CTA is warp-specialised: a producer warp streams slices of A
-// through a ring of four shared-memory slots and B through two slots
+// through a ring of eight shared-memory slots and B through two slots
 // (cp.async.bulk, mbarrier transaction counts); an MMA warp issues
 // tcgen05.mma from one thread and releases each slot with tcgen05.commit;
 // eight epilogue warps drain TMEM after every K chunk while the producer
@@ -38,6 +47,7 @@
 // out records where in a status word, lets the other roles stop, waits
 // (bounded) for its own copies and MMAs in flight, frees TMEM and returns,
 // and CTAs that start after a failure return at once.
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -47,36 +57,36 @@
 namespace pexsi {
 namespace {
 
-constexpr int kOzM = 128;     // rows of A per CTA (TMEM lanes)
-constexpr int kOzN = 32;      // rows of B (output columns) per CTA
-constexpr int kOzK = 64;      // K per staged tile
-constexpr int kOzChunk = 4;   // K tiles per exact FP32 accumulation (256)
+constexpr int kOzRows = 64;   // complex rows of A (and of B) per tile
+constexpr int kOzK = 32;      // K per staged tile
+constexpr int kOzChunk = 8;   // K tiles per exact FP32 accumulation (256)
 constexpr int kOzFlush = 8;   // chunks per 64-bit integer partial sum
-constexpr int kTileA = kOzM * kOzK * 2;  // bytes of one A slice plane tile (16 KiB)
-constexpr int kTileB = kOzN * kOzK * 2;  // bytes of one B slice plane tile (4 KiB)
-constexpr int kSlotsA = 4;    // A ring: one slice (re + im planes) of one K tile per slot
-constexpr int kSlotsB = 2;    // B ring: all 2S planes of one K tile per slot
-constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, 16 columns each
+constexpr int kBlk = kOzRows * kOzK * 2;  // bytes of one 64-row block of one slice (4 KiB)
+constexpr int kSliceA = 3 * kBlk;         // Ar, Ai, -Ar (12 KiB)
+constexpr int kSliceB = 2 * kBlk;         // Br, Bi (8 KiB)
+constexpr int kSlotsA = 8;    // A ring: one slice of one K tile per slot
+constexpr int kSlotsB = 2;    // B ring: all S slices of one K tile per slot
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter, 32 columns each
 constexpr int kGemmThreads = (kEpiWarps + 2) * 32;  // + producer warp + MMA warp
 constexpr int kNanExp = 0x7FFF;                     // exponent marker of a row holding Inf or NaN
-constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per wait
+constexpr uint64_t kWaitNs = 1000000000ull;         // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
 // Shared-memory matrix descriptor, no swizzle, K-major: LBO = 128 B between
-// core matrices along K, SBO = 1024 B between 8-row groups, version 1.
+// core matrices along K, SBO = 512 B between 8-row groups, version 1.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) |
+  return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(512 >> 4) << 32) |
          (uint64_t(1) << 46);
 }
 
 // Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major,
-// N = 32, M = 128; optionally B negated.
+// N = 64, M = 128; optionally B negated.
 __device__ __forceinline__ uint32_t idesc(bool negate_b) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_b ? (1u << 14) : 0u) | (uint32_t(kOzN >> 3) << 17) |
-         (uint32_t(kOzM >> 4) << 24);
+  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_b ? (1u << 14) : 0u) | (uint32_t(64 >> 3) << 17) |
+         (uint32_t(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
@@ -185,6 +195,27 @@ __device__ __forceinline__ uint32_t bf16_bits(int d) {
   return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
 }
 
+// v 2^sc rounded to the nearest double (ties to even) with integer
+// operations only; results outside the normal range go through ldexp.
+__device__ __forceinline__ double i64_scaled(long long v, int sc) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = v < 0 ? 0ull - static_cast<unsigned long long>(v) : static_cast<unsigned long long>(v);
+  const int lz = __clzll(static_cast<long long>(u));
+  u <<= lz;                            // leading one at bit 63
+  unsigned long long mant = u >> 11;   // 53 significant bits
+  const unsigned long long rest = u & 0x7FFull;
+  if (rest > 0x400ull || (rest == 0x400ull && (mant & 1ull))) ++mant;
+  int E = 63 - lz + sc + 1023;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++E;
+  }
+  if (E <= 0 || E >= 2047) return ldexp(static_cast<double>(v), sc);
+  return __longlong_as_double(
+      static_cast<long long>(sign | (static_cast<unsigned long long>(E) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // Per-(front, pole) geometry of the active panel.
 struct PanelDims {
   int f, s, m, bb, q0, mp;
@@ -202,6 +233,8 @@ __device__ __forceinline__ bool panel_dims(const DevFronts& fr, const int32_t* f
   return d.mp > 0;
 }
 
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
 // ---------------------------------------------------------------- slicing
 // PHASE 0 (Takahashi): A = Y[S,S] (row i = column q0 + i of the symmetric
 //   trailing block, K = m_p), B = L[S,P] (row j = panel column p0 + j).
@@ -210,9 +243,9 @@ __device__ __forceinline__ bool panel_dims(const DevFronts& fr, const int32_t* f
 // One block of 256 threads per group of 8 operand rows; grid (groups of A,
 // then groups of B; fronts; poles). Pass 1: warp w finds the exponent of row
 // 8g + w. Pass 2: thread (r, o) cuts the 8 entries of row 8g + r at K octet
-// o into 2S 16-byte words, one per slice plane, at the place the MMA
-// descriptors read them. Rows past the operand (inside the last group) and K
-// past its end are written as zeros.
+// o into 16-byte words, per slice: Ar, Ai and -Ar for A, Br and Bi for B,
+// at the place the MMA descriptors read them. Rows past the operand (inside
+// the last group) and K past its end are written as zeros.
 template <int PHASE>
 __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y, const double2* __restrict__ F,
                                                   DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
@@ -225,10 +258,9 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
   const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
   const double2* src;
   int64_t si, sk;
-  int rows, K, nkt;
+  int rows, K;
   if (PHASE == 0) {
     K = d.mp;
-    nkt = (d.mp + kOzK - 1) / kOzK;
     si = d.m;
     sk = 1;
     if (isA) {
@@ -240,7 +272,6 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
     }
   } else {
     K = d.bb;
-    nkt = 1;
     rows = d.mp;
     if (isA) {
       src = F + fo + d.q0 + int64_t(d.m) * p0;
@@ -252,8 +283,8 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
       sk = 1;
     }
   }
-  const int R = isA ? kOzM : kOzN;
-  const int TB = isA ? kTileA : kTileB;
+  const int nkt = ceil_div(K, kOzK);
+  const int slice = isA ? kSliceA : kSliceB;
   uint8_t* dst = isA ? oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f]
                      : oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f];
   int* ex = isA ? oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f]
@@ -286,11 +317,11 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
   const int r = threadIdx.x & 7;
   const int i = g * 8 + r;
   const int e = s_e[r];
-  const int planes = 2 * S;
-  uint8_t* rowbase = dst + int64_t(i / R) * nkt * planes * TB + ((i % R) >> 3) * 1024 + r * 16;
+  // row tile i / 64; inside it, the 8-row group of i and row i % 8
+  uint8_t* rowbase = dst + int64_t(i / kOzRows) * nkt * S * slice + ((i % kOzRows) >> 3) * 512 + r * 16;
   const double2* row = src + int64_t(i) * si;
-  for (int o = threadIdx.x >> 3; o < nkt * 8; o += 32) {
-    uint32_t w[12][4];
+  for (int o = threadIdx.x >> 3; o < nkt * (kOzK / 8); o += 32) {
+    uint32_t wr[6][4], wi[6][4], wn[6][4];
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
       const int k0 = o * 8 + u;
@@ -306,24 +337,95 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
       digits(v1.y, e, S, i1);
 #pragma unroll
       for (int s = 0; s < 6; ++s) {
-        w[2 * s][u / 2] = bf16_bits(r0[s]) | (bf16_bits(r1[s]) << 16);
-        w[2 * s + 1][u / 2] = bf16_bits(i0[s]) | (bf16_bits(i1[s]) << 16);
+        wr[s][u / 2] = bf16_bits(r0[s]) | (bf16_bits(r1[s]) << 16);
+        wi[s][u / 2] = bf16_bits(i0[s]) | (bf16_bits(i1[s]) << 16);
+        wn[s][u / 2] = bf16_bits(-r0[s]) | (bf16_bits(-r1[s]) << 16);
       }
     }
-    uint8_t* p = rowbase + int64_t(o >> 3) * planes * TB + (o & 7) * 128;
+    uint8_t* p = rowbase + int64_t(o >> 2) * S * slice + (o & 3) * 128;
 #pragma unroll
-    for (int q = 0; q < 12; ++q)
-      if (q < planes) *reinterpret_cast<uint4*>(p + q * TB) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    for (int s = 0; s < 6; ++s)
+      if (s < S) {
+        uint8_t* q = p + s * slice;
+        *reinterpret_cast<uint4*>(q) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+        *reinterpret_cast<uint4*>(q + kBlk) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+        if (isA) *reinterpret_cast<uint4*>(q + 2 * kBlk) = make_uint4(wn[s][0], wn[s][1], wn[s][2], wn[s][3]);
+      }
   }
 }
 
-// Output tiles of the Schur update that touch the lower triangle of the
-// m_p x m_p trailing block: for row tile mt, column tiles 0 .. 4 mt + 3.
-__host__ __device__ inline int schur_tiles(int mp) {
-  const int nmt = (mp + kOzM - 1) / kOzM, nnt = (mp + kOzN - 1) / kOzN;
-  int t = 0;
-  for (int mt = 0; mt < nmt; ++mt) t += min(4 * mt + 4, nnt);
-  return t;
+// Real operands of the Schur update (LDL^T of H - sigma S for inertia
+// counts): A = L[S,P] rows (tiles of 128 rows), B = W[S,P] rows (tiles of 64
+// rows), K = the panel's bb columns; one 16-byte word per slice and row
+// octet, in the same core-matrix layout (a slice of A is two 64-row blocks,
+// one of B is one block). Grid and passes as k_oz_slice.
+__global__ void __launch_bounds__(256) k_oz_slice_real(const double* __restrict__ F, DevFronts fr,
+                                                       const int32_t* __restrict__ fronts, int p0, int b, int S,
+                                                       int groupsA, OzScratch oz) {
+  PanelDims d;
+  if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
+  const int pole = blockIdx.z;
+  const bool isA = int(blockIdx.x) < groupsA;
+  const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
+  const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
+  const int rows = d.mp, K = d.bb, nkt = ceil_div(K, kOzK);
+  const double* src = isA ? F + fo + d.q0 + int64_t(d.m) * p0 : F + fo + p0 + int64_t(d.m) * d.q0;
+  const int64_t si = isA ? 1 : d.m, sk = isA ? d.m : 1;
+  const int R = isA ? 2 * kOzRows : kOzRows;
+  const int slice = isA ? 2 * kBlk : kBlk;
+  uint8_t* dst = isA ? oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f]
+                     : oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f];
+  int* ex = isA ? oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f]
+                : oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];
+  if (g * 8 >= rows) return;
+
+  __shared__ int s_e[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const int i = g * 8 + warp;
+    uint32_t mx = 0;
+    if (i < rows)
+      for (int k = lane; k < K; k += 32)
+        mx = max(mx, uint32_t(__double2hiint(src[int64_t(i) * si + int64_t(k) * sk])) & 0x7FFFFFFFu);
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    int e = 0;
+    if (mx >= 0x7FF00000u)
+      e = kNanExp;
+    else if (mx != 0)
+      e = int(mx >> 20) - 1022;
+    if (lane == 0) {
+      s_e[warp] = e;
+      if (i < rows) ex[i] = e;
+    }
+  }
+  __syncthreads();
+
+  const int r = threadIdx.x & 7;
+  const int i = g * 8 + r;
+  const int e = s_e[r];
+  uint8_t* rowbase = dst + int64_t(i / R) * nkt * S * slice + ((i % R) >> 3) * 512 + r * 16;
+  const double* row = src + int64_t(i) * si;
+  for (int o = threadIdx.x >> 3; o < nkt * (kOzK / 8); o += 32) {
+    uint32_t w[6][4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const int k0 = o * 8 + u;
+      double v0 = 0.0, v1 = 0.0;
+      if (i < rows) {
+        if (k0 < K) v0 = row[int64_t(k0) * sk];
+        if (k0 + 1 < K) v1 = row[int64_t(k0 + 1) * sk];
+      }
+      int d0[6], d1[6];
+      digits(v0, e, S, d0);
+      digits(v1, e, S, d1);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) w[q][u / 2] = bf16_bits(d0[q]) | (bf16_bits(d1[q]) << 16);
+    }
+    uint8_t* p = rowbase + int64_t(o >> 2) * S * slice + (o & 3) * 128;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if (q < S) *reinterpret_cast<uint4*>(p + q * slice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  }
 }
 
 // Where a wait ran out: site (1..8) + 16 * (K tile mod 64).
@@ -332,13 +434,16 @@ __device__ __forceinline__ void record_fail(int* s_fail, int site, int kt) {
 }
 
 // ---------------------------------------------------------------- GEMM
-// MODE 0, Takahashi: one CTA per (128-row tile of S, 32-column tile of P,
-//   front, pole); Y[S,P] = -A B^T with A = Y[S,S], B = L[S,P]^T, and mirror.
-// MODE 1, Schur: one CTA per lower-triangle output tile (128 x 32) of the
-//   trailing block; F[S,S] -= A B^T with A = L[S,P], B = W[S,P] (K = bb).
+// MODE 0, Takahashi: one CTA per (64-row tile of S, front, pole); the panel's
+//   bb <= 64 columns are one N tile. Y[S,P] = -A B^T with A = Y[S,S],
+//   B = L[S,P]^T, and its mirror Y[P,S].
+// MODE 1, Schur: one CTA per lower-triangle output tile (64 x 64 complex) of
+//   the trailing block; F[S,S] -= A B^T with A = L[S,P], B = W[S,P] (K = bb).
+// CPLX = false (MODE 1 only): the real Schur update of the inertia LDL^T,
+//   128 x 64 output tiles, one MMA per slice pair and K step.
 // Warps 0-7 epilogue, warp 8 producer, warp 9 MMA issuer (and TMEM owner).
-template <int MODE>
-__global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict__ Y, DevFronts fr,
+template <int MODE, bool CPLX>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ Yv, DevFronts fr,
                                                              const int32_t* __restrict__ fronts, int p0, int b,
                                                              int S, OzScratch oz) {
   extern __shared__ __align__(128) uint8_t osm[];
@@ -346,42 +451,65 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
   __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
+  __shared__ int s_ea[2 * kOzRows], s_eb[kOzRows];  // exponents of the tile's rows of A and of B
+  constexpr int TR = CPLX ? kOzRows : 2 * kOzRows;     // output rows per tile
+  constexpr int SA = CPLX ? kSliceA : 2 * kBlk;        // bytes of one slice of A (one K tile)
+  constexpr int SB = CPLX ? kSliceB : kBlk;            // bytes of one slice of B (one K tile)
   PanelDims d;
   if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
   if (*static_cast<volatile int*>(oz.fail)) return;  // an earlier CTA gave up: the result is void anyway
   int mt, nt, nkt;
   if (MODE == 0) {
-    const int nmt = (d.mp + kOzM - 1) / kOzM, nnt = (d.bb + kOzN - 1) / kOzN;
-    if (int(blockIdx.x) >= nmt * nnt) return;
-    mt = blockIdx.x / nnt;
-    nt = blockIdx.x % nnt;
-    nkt = (d.mp + kOzK - 1) / kOzK;
+    if (int(blockIdx.x) >= ceil_div(d.mp, kOzRows)) return;
+    mt = blockIdx.x;
+    nt = 0;
+    nkt = ceil_div(d.mp, kOzK);
+  } else if (CPLX) {
+    // lower-triangle tiles in row order: tile t of row tile mt has nt = t - mt (mt + 1) / 2
+    const int t = blockIdx.x;
+    const int nmt = ceil_div(d.mp, kOzRows);
+    if (t >= nmt * (nmt + 1) / 2) return;
+    mt = int((sqrtf(8.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
+    while (mt * (mt + 1) / 2 > t) --mt;
+    while ((mt + 1) * (mt + 2) / 2 <= t) ++mt;
+    nt = t - mt * (mt + 1) / 2;
+    nkt = ceil_div(d.bb, kOzK);
   } else {
-    const int nmt = (d.mp + kOzM - 1) / kOzM, nnt = (d.mp + kOzN - 1) / kOzN;
+    // 128-row tiles mt, 64-column tiles nt = 0 .. min(2 mt + 1, nnt - 1)
+    const int nmt = ceil_div(d.mp, 2 * kOzRows), nnt = ceil_div(d.mp, kOzRows);
     int t = blockIdx.x;
     mt = -1;
-    for (int q = 0; q < nmt; ++q) {
-      const int c = min(4 * q + 4, nnt);
+    for (int r = 0; r < nmt; ++r) {
+      const int c = min(2 * r + 2, nnt);
       if (t < c) {
-        mt = q;
+        mt = r;
         break;
       }
       t -= c;
     }
     if (mt < 0) return;
     nt = t;
-    nkt = 1;
+    nkt = ceil_div(d.bb, kOzK);
   }
   const int pole = blockIdx.z;
-  const int planes = 2 * S;
-  const int nchunks = (nkt + kOzChunk - 1) / kOzChunk;
-  uint8_t* sA = osm;                          // kSlotsA x (re, im) planes of one A slice
-  uint8_t* sB = osm + kSlotsA * 2 * kTileA;   // kSlotsB x 2S planes of B
-  const uint8_t* gA = oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f] + int64_t(mt) * nkt * planes * kTileA;
-  const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + int64_t(nt) * nkt * planes * kTileB;
+  const int nchunks = ceil_div(nkt, kOzChunk);
+  uint8_t* sA = osm;                         // kSlotsA x one slice of A (Ar, Ai, -Ar; or Ar)
+  uint8_t* sB = osm + kSlotsA * kSliceA;     // kSlotsB x S slices of B (Br, Bi; or Br)
+  const uint8_t* gA = oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f] + int64_t(mt) * nkt * S * SA;
+  const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + int64_t(nt) * nkt * S * SB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* fail = &s_fail;
 
+  if (threadIdx.x < TR + kOzRows) {  // staged once, read by the epilogue without global round trips
+    if (threadIdx.x < TR) {
+      const int i = mt * TR + threadIdx.x;
+      s_ea[threadIdx.x] = i < d.mp ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
+    } else {
+      const int t = threadIdx.x - TR;
+      const int j = nt * kOzRows + t;
+      s_eb[t] = j < (MODE == 1 ? d.mp : d.bb) ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + j] : 0;
+    }
+  }
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int j = 0; j < kSlotsA; ++j) {
@@ -407,11 +535,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
 
-  // epilogue state: rows of TMEM lane quarter q, columns 16 h .. 16 h + 15
+  // epilogue state: TMEM lanes 32 q .. 32 q + 31 (real rows; rows < 64 are
+  // real parts, rows >= 64 imaginary parts), columns 32 h .. 32 h + 31
   const int q = warp & 3, h = (warp >> 2) & 1;
-  double dre[16], dim[16];
+  unsigned long long acc[32];
+  double dacc[32];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) dre[c] = dim[c] = 0.0;
+  for (int c = 0; c < 32; ++c) {
+    acc[c] = 0ull;
+    dacc[c] = 0.0;
+  }
+  const bool multi = MODE == 0 && nchunks > kOzFlush;  // more than one 64-bit partial sum (K > 2048)
 
   if (warp == kEpiWarps) {
     if (lane == 0) {  // ---- producer
@@ -422,8 +556,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
           record_fail(&s_fail, 1, kt);
           break;
         }
-        bar_expect(smem_u32(&full_b[sb]), uint32_t(planes * kTileB));
-        bulk_load(smem_u32(sB + sb * planes * kTileB), gB + int64_t(kt) * planes * kTileB, uint32_t(planes * kTileB),
+        bar_expect(smem_u32(&full_b[sb]), uint32_t(S * SB));
+        bulk_load(smem_u32(sB + sb * S * kSliceB), gB + int64_t(kt) * S * SB, uint32_t(S * SB),
                   smem_u32(&full_b[sb]));
         ++nbf;
         bool ok = true;
@@ -434,8 +568,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
             ok = false;
             break;
           }
-          bar_expect(smem_u32(&full_a[sa]), uint32_t(2 * kTileA));
-          bulk_load(smem_u32(sA + sa * 2 * kTileA), gA + (int64_t(kt) * planes + 2 * s) * kTileA, uint32_t(2 * kTileA),
+          bar_expect(smem_u32(&full_a[sa]), uint32_t(SA));
+          bulk_load(smem_u32(sA + sa * kSliceA), gA + (int64_t(kt) * S + s) * SA, uint32_t(SA),
                     smem_u32(&full_a[sa]));
           ++na;
         }
@@ -471,22 +605,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t aR = smem_u32(sA + sa * 2 * kTileA), aI = aR + kTileA;
-          // accumulators: (diagonal D = s + t, part) at column ((D - 2) * 2 + part) * 32
+          const uint32_t a1 = smem_u32(sA + sa * kSliceA), a2 = a1 + kBlk;  // [Ar; Ai], [Ai; -Ar]
           for (int t = 1; s + t <= S + 1; ++t) {
-            const uint32_t acc_re = tmem + uint32_t(((s + t - 2) * 2 + 0) * kOzN);
-            const uint32_t acc_im = tmem + uint32_t(((s + t - 2) * 2 + 1) * kOzN);
-            const uint32_t bR = smem_u32(sB + sb * planes * kTileB + (2 * (t - 1)) * kTileB), bI = bR + kTileB;
+            const uint32_t acc_d = tmem + uint32_t((s + t - 2) * 64);  // diagonal D = s + t
+            const uint32_t br = smem_u32(sB + sb * S * kSliceB + (t - 1) * SB), bi = br + kBlk;
 #pragma unroll
             for (int ks = 0; ks < kOzK / 16; ++ks) {
               const uint32_t ko = uint32_t(ks * 256);  // two core matrices along K
               // the first product into each accumulator of a chunk overwrites
               // it: for diagonal D that is the pair (1, D - 1) at ks = 0
-              const uint32_t acc = (in_chunk == 0 && ks == 0 && s == 1) ? 0u : 1u;
-              mma(acc_re, sdesc(aR + ko), sdesc(bR + ko), id_pos, acc);
-              mma(acc_re, sdesc(aI + ko), sdesc(bI + ko), id_neg, 1u);
-              mma(acc_im, sdesc(aR + ko), sdesc(bI + ko), id_pos, acc);
-              mma(acc_im, sdesc(aI + ko), sdesc(bR + ko), id_pos, 1u);
+              const uint32_t first = (in_chunk == 0 && ks == 0 && s == 1) ? 0u : 1u;
+              mma(acc_d, sdesc(a1 + ko), sdesc(br + ko), id_pos, first);
+              if (CPLX) mma(acc_d, sdesc(a2 + ko), sdesc(bi + ko), id_neg, 1u);
             }
           }
           mma_commit(smem_u32(&empty_a[sa]));
@@ -500,10 +630,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
       mma_commit(smem_u32(&mma_done));
       if (!bar_wait_all(smem_u32(&mma_done), 0)) record_fail(&s_fail, 7, 0);
     }
-  } else {  // ---- epilogue: exact FP32 integers -> 64-bit integers -> FP64
-    unsigned long long pre[16], pim[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) pre[c] = pim[c] = 0ull;
+  } else {  // ---- epilogue: exact FP32 integers -> 64-bit integers
     int pending = 0;
     for (int ch = 0; ch < nchunks; ++ch) {
       bool ok = true;
@@ -517,9 +644,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
       for (int D = 2; D <= S + 1; ++D) {
         const int sh = 7 * (S + 1 - D);
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
+        for (int half = 0; half < 2; ++half) {
           uint32_t v[16];
-          const uint32_t addr = tmem + (uint32_t(q * 32) << 16) + uint32_t(((D - 2) * 2 + part) * kOzN + h * 16);
+          const uint32_t addr = tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + half * 16);
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
               "[%16];"
@@ -529,25 +656,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
               : "r"(addr));
           asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const unsigned long long t =
+          for (int c = 0; c < 16; ++c)
+            acc[half * 16 + c] +=
                 static_cast<unsigned long long>(static_cast<long long>(__float2int_rn(__uint_as_float(v[c])))) << sh;
-            if (part == 0)
-              pre[c] += t;
-            else
-              pim[c] += t;
-          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) bar_arrive(smem_u32(&acc_empty));
-      if (++pending == kOzFlush || ch == nchunks - 1) {
+      if (multi && (++pending == kOzFlush || ch == nchunks - 1)) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          dre[c] += double(static_cast<long long>(pre[c]));
-          dim[c] += double(static_cast<long long>(pim[c]));
-          pre[c] = pim[c] = 0ull;
+        for (int c = 0; c < 32; ++c) {
+          dacc[c] += i64_scaled(static_cast<long long>(acc[c]), 0);
+          acc[c] = 0ull;
         }
         pending = 0;
       }
@@ -559,33 +680,47 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
     if (threadIdx.x == 0)  // where the wait gave up: mode, site + 16 * K tile, tile
       atomicMax(oz.fail, 1 + (MODE << 30) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
   } else if (warp < kEpiWarps) {
-    const int i = mt * kOzM + q * 32 + lane;  // row of the trailing block
+    // complex: lanes 0-63 hold real parts, 64-127 imaginary parts of the
+    // tile's 64 complex rows; real: lane = row of the 128-row tile
+    const int ri = CPLX ? (q & 1) * 32 + lane : q * 32 + lane;
+    const int part = CPLX ? q >> 1 : 0;
+    const int i = mt * TR + ri;  // row of the trailing block
     if (i < d.mp) {
-      const int ea = oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i];
-      double2* Yb = Y + int64_t(pole) * fr.pool + fr.off[d.f];
+      const int ea = s_ea[ri];
+      constexpr int ES = CPLX ? 2 : 1;  // doubles per element
+      double* Yb = static_cast<double*>(Yv) + ES * (int64_t(pole) * fr.pool + fr.off[d.f]) + part;
+      // Schur: the old values of 16 columns are loaded before any of them is
+      // stored, so that their loads are in flight together
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int j = nt * kOzN + h * 16 + c;
-        const bool in = MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb);
-        if (in) {
-          const int eb = oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + j];
-          double2 v;
-          if (ea == kNanExp || eb == kNanExp) {
-            v = make_double2(__longlong_as_double(0x7FF8000000000000LL), __longlong_as_double(0x7FF8000000000000LL));
-          } else {
-            const int sc = ea + eb - 7 * (S + 1);
-            v = make_double2(ldexp(dre[c], sc), ldexp(dim[c], sc));
+      for (int c0 = 0; c0 < 32; c0 += 16) {
+        double old[16];
+        if (MODE == 1) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int j = nt * kOzRows + h * 32 + c0 + c;
+            old[c] = (j <= i && j < d.mp) ? Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] : 0.0;
           }
-          if (MODE == 1) {
-            double2* dst = Yb + (d.q0 + i) + int64_t(d.m) * (d.q0 + j);
-            double2 o = *dst;
-            o.x -= v.x;
-            o.y -= v.y;
-            *dst = o;
-          } else {
-            const double2 nv = make_double2(-v.x, -v.y);
-            Yb[(d.q0 + i) + int64_t(d.m) * (p0 + j)] = nv;
-            Yb[(p0 + j) + int64_t(d.m) * (d.q0 + i)] = nv;
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int j = nt * kOzRows + h * 32 + c0 + c;
+          const bool in = MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb);
+          if (in) {
+            const int eb = s_eb[h * 32 + c0 + c];
+            const int sc = ea + eb - 7 * (S + 1);
+            double v;
+            if (ea == kNanExp || eb == kNanExp)
+              v = __longlong_as_double(0x7FF8000000000000LL);
+            else if (multi)
+              v = ldexp(dacc[c0 + c], sc);
+            else
+              v = i64_scaled(static_cast<long long>(acc[c0 + c]), sc);
+            if (MODE == 1) {
+              Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] = old[c] - v;
+            } else {
+              Yb[ES * ((d.q0 + i) + int64_t(d.m) * (p0 + j))] = -v;
+              Yb[ES * ((p0 + j) + int64_t(d.m) * (d.q0 + i))] = -v;
+            }
           }
         }
       }
@@ -599,18 +734,66 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(double2* __restrict
 
 }  // namespace
 
-size_t oz_smem_bytes(int S) { return size_t(kSlotsA) * 2 * kTileA + size_t(kSlotsB) * 2 * S * kTileB; }
+size_t oz_smem_bytes(int S) { return size_t(kSlotsA) * kSliceA + size_t(kSlotsB) * S * kSliceB; }
 
-int oz_tile_bytes_A() { return kTileA; }
-int oz_tile_bytes_B() { return kTileB; }
-
-cudaError_t oz_configure(int S) {
-  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(oz_smem_bytes(S)));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_oz_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(oz_smem_bytes(S)));
+// Scratch bytes of one front (per pole) whose first panel leaves mp rows
+// below it, for both phases: Takahashi A = Y[S,S] (mp x mp), B = L[S,P]
+// (bb x mp); Schur A = L[S,P] (mp x bb), B = W[S,P] (mp x bb).
+int64_t oz_front_bytes_A(int64_t mp, int b, int S) {
+  const int64_t rt = (mp + kOzRows - 1) / kOzRows;
+  return rt * std::max<int64_t>((mp + kOzK - 1) / kOzK, (b + kOzK - 1) / kOzK) * S * kSliceA;
 }
 
-int oz_schur_tiles(int mp) { return schur_tiles(mp); }
+int64_t oz_front_bytes_B(int64_t mp, int b, int S) {
+  const int64_t tak = ((b + kOzRows - 1) / kOzRows) * ((mp + kOzK - 1) / kOzK);
+  const int64_t sch = ((mp + kOzRows - 1) / kOzRows) * ((b + kOzK - 1) / kOzK);
+  return std::max(tak, sch) * S * kSliceB;
+}
+
+cudaError_t oz_configure(int S) {
+  const int smem = int(oz_smem_bytes(S));
+  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+int64_t oz_front_bytes_A_real(int64_t mp, int b, int S) {
+  return ((mp + 2 * kOzRows - 1) / (2 * kOzRows)) * ((b + kOzK - 1) / kOzK) * S * (2 * kBlk);
+}
+
+int64_t oz_front_bytes_B_real(int64_t mp, int b, int S) {
+  return ((mp + kOzRows - 1) / kOzRows) * ((b + kOzK - 1) / kOzK) * S * kBlk;
+}
+
+int oz_schur_tiles_real(int mp) {
+  const int nmt = ceil_div(mp, 2 * kOzRows), nnt = ceil_div(mp, kOzRows);
+  int t = 0;
+  for (int r = 0; r < nmt; ++r) t += min(2 * r + 2, nnt);
+  return t;
+}
+
+void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
+                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
+  if (nfronts <= 0 || max_mp <= 0) return;
+  const int groups = (max_mp + 7) / 8;
+  dim3 g(2 * groups, nfronts, nb);
+  k_oz_slice_real<<<g, 256, 0, st>>>(F, fr, fronts, p0, b, S, groups, oz);
+}
+
+void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
+                               int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
+  if (nfronts <= 0 || max_tiles <= 0) return;
+  dim3 gg(max_tiles, nfronts, nb);
+  k_oz_gemm<1, false><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
+}
+
+int oz_offdiag_tiles(int mp) { return ceil_div(mp, kOzRows); }
+
+int oz_schur_tiles(int mp) {
+  const int nmt = ceil_div(mp, kOzRows);
+  return nmt * (nmt + 1) / 2;
+}
 
 void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
                            int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
@@ -624,7 +807,7 @@ void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts
                           int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
   if (nfronts <= 0 || max_tiles <= 0) return;
   dim3 gg(max_tiles, nfronts, nb);
-  k_oz_gemm<1><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
+  k_oz_gemm<1, true><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
 }
 
 void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts,
@@ -640,7 +823,7 @@ void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fron
                             int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
   if (nfronts <= 0 || max_tiles <= 0) return;
   dim3 gg(max_tiles, nfronts, nb);
-  k_oz_gemm<0><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(Y, fr, fronts, p0, b, S, oz);
+  k_oz_gemm<0, true><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(Y, fr, fronts, p0, b, S, oz);
 }
 
 }  // namespace pexsi

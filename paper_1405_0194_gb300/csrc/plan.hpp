@@ -113,6 +113,10 @@ struct pexsi_plan {
   int oz_slices = 0;
   int64_t *d_ozA_off = nullptr, *d_ozB_off = nullptr, *d_exA_off = nullptr, *d_exB_off = nullptr;
   int64_t ozA_stride = 0, ozB_stride = 0, exA_stride = 0, exB_stride = 0;
+  // the same for the real Schur update of the inertia factorisation (twice
+  // as many batch members share the scratch; exponents use the offsets above)
+  int64_t *d_ozA_off_r = nullptr, *d_ozB_off_r = nullptr;
+  int64_t ozA_stride_r = 0, ozB_stride_r = 0;
   std::vector<pexsi::Level> levels;
   pexsi::FlopCounts flops;
   int trace_blocks = 256;

@@ -1,6 +1,8 @@
 """Split-precision path (bf16 Ozaki slices on the tcgen05 tensor cores for the
-Takahashi GEMM) against the FP64 oracle: max |Delta DM| <= 1e-7, the stated
-tolerance of the split path; errors printed per slice count."""
+Schur update and the Takahashi GEMM) against the FP64 oracle: max |Delta DM|
+<= 1e-7, the stated tolerance of the split path; errors printed per slice
+count. Inertia counts through the split real Schur update must equal the
+oracle's eigenvalue counts exactly."""
 import numpy as np
 import pytest
 
@@ -45,6 +47,25 @@ def test_split_dm_within_tolerance(cases, name):
     assert dtr <= 1e-8
     assert np.max(np.abs(edm - edm0)) <= TOL_SPLIT * max(1.0, np.max(np.abs(edm0)))
     assert np.max(np.abs(fdm - fdm0)) <= TOL_SPLIT * max(1.0, np.max(np.abs(fdm0)))
+
+
+@pytest.mark.parametrize("name", ["chain64", "fluid24", "sheet8"])
+def test_split_inertia_counts_exact(cases, name):
+    """Sylvester's law through the split real LDL^T: counts equal the number of
+    generalised eigenvalues below each shift (shifts kept 1e-6 away from every
+    eigenvalue, so that the count is well defined at the split path's error)."""
+    s, mu, dE = cases[name]
+    lam = dense.eig_pencil(s.n, s.colptr, s.rowind, s.H, s.S)[0]
+    shifts = []
+    for x in mu + np.linspace(-0.6, 0.6, 13):
+        while np.min(np.abs(lam - x)) < 1e-6:
+            x += 3.7e-6
+        shifts.append(x)
+    want = np.array([np.count_nonzero(lam < x) for x in shifts])
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(split_slices=6))
+    got = px.pexsi_inertia(plan, s.H, s.S, np.array(shifts))
+    px.pexsi_plan_destroy(plan)
+    np.testing.assert_array_equal(got, want)
 
 
 def test_split_selinv_error_falls_with_slices(cases):
