@@ -299,25 +299,38 @@ __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* 
   __syncthreads();
   int k = 0;
   while (k < n) {
-    if (threadIdx.x == 0) {
-      double akk = fabs(Bm[k * ld + k]);
+    if (threadIdx.x < 32) {  // pivot choice by warp 0: same decisions as a serial scan (first maximum)
+      const int lane = threadIdx.x;
       double lam = 0.0;
       int r = k;
-      for (int i = k + 1; i < n; ++i)
-        if (fabs(Bm[i * ld + k]) > lam) { lam = fabs(Bm[i * ld + k]); r = i; }
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        const double a = fabs(Bm[i * ld + k]);
+        if (a > lam) { lam = a; r = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ol = __shfl_xor_sync(0xffffffffu, lam, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+        if (ol > lam || (ol == lam && orr < r)) { lam = ol; r = orr; }
+      }
+      const double akk = fabs(Bm[k * ld + k]);
       int kind = 1, swapr = k;
-      if (lam == 0.0 && akk == 0.0) { *singular = true; kind = 1; }
+      bool sing = false;
+      if (lam == 0.0 && akk == 0.0) { sing = true; kind = 1; }
       else if (akk >= alpha * lam) { kind = 1; }
       else {
         double sig = 0.0;
-        for (int j = k; j < n; ++j)
+        for (int j = k + lane; j < n; j += 32)
           if (j != r) sig = fmax(sig, fabs(Bm[r * ld + j]));
+        for (int o = 16; o > 0; o >>= 1) sig = fmax(sig, __shfl_xor_sync(0xffffffffu, sig, o));
         if (akk * sig >= alpha * lam * lam) kind = 1;
         else if (fabs(Bm[r * ld + r]) >= alpha * sig) { kind = 1; swapr = r; }
         else { kind = 2; swapr = r; }
       }
-      s_piv[0] = kind;
-      s_piv[1] = swapr;
+      if (lane == 0) {
+        s_piv[0] = kind;
+        s_piv[1] = swapr;
+        if (sing) *singular = true;
+      }
     }
     __syncthreads();
     const int kind = s_piv[0], sr = s_piv[1];
@@ -375,19 +388,20 @@ template <typename T>
 __global__ void k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
                            DevStatus st, int count_inertia) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Aug = reinterpret_cast<T*>(smem_raw);  // bb x (2 bb), row-major, stride 2b+1
+  T* Aug = reinterpret_cast<T*>(smem_raw);  // bb x bb, row-major, stride b+1, inverted in place
   const int f = fronts[blockIdx.x];
   const int pb = blockIdx.y;
   const int s = fr.s[f], m = fr.m[f];
   if (p0 >= s) return;
   const int bb = min(b, s - p0);
-  const int ld = 2 * b + 1;
+  const int ld = b + 1;
   T* Fd = F + int64_t(pb) * fr.pool + fr.off[f] + p0 + int64_t(m) * p0;
   __shared__ double s_max;
   __shared__ int s_piv;
   __shared__ double s_pmin;
   __shared__ bool s_bad;
   __shared__ T s_fac[64];
+  __shared__ int s_perm[64];
   if (threadIdx.x == 0) { s_max = 0.0; s_pmin = DBL_MAX; s_bad = false; }
   __syncthreads();
   double lmax = 0.0;
@@ -395,7 +409,6 @@ __global__ void k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __res
     int i = idx % bb, j = idx / bb;
     T v = (i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
     Aug[i * ld + j] = v;
-    Aug[i * ld + bb + j] = (i == j) ? one_of(T()) : zero_of(T());
     lmax = fmax(lmax, absv(v));
   }
   // block max |entry| for the pivot ratio
@@ -445,25 +458,39 @@ __global__ void k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __res
     }
     __syncthreads();
     const int pr = s_piv;
+    if (threadIdx.x == 0) s_perm[k] = pr;
     if (pr != k)
-      for (int j = threadIdx.x; j < 2 * bb; j += blockDim.x) {
+      for (int j = threadIdx.x; j < bb; j += blockDim.x) {
         T t = Aug[k * ld + j]; Aug[k * ld + j] = Aug[pr * ld + j]; Aug[pr * ld + j] = t;
       }
     __syncthreads();
+    // in-place Gauss-Jordan step: column k keeps the multipliers' negatives
+    // over the pivot, row k is scaled by the pivot's reciprocal
     const T inv = s_bad ? zero_of(T()) : recipv(Aug[k * ld + k]);
-    for (int j = k + threadIdx.x; j < 2 * bb; j += blockDim.x) Aug[k * ld + j] = mulv(Aug[k * ld + j], inv);
     for (int i = threadIdx.x; i < bb; i += blockDim.x) s_fac[i] = Aug[i * ld + k];
     __syncthreads();
-    const int w = 2 * bb - k - 1;
-    for (int idx = threadIdx.x; idx < bb * w; idx += blockDim.x) {
-      int i = idx / w, j = k + 1 + idx % w;
-      if (i != k) Aug[i * ld + j] = subv(Aug[i * ld + j], mulv(s_fac[i], Aug[k * ld + j]));
+    for (int j = threadIdx.x; j < bb; j += blockDim.x) Aug[k * ld + j] = (j == k) ? inv : mulv(Aug[k * ld + j], inv);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+      const int i = idx / bb, j = idx % bb;
+      if (i == k) continue;
+      Aug[i * ld + j] = (j == k) ? subv(zero_of(T()), mulv(s_fac[i], inv))
+                                 : subv(Aug[i * ld + j], mulv(s_fac[i], Aug[k * ld + j]));
     }
+    __syncthreads();
+  }
+  // the row interchanges become column interchanges of the inverse, undone in reverse order
+  for (int k = bb - 1; k >= 0; --k) {
+    const int pr = s_perm[k];
+    if (pr != k)
+      for (int i = threadIdx.x; i < bb; i += blockDim.x) {
+        T t = Aug[i * ld + k]; Aug[i * ld + k] = Aug[i * ld + pr]; Aug[i * ld + pr] = t;
+      }
     __syncthreads();
   }
   for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
     int i = idx % bb, j = idx / bb;
-    Fd[i + int64_t(m) * j] = Aug[i * ld + bb + j];
+    Fd[i + int64_t(m) * j] = Aug[i * ld + j];
   }
   if (threadIdx.x == 0) {
     double ratio = s_max > 0 ? s_pmin / s_max : 0.0;
@@ -739,7 +766,7 @@ template <typename T>
 void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                      const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
   if (nfronts <= 0) return;
-  size_t smem = sizeof(T) * size_t(b) * (2 * b + 1) + (count_inertia ? sizeof(double) * b * b : 0);
+  size_t smem = sizeof(T) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
   k_diag_inv<T><<<grid, 256, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
 }
@@ -811,8 +838,8 @@ void launch_traces(const double* dm, const double* edm, const double* fdm, const
 }
 
 cudaError_t configure_kernels(int b) {
-  size_t need_c = sizeof(double2) * size_t(b) * (2 * b + 1);
-  size_t need_r = sizeof(double) * size_t(b) * (2 * b + 1) + sizeof(double) * b * b;
+  size_t need_c = sizeof(double2) * size_t(b) * (b + 1);
+  size_t need_r = sizeof(double) * size_t(b) * (b + 1) + sizeof(double) * b * b;
   cudaError_t e = cudaFuncSetAttribute(k_diag_inv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_c));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_r));
