@@ -184,13 +184,21 @@ PanelWork panel_work(const Level& lv, int p0, int b, double es, double fma_fl) {
     w.dpart_fl += fma_fl * bb * bb * mp;
     w.dpart_by += (2 * mp * bb + nt * bb * bb) * es;
     w.dred_by += (nt + 2) * bb * bb * es;
-    w.slice_off_by += (mp * mp + mp * bb) * (es + 4.0 * 6);
+    w.slice_off_by += mp * mp * es + mp * bb * (es + 4.0 * 6);  // A: exponents only; B: slices
     w.slice_schur_by += 2 * mp * bb * (es + 4.0 * 6);
   }
   return w;
 }
 
 Profiler g_off;  // a profiler that is never switched on
+
+// Split-precision scratch of a workspace: the complex layout (poles) or the
+// real one (inertia shifts, twice as many batch members).
+OzScratch split_scratch(const pexsi_plan* p, Workspace& ws, bool real) {
+  return OzScratch{ws.ozA, real ? p->d_ozA_off_r : p->d_ozA_off, real ? p->ozA_stride_r : p->ozA_stride,
+                   ws.ozB, real ? p->d_ozB_off_r : p->d_ozB_off, real ? p->ozB_stride_r : p->ozB_stride,
+                   ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+}
 
 // Factor the batch in F (assembled), leaves to root.
 template <typename T>
@@ -215,24 +223,40 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
       launch_diag_inv<T>(F, fr, dfr, g.nact, p0, b, sh, status, count, st);
       pf.end(a, P_DIAG, st, nb * w.diag_fl, nb * w.diag_by);
       a = pf.begin(st);
-      launch_panel_solve<T>(F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
-      pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
+      const int S = p->oz_slices;
+      // executed tensor flops per algorithmic flop: S(S+1)/2 slice pairs, 4 real
+      // products per complex multiply-add (8 flops) or 1 per real one (2 flops)
+      const double tens = S * (S + 1) / 2.0;
+      if (S > 0 && sizeof(T) == sizeof(double2)) {
+        OzScratch oz = split_scratch(p, ws, false);
+        launch_oz_panel(reinterpret_cast<double2*>(F), fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, false);
+        pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by / 2);
+        a = pf.begin(st);
+        launch_oz_panel(reinterpret_cast<double2*>(F), fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, true);
+        pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by, 1, nb * w.panel_fl * tens);
+      } else if (S > 0) {
+        OzScratch oz = split_scratch(p, ws, true);
+        launch_oz_panel_real(reinterpret_cast<double*>(F), fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, false);
+        pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by / 2);
+        a = pf.begin(st);
+        launch_oz_panel_real(reinterpret_cast<double*>(F), fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, true);
+        pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by, 1, nb * w.panel_fl * tens);
+      } else {
+        launch_panel_solve<T>(F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
+        pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
+      }
       a = pf.begin(st);
       if (sizeof(T) == sizeof(double2) && p->oz_slices > 0) {
-        OzScratch oz{ws.ozA, p->d_ozA_off, p->ozA_stride, ws.ozB, p->d_ozB_off, p->ozB_stride,
-                     ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+        OzScratch oz = split_scratch(p, ws, false);
         double2* Fz = reinterpret_cast<double2*>(F);
-        const int S = p->oz_slices;
         launch_oz_slice_schur(Fz, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
         pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by);
         a = pf.begin(st);
         launch_oz_gemm_schur(Fz, fr, dfr, g.nact, g.oz_schur, p0, b, S, oz, sh.nb, st);
         pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by, 1, nb * w.schur_fl * 4.0 * S * (S + 1) / 2 / 8.0 * 2.0);
       } else if (sizeof(T) == sizeof(double) && p->oz_slices > 0) {
-        OzScratch oz{ws.ozA, p->d_ozA_off_r, p->ozA_stride_r, ws.ozB, p->d_ozB_off_r, p->ozB_stride_r,
-                     ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+        OzScratch oz = split_scratch(p, ws, true);
         double* Fr = reinterpret_cast<double*>(F);
-        const int S = p->oz_slices;
         launch_oz_slice_schur_real(Fr, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
         pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by);
         a = pf.begin(st);
@@ -265,13 +289,12 @@ void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Pro
       PanelWork w = pf.on ? panel_work(lv, p0, b, es, 8.0) : PanelWork();
       a = pf.begin(st);
       if (p->oz_slices > 0) {
-        OzScratch oz{ws.ozA, p->d_ozA_off, p->ozA_stride, ws.ozB, p->d_ozB_off, p->ozB_stride,
-                     ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+        OzScratch oz = split_scratch(p, ws, false);
         const int S = p->oz_slices;
-        launch_oz_slice_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
+        launch_oz_takahashi(ws.Y, ws.F, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, true);
         pf.end(a, P_SLICE, st, 0.0, nb * w.slice_off_by);
         a = pf.begin(st);
-        launch_oz_gemm_offdiag(ws.Y, fr, dfr, g.nact, g.oz_tiles, p0, b, S, oz, sh.nb, st);
+        launch_oz_takahashi(ws.Y, ws.F, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, false);
         pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by, 1, nb * w.off_fl * 4.0 * S * (S + 1) / 2 / 8.0 * 2.0);
       } else {
         launch_selinv_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);

@@ -111,6 +111,10 @@ void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts
                              cudaStream_t st);
 void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
                             int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+// The same step with A = Y[S,S] sliced on the fly inside the GEMM: prep = true
+// computes the row exponents of A and slices B, prep = false runs the GEMM.
+void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                         int max_mp, int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool prep);
 // Split-precision Schur update F[S,S] -= L[S,P] W[S,P]^T (lower triangle):
 // slicing of L rows and W rows, then the tcgen05 GEMM with an FP64
 // read-modify-write (max_tiles = max over fronts of oz_schur_tiles(m_p)).
@@ -130,6 +134,12 @@ int64_t oz_front_bytes_B_real(int64_t mp, int b, int S);
 // H - sigma S): slicing of L rows and W rows, then the tcgen05 GEMM on
 // 128 x 64 lower-triangle tiles (max_tiles = max of oz_schur_tiles_real).
 int oz_schur_tiles_real(int mp);
+// Split-precision panel solve L[S,P] = W[S,P] D^-1 (W^T kept in the upper
+// triangle): gemm = false launches the slicing, gemm = true the tcgen05 GEMM.
+void launch_oz_panel(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp, int p0, int b,
+                     int S, const OzScratch& oz, int nb, cudaStream_t st, bool gemm);
+void launch_oz_panel_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp, int p0,
+                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool gemm);
 void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
                                 int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
 void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,

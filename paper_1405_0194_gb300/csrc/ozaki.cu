@@ -240,6 +240,9 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 //   trailing block, K = m_p), B = L[S,P] (row j = panel column p0 + j).
 // PHASE 1 (Schur): A = L[S,P] (row i = front row q0 + i, K = the panel's bb
 //   columns), B = W[S,P] (row j = column q0 + j of the stored W^T).
+// PHASE 2 (panel solve L = W D^-1): A = W[S,P] by rows (where L will be
+//   written; each entry is also copied to W^T in the upper triangle), B =
+//   the columns of the symmetric D^-1.
 // One block of 256 threads per group of 8 operand rows; grid (groups of A,
 // then groups of B; fronts; poles). Pass 1: warp w finds the exponent of row
 // 8g + w. Pass 2: thread (r, o) cuts the 8 entries of row 8g + r at K octet
@@ -247,7 +250,7 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 // at the place the MMA descriptors read them. Rows past the operand (inside
 // the last group) and K past its end are written as zeros.
 template <int PHASE>
-__global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y, const double2* __restrict__ F,
+__global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y, double2* __restrict__ F,
                                                   DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
                                                   int S, int groupsA, OzScratch oz) {
   PanelDims d;
@@ -272,13 +275,13 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
     }
   } else {
     K = d.bb;
-    rows = d.mp;
+    rows = (PHASE == 2 && !isA) ? d.bb : d.mp;
     if (isA) {
       src = F + fo + d.q0 + int64_t(d.m) * p0;
       si = 1;
       sk = d.m;
     } else {
-      src = F + fo + p0 + int64_t(d.m) * d.q0;
+      src = F + fo + p0 + int64_t(d.m) * (PHASE == 2 ? p0 : d.q0);
       si = d.m;
       sk = 1;
     }
@@ -329,6 +332,11 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
       if (i < rows) {
         if (k0 < K) v0 = row[int64_t(k0) * sk];
         if (k0 + 1 < K) v1 = row[int64_t(k0 + 1) * sk];
+        if (PHASE == 2 && isA) {  // W^T into the upper triangle (rows p0.., column q0 + i)
+          double2* wt = F + fo + p0 + int64_t(d.m) * (d.q0 + i);
+          if (k0 < K) wt[k0] = v0;
+          if (k0 + 1 < K) wt[k0 + 1] = v1;
+        }
       }
       int r0[6], i0[6], r1[6], i1[6];
       digits(v0.x, e, S, r0);
@@ -354,12 +362,14 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
   }
 }
 
-// Real operands of the Schur update (LDL^T of H - sigma S for inertia
-// counts): A = L[S,P] rows (tiles of 128 rows), B = W[S,P] rows (tiles of 64
-// rows), K = the panel's bb columns; one 16-byte word per slice and row
-// octet, in the same core-matrix layout (a slice of A is two 64-row blocks,
-// one of B is one block). Grid and passes as k_oz_slice.
-__global__ void __launch_bounds__(256) k_oz_slice_real(const double* __restrict__ F, DevFronts fr,
+// Real operands (LDL^T of H - sigma S for inertia counts), PHASE 1 (Schur):
+// A = L[S,P] rows (tiles of 128 rows), B = W[S,P] rows (tiles of 64 rows);
+// PHASE 2 (panel solve): A = W[S,P] rows (copied to W^T on the way), B = the
+// columns of D^-1; K = the panel's bb columns; one 16-byte word per slice and
+// row octet, in the same core-matrix layout (a slice of A is two 64-row
+// blocks, one of B is one block). Grid and passes as k_oz_slice.
+template <int PHASE>
+__global__ void __launch_bounds__(256) k_oz_slice_real(double* __restrict__ F, DevFronts fr,
                                                        const int32_t* __restrict__ fronts, int p0, int b, int S,
                                                        int groupsA, OzScratch oz) {
   PanelDims d;
@@ -368,8 +378,8 @@ __global__ void __launch_bounds__(256) k_oz_slice_real(const double* __restrict_
   const bool isA = int(blockIdx.x) < groupsA;
   const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
   const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
-  const int rows = d.mp, K = d.bb, nkt = ceil_div(K, kOzK);
-  const double* src = isA ? F + fo + d.q0 + int64_t(d.m) * p0 : F + fo + p0 + int64_t(d.m) * d.q0;
+  const int rows = (PHASE == 2 && !isA) ? d.bb : d.mp, K = d.bb, nkt = ceil_div(K, kOzK);
+  const double* src = isA ? F + fo + d.q0 + int64_t(d.m) * p0 : F + fo + p0 + int64_t(d.m) * (PHASE == 2 ? p0 : d.q0);
   const int64_t si = isA ? 1 : d.m, sk = isA ? d.m : 1;
   const int R = isA ? 2 * kOzRows : kOzRows;
   const int slice = isA ? 2 * kBlk : kBlk;
@@ -414,6 +424,11 @@ __global__ void __launch_bounds__(256) k_oz_slice_real(const double* __restrict_
       if (i < rows) {
         if (k0 < K) v0 = row[int64_t(k0) * sk];
         if (k0 + 1 < K) v1 = row[int64_t(k0 + 1) * sk];
+        if (PHASE == 2 && isA) {  // W^T into the upper triangle
+          double* wt = F + fo + p0 + int64_t(d.m) * (d.q0 + i);
+          if (k0 < K) wt[k0] = v0;
+          if (k0 + 1 < K) wt[k0 + 1] = v1;
+        }
       }
       int d0[6], d1[6];
       digits(v0, e, S, d0);
@@ -439,8 +454,10 @@ __device__ __forceinline__ void record_fail(int* s_fail, int site, int kt) {
 //   B = L[S,P]^T, and its mirror Y[P,S].
 // MODE 1, Schur: one CTA per lower-triangle output tile (64 x 64 complex) of
 //   the trailing block; F[S,S] -= A B^T with A = L[S,P], B = W[S,P] (K = bb).
-// CPLX = false (MODE 1 only): the real Schur update of the inertia LDL^T,
-//   128 x 64 output tiles, one MMA per slice pair and K step.
+// MODE 2, panel solve: one CTA per row tile of S; L[S,P] = W[S,P] D^-1 with
+//   A = W[S,P], B = D^-1 (K = bb), written where W was.
+// CPLX = false (MODES 1 and 2): the real LDL^T of the inertia counts, 128 x 64
+//   output tiles, one MMA per slice pair and K step.
 // Warps 0-7 epilogue, warp 8 producer, warp 9 MMA issuer (and TMEM owner).
 template <int MODE, bool CPLX>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ Yv, DevFronts fr,
@@ -459,11 +476,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
   if (*static_cast<volatile int*>(oz.fail)) return;  // an earlier CTA gave up: the result is void anyway
   int mt, nt, nkt;
-  if (MODE == 0) {
-    if (int(blockIdx.x) >= ceil_div(d.mp, kOzRows)) return;
+  if (MODE == 0 || MODE == 2) {
+    if (int(blockIdx.x) >= ceil_div(d.mp, TR)) return;
     mt = blockIdx.x;
     nt = 0;
-    nkt = ceil_div(d.mp, kOzK);
+    nkt = ceil_div(MODE == 0 ? d.mp : d.bb, kOzK);
   } else if (CPLX) {
     // lower-triangle tiles in row order: tile t of row tile mt has nt = t - mt (mt + 1) / 2
     const int t = blockIdx.x;
@@ -717,6 +734,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
               v = i64_scaled(static_cast<long long>(acc[c0 + c]), sc);
             if (MODE == 1) {
               Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] = old[c] - v;
+            } else if (MODE == 2) {
+              Yb[ES * ((d.q0 + i) + int64_t(d.m) * (p0 + j))] = v;
             } else {
               Yb[ES * ((d.q0 + i) + int64_t(d.m) * (p0 + j))] = -v;
               Yb[ES * ((p0 + j) + int64_t(d.m) * (d.q0 + i))] = -v;
@@ -730,6 +749,434 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == kEpiWarps + 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------- fused Takahashi step
+// Y[S,P] = -Y[S,S] L[S,P] with A = Y[S,S] sliced on the fly: the worker warps
+// read the FP64 trailing block straight from the front and write its slices
+// into shared memory, so A never makes a round trip through HBM as slices
+// (16 B per complex entry read once, instead of 16 B read, 36 B written and
+// 36 B read again). Row exponents of A and the slices of B = L[S,P] come from
+// k_oz_tak_prep. K tiles of 16; a ring of three slots, each holding all S
+// slices of A (6 KiB each: Ar, Ai, -Ar) and of B (4 KiB each: Br, Bi).
+constexpr int kFK = 16;                     // K per tile
+constexpr int kFBlk = kOzRows * kFK * 2;    // one 64-row block of one slice (2 KiB)
+constexpr int kFSliceA = 3 * kFBlk;
+constexpr int kFSliceB = 2 * kFBlk;
+constexpr int kFSlots = 3;
+constexpr int kFSlotA = 6 * kFSliceA;       // A part of a slot (S <= 6)
+constexpr int kFSlot = kFSlotA + 6 * kFSliceB;
+constexpr int kFChunk = 256 / kFK;          // K tiles per exact chunk
+constexpr int kFWorkers = 8;
+constexpr int kFThreads = (kFWorkers + 1) * 32;
+
+// K-major no-swizzle descriptor for 16-deep tiles: SBO = 256 B.
+__device__ __forceinline__ uint64_t sdesc16(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(256 >> 4) << 32) |
+         (uint64_t(1) << 46);
+}
+
+// 32 lanes x 16 / 32 consecutive TMEM columns of this warp's lane quarter.
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t addr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(addr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+// The integer nearest to x 2^(7 S - e) (|x| < 2^e), from the bit pattern.
+__device__ __forceinline__ long long fixed_point(double x, int e, int S) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = int((bits >> 52) & 0x7FF);
+  unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+  int Ee = 1;
+  if (E != 0) {
+    mant |= 1ull << 52;
+    Ee = E;
+  }
+  const int n = 1075 - Ee - 7 * S + e;
+  long long X = 0;
+  if (n > 0 && n < 54) X = static_cast<long long>((mant + (1ull << (n - 1))) >> n);
+  return (bits >> 63) ? -X : X;
+}
+
+// Row exponents of A = Y[S,S] (A groups) and the slices of B = L[S,P] in the
+// 16-deep tile layout (B groups); grid (groups of A, then of B; fronts; poles).
+__global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__ Y, const double2* __restrict__ F,
+                                                     DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
+                                                     int S, int groupsA, OzScratch oz) {
+  PanelDims d;
+  if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
+  const int pole = blockIdx.z;
+  const bool isA = int(blockIdx.x) < groupsA;
+  const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
+  const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
+  const double2* src = isA ? Y + fo + int64_t(d.q0) * d.m + d.q0 : F + fo + int64_t(p0) * d.m + d.q0;
+  const int rows = isA ? d.mp : d.bb, K = d.mp;
+  int* ex = isA ? oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f]
+                : oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];
+  if (g * 8 >= rows) return;
+  __shared__ int s_e[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const int i = g * 8 + warp;
+    uint32_t mx = 0;
+    if (i < rows)
+      for (int k = lane; k < K; k += 32) {
+        const double2 v = src[int64_t(i) * d.m + k];
+        mx = max(mx, max(uint32_t(__double2hiint(v.x)) & 0x7FFFFFFFu, uint32_t(__double2hiint(v.y)) & 0x7FFFFFFFu));
+      }
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    int e = 0;
+    if (mx >= 0x7FF00000u)
+      e = kNanExp;
+    else if (mx != 0)
+      e = int(mx >> 20) - 1022;
+    if (lane == 0) {
+      s_e[warp] = e;
+      if (i < rows) ex[i] = e;
+    }
+  }
+  if (isA) return;
+  __syncthreads();
+  const int r = threadIdx.x & 7;
+  const int j = g * 8 + r;
+  const int e = s_e[r];
+  const int nkt = ceil_div(K, kFK);
+  uint8_t* rowbase = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + (j >> 3) * 256 + r * 16;
+  const double2* row = src + int64_t(j) * d.m;
+  for (int o = threadIdx.x >> 3; o < nkt * (kFK / 8); o += 32) {
+    uint32_t wr[6][4], wi[6][4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const int k0 = o * 8 + u;
+      double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
+      if (j < rows) {
+        if (k0 < K) v0 = row[k0];
+        if (k0 + 1 < K) v1 = row[k0 + 1];
+      }
+      int r0[6], i0[6], r1[6], i1[6];
+      digits(v0.x, e, S, r0);
+      digits(v0.y, e, S, i0);
+      digits(v1.x, e, S, r1);
+      digits(v1.y, e, S, i1);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        wr[q][u / 2] = bf16_bits(r0[q]) | (bf16_bits(r1[q]) << 16);
+        wi[q][u / 2] = bf16_bits(i0[q]) | (bf16_bits(i1[q]) << 16);
+      }
+    }
+    uint8_t* p = rowbase + int64_t(o >> 1) * S * kFSliceB + (o & 1) * 128;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if (q < S) {
+        *reinterpret_cast<uint4*>(p + q * kFSliceB) = make_uint4(wr[q][0], wr[q][1], wr[q][2], wr[q][3]);
+        *reinterpret_cast<uint4*>(p + q * kFSliceB + kFBlk) = make_uint4(wi[q][0], wi[q][1], wi[q][2], wi[q][3]);
+      }
+  }
+}
+
+// One CTA per 64-row tile of S (front, pole). Warps 0-7: workers (warps 0-3
+// produce the even K tiles, 4-7 the odd ones: thread (row r, octet o) cuts
+// 8 entries of row r of A into S x 3 words; every warp also drains its part
+// of TMEM after each chunk); warp 8: TMEM owner and MMA issuer.
+__global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restrict__ Y, DevFronts fr,
+                                                              const int32_t* __restrict__ fronts, int p0, int b,
+                                                              int S, OzScratch oz) {
+  extern __shared__ __align__(128) uint8_t osm[];
+  __shared__ __align__(8) uint64_t full_a[kFSlots], full_b[kFSlots], empty[kFSlots];
+  __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  __shared__ int s_last_b[kFSlots];
+  __shared__ int s_ea[kOzRows], s_eb[kOzRows];
+  PanelDims d;
+  if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
+  if (*static_cast<volatile int*>(oz.fail)) return;
+  const int mt = blockIdx.x;
+  if (mt >= ceil_div(d.mp, kOzRows)) return;
+  const int pole = blockIdx.z;
+  const int nkt = ceil_div(d.mp, kFK);
+  const int nchunks = ceil_div(nkt, kFChunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* fail = &s_fail;
+  const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f];
+
+  if (threadIdx.x < 2 * kOzRows) {
+    if (threadIdx.x < kOzRows) {
+      const int i = mt * kOzRows + threadIdx.x;
+      s_ea[threadIdx.x] = i < d.mp ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
+    } else {
+      const int j = threadIdx.x - kOzRows;
+      s_eb[j] = j < d.bb ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + j] : 0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int j = 0; j < kFSlots; ++j) {
+      bar_init(smem_u32(&full_a[j]), 4 * 32);  // the producing half: 128 threads
+      bar_init(smem_u32(&full_b[j]), 1);
+      bar_init(smem_u32(&empty[j]), 1);
+      s_last_b[j] = -1;
+    }
+    bar_init(smem_u32(&acc_full), 1);
+    bar_init(smem_u32(&acc_empty), kFWorkers);
+    bar_init(smem_u32(&mma_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == kFWorkers) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const bool multi = nchunks > kOzFlush;
+
+  const int q = warp & 3, h = (warp >> 2) & 1;
+  // this warp's exact int64 partial sums live in TMEM columns 384 + 64 h ..
+  // (lo, hi words of column c at 2c, 2c + 1), next to the six accumulators
+  const uint32_t tsum = tmem + (uint32_t(q * 32) << 16) + uint32_t(6 * 64 + h * 64);
+  // output row of this thread's TMEM lane (real part in lanes 0-63, imaginary in 64-127)
+  const int orow = mt * kOzRows + (q & 1) * 32 + lane;
+  double* Yout = reinterpret_cast<double*>(Y + int64_t(pole) * fr.pool + fr.off[d.f]) + (q >> 1);
+
+  if (warp == kFWorkers) {
+    if (lane == 0) {  // ---- MMA issuer
+      const uint32_t id_pos = idesc(false), id_neg = idesc(true);
+      for (int kt = 0; kt < nkt; ++kt) {
+        const int c = kt / kFChunk, in_chunk = kt % kFChunk;
+        if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail)) {
+          record_fail(&s_fail, 4, kt);
+          break;
+        }
+        const int slot = kt % kFSlots;
+        const uint32_t par = (kt / kFSlots) & 1;
+        if (!bar_wait(smem_u32(&full_a[slot]), par, fail) || !bar_wait(smem_u32(&full_b[slot]), par, fail)) {
+          record_fail(&s_fail, 6, kt);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t base = smem_u32(osm + slot * kFSlot);
+        for (int s = 1; s <= S; ++s) {
+          const uint32_t a1 = base + (s - 1) * kFSliceA, a2 = a1 + kFBlk;  // [Ar; Ai], [Ai; -Ar]
+          for (int t = 1; s + t <= S + 1; ++t) {
+            const uint32_t acc_d = tmem + uint32_t((s + t - 2) * 64);
+            const uint32_t br = base + kFSlotA + (t - 1) * kFSliceB, bi = br + kFBlk;
+            const uint32_t first = (in_chunk == 0 && s == 1) ? 0u : 1u;
+            mma(acc_d, sdesc16(a1), sdesc16(br), id_pos, first);
+            mma(acc_d, sdesc16(a2), sdesc16(bi), id_neg, 1u);
+          }
+        }
+        mma_commit(smem_u32(&empty[slot]));
+        if (in_chunk == kFChunk - 1 || kt == nkt - 1) mma_commit(smem_u32(&acc_full));
+      }
+      mma_commit(smem_u32(&mma_done));
+      if (!bar_wait_all(smem_u32(&mma_done), 0)) record_fail(&s_fail, 7, 0);
+    }
+  } else {  // ---- workers: produce A slices, drain TMEM after each chunk
+    const int half = warp >> 2;
+    const int item = q * 32 + lane;        // 0..127
+    const int r = item & (kOzRows - 1), oct = item >> 6;
+    const int i = mt * kOzRows + r;
+    const bool rowok = i < d.mp;
+    const int e = s_ea[r];
+    const double2* col = Y + int64_t(pole) * fr.pool + fr.off[d.f] + int64_t(d.q0 + (rowok ? i : 0)) * d.m + d.q0;
+    const uint32_t wbase = uint32_t((r >> 3) * 256 + oct * 128 + (r & 7) * 16);
+    int drained = 0, pending = 0;
+    bool ok = true;
+    auto drain = [&](int ch) -> bool {
+      bool got = true;
+      if (lane == 0) got = bar_wait(smem_u32(&acc_full), ch & 1, fail);
+      got = __shfl_sync(0xFFFFFFFFu, got, 0);
+      if (!got) {
+        if (lane == 0) record_fail(&s_fail, 8, ch * kFChunk);
+        return false;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {  // 16 output columns at a time
+        uint32_t w[32];
+        if (pending > 0) {
+          tmem_ld32(tsum + hh * 32, w);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) w[c] = 0u;
+        }
+        for (int D = 2; D <= S + 1; ++D) {
+          const int sh = 7 * (S + 1 - D);
+          uint32_t v[16];
+          tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 16), v);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            unsigned long long a64 = (static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c];
+            a64 += static_cast<unsigned long long>(static_cast<long long>(__float2int_rn(__uint_as_float(v[c])))) << sh;
+            w[2 * c] = uint32_t(a64);
+            w[2 * c + 1] = uint32_t(a64 >> 32);
+          }
+        }
+        if (multi && pending + 1 == kOzFlush && ch != nchunks - 1) {
+          // K > 2048: move the exact partial sum into this thread's own
+          // Y[S,P] entries (rounded once), which no operand of the launch reads
+          if (orow < d.mp) {
+            const int ea = s_ea[orow - mt * kOzRows];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int j = h * 32 + hh * 16 + c;
+              if (j < d.bb) {
+                double* o = Yout + 2 * ((d.q0 + orow) + int64_t(d.m) * (p0 + j));
+                const long long a64 = static_cast<long long>((static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c]);
+                const double v = i64_scaled(a64, ea + s_eb[j] - 7 * (S + 1));
+                *o = (ch + 1 == kOzFlush ? 0.0 : *o) + v;
+              }
+            }
+          }
+        } else {
+          tmem_st32(tsum + hh * 32, w);
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) bar_arrive(smem_u32(&acc_empty));
+      pending = (multi && pending + 1 == kOzFlush && ch != nchunks - 1) ? 0 : pending + 1;
+      return true;
+    };
+    for (int kt = half; kt < nkt && ok; kt += 2) {
+      // the slot of tile kt is freed only by MMAs of the next chunk, which
+      // wait for the drain of the previous one: drain it first
+      while (ok && drained < nchunks && kt >= kFChunk * (drained + 1) + kFSlots) ok = drain(drained++);
+      if (!ok) break;
+      const int slot = kt % kFSlots, use = kt / kFSlots;
+      bool free_slot = true;
+      if (use > 0) {
+        if (lane == 0) free_slot = bar_wait(smem_u32(&empty[slot]), (use - 1) & 1, fail);
+        free_slot = __shfl_sync(0xFFFFFFFFu, free_slot, 0);
+      }
+      if (!free_slot) {
+        if (lane == 0) record_fail(&s_fail, 2, kt);
+        ok = false;
+        break;
+      }
+      uint8_t* sbase = osm + slot * kFSlot;
+      if (item == 0) {  // B: all S slices of this K tile, one bulk copy
+        bar_expect(smem_u32(&full_b[slot]), uint32_t(S * kFSliceB));
+        bulk_load(smem_u32(sbase + kFSlotA), gB + int64_t(kt) * S * kFSliceB, uint32_t(S * kFSliceB),
+                  smem_u32(&full_b[slot]));
+        atomicMax(&s_last_b[slot], kt);
+      }
+      // A: 8 entries of row r at k = 16 kt + 8 oct .. + 7, as fixed-point integers
+      long long X[16];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = kt * kFK + oct * 8 + u;
+        double2 v = make_double2(0.0, 0.0);
+        if (rowok && k < d.mp) v = col[k];
+        X[2 * u] = fixed_point(v.x, e, S);
+        X[2 * u + 1] = fixed_point(v.y, e, S);
+      }
+      // balanced base-128 digits from the low end: slice S-1 first
+#pragma unroll
+      for (int sl = 5; sl >= 0; --sl) {
+        if (sl >= S) continue;
+        int dg[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          if (sl > 0) {
+            dg[t] = int((X[t] + 64) & 127) - 64;
+            X[t] = (X[t] - dg[t]) >> 7;
+          } else {
+            dg[t] = int(X[t]);
+          }
+        }
+        uint4 wre, wim, wneg;
+        wre.x = bf16_bits(dg[0]) | (bf16_bits(dg[2]) << 16);
+        wre.y = bf16_bits(dg[4]) | (bf16_bits(dg[6]) << 16);
+        wre.z = bf16_bits(dg[8]) | (bf16_bits(dg[10]) << 16);
+        wre.w = bf16_bits(dg[12]) | (bf16_bits(dg[14]) << 16);
+        wim.x = bf16_bits(dg[1]) | (bf16_bits(dg[3]) << 16);
+        wim.y = bf16_bits(dg[5]) | (bf16_bits(dg[7]) << 16);
+        wim.z = bf16_bits(dg[9]) | (bf16_bits(dg[11]) << 16);
+        wim.w = bf16_bits(dg[13]) | (bf16_bits(dg[15]) << 16);
+        wneg.x = wre.x ^ 0x80008000u;  // -d: flip the sign bits (zero becomes -0, an exact zero)
+        wneg.y = wre.y ^ 0x80008000u;
+        wneg.z = wre.z ^ 0x80008000u;
+        wneg.w = wre.w ^ 0x80008000u;
+        uint8_t* ps = sbase + sl * kFSliceA + wbase;
+        *reinterpret_cast<uint4*>(ps) = wre;
+        *reinterpret_cast<uint4*>(ps + kFBlk) = wim;
+        *reinterpret_cast<uint4*>(ps + 2 * kFBlk) = wneg;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_arrive(smem_u32(&full_a[slot]));
+    }
+    while (ok && drained < nchunks) ok = drain(drained++);
+  }
+
+  __syncthreads();
+  if (threadIdx.x == 0)  // bulk copies still in flight after a failure land before the CTA leaves
+    for (int j = 0; j < kFSlots; ++j)
+      if (s_last_b[j] >= 0 && !bar_wait_all(smem_u32(&full_b[j]), (s_last_b[j] / kFSlots) & 1))
+        record_fail(&s_fail, 3, j);
+  __syncthreads();
+  if (s_fail) {
+    if (threadIdx.x == 0)
+      atomicMax(oz.fail, 1 + (3 << 28) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
+  } else if (warp < kFWorkers) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int ea = orow < d.mp ? s_ea[orow - mt * kOzRows] : 0;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      uint32_t w[32];
+      tmem_ld32(tsum + hh * 32, w);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int j = h * 32 + hh * 16 + c;
+        if (orow < d.mp && j < d.bb) {
+          const int eb = s_eb[j];
+          double* o = Yout + 2 * ((d.q0 + orow) + int64_t(d.m) * (p0 + j));
+          const long long a64 =
+              static_cast<long long>((static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c]);
+          double v = i64_scaled(a64, ea + eb - 7 * (S + 1));
+          if (multi) v += *o;  // the partial sums moved out every eight chunks
+          if (ea == kNanExp || eb == kNanExp) v = __longlong_as_double(0x7FF8000000000000LL);
+          *o = -v;
+          Yout[2 * ((p0 + j) + int64_t(d.m) * (d.q0 + orow))] = -v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == kFWorkers) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 }  // namespace
@@ -755,6 +1202,10 @@ cudaError_t oz_configure(int S) {
   cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_oz_tak_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSlots * kFSlot));
   return e;
 }
 
@@ -778,7 +1229,7 @@ void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int3
   if (nfronts <= 0 || max_mp <= 0) return;
   const int groups = (max_mp + 7) / 8;
   dim3 g(2 * groups, nfronts, nb);
-  k_oz_slice_real<<<g, 256, 0, st>>>(F, fr, fronts, p0, b, S, groups, oz);
+  k_oz_slice_real<1><<<g, 256, 0, st>>>(const_cast<double*>(F), fr, fronts, p0, b, S, groups, oz);
 }
 
 void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
@@ -800,7 +1251,7 @@ void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t*
   if (nfronts <= 0 || max_mp <= 0) return;
   const int groups = (max_mp + 7) / 8;
   dim3 g(2 * groups, nfronts, nb);
-  k_oz_slice<1><<<g, 256, 0, st>>>(F, F, fr, fronts, p0, b, S, groups, oz);
+  k_oz_slice<1><<<g, 256, 0, st>>>(F, const_cast<double2*>(F), fr, fronts, p0, b, S, groups, oz);
 }
 
 void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
@@ -816,7 +1267,7 @@ void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts
   if (nfronts <= 0 || max_rows <= 0) return;
   const int groupsA = (max_rows + 7) / 8, groupsB = (b + 7) / 8;
   dim3 g(groupsA + groupsB, nfronts, nb);
-  k_oz_slice<0><<<g, 256, 0, st>>>(Y, F, fr, fronts, p0, b, S, groupsA, oz);
+  k_oz_slice<0><<<g, 256, 0, st>>>(Y, const_cast<double2*>(F), fr, fronts, p0, b, S, groupsA, oz);
 }
 
 void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
@@ -824,6 +1275,50 @@ void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fron
   if (nfronts <= 0 || max_tiles <= 0) return;
   dim3 gg(max_tiles, nfronts, nb);
   k_oz_gemm<0, true><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(Y, fr, fronts, p0, b, S, oz);
+}
+
+// Split-precision panel solve L[S,P] = W[S,P] D^-1 (complex poles and real
+// inertia shifts): slicing of W rows (W^T saved on the way) and of D^-1, then
+// the GEMM writing L over W.
+void launch_oz_panel(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp, int p0, int b,
+                     int S, const OzScratch& oz, int nb, cudaStream_t st, bool gemm) {
+  if (nfronts <= 0 || max_mp <= 0) return;
+  if (!gemm) {
+    const int groupsA = (max_mp + 7) / 8, groupsB = (b + 7) / 8;
+    dim3 g(groupsA + groupsB, nfronts, nb);
+    k_oz_slice<2><<<g, 256, 0, st>>>(nullptr, F, fr, fronts, p0, b, S, groupsA, oz);
+  } else {
+    dim3 gg(ceil_div(max_mp, kOzRows), nfronts, nb);
+    k_oz_gemm<2, true><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
+  }
+}
+
+void launch_oz_panel_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp, int p0,
+                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool gemm) {
+  if (nfronts <= 0 || max_mp <= 0) return;
+  if (!gemm) {
+    const int groupsA = (max_mp + 7) / 8, groupsB = (b + 7) / 8;
+    dim3 g(groupsA + groupsB, nfronts, nb);
+    k_oz_slice_real<2><<<g, 256, 0, st>>>(F, fr, fronts, p0, b, S, groupsA, oz);
+  } else {
+    dim3 gg(ceil_div(max_mp, 2 * kOzRows), nfronts, nb);
+    k_oz_gemm<2, false><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
+  }
+}
+
+// Fused Takahashi step: exponents of A and slices of B (prep = true), then
+// the GEMM that slices A on the fly (prep = false).
+void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                         int max_mp, int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool prep) {
+  if (nfronts <= 0 || max_mp <= 0) return;
+  if (prep) {
+    const int groupsA = (max_mp + 7) / 8, groupsB = (b + 7) / 8;
+    dim3 g(groupsA + groupsB, nfronts, nb);
+    k_oz_tak_prep<<<g, 256, 0, st>>>(Y, F, fr, fronts, p0, b, S, groupsA, oz);
+  } else {
+    dim3 gg(ceil_div(max_mp, kOzRows), nfronts, nb);
+    k_oz_tak_fused<<<gg, kFThreads, size_t(kFSlots) * kFSlot, st>>>(Y, fr, fronts, p0, b, S, oz);
+  }
 }
 
 }  // namespace pexsi
