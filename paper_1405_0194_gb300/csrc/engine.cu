@@ -138,7 +138,7 @@ void workspace_free(Workspace& ws) {
 namespace {
 
 struct PanelGeom {
-  int nact = 0, row_tiles = 0, tri_tiles = 0, max_mp = 0, oz_tiles = 0, oz_schur = 0, oz_schur_r = 0;
+  int nact = 0, row_tiles = 0, tri_tiles = 0, max_mp = 0, oz_schur = 0, oz_schur_r = 0;
 };
 
 PanelGeom panel_geom(const Level& lv, int p0, int b) {
@@ -152,7 +152,6 @@ PanelGeom panel_geom(const Level& lv, int p0, int b) {
     g.row_tiles = std::max(g.row_tiles, rt);
     g.tri_tiles = std::max(g.tri_tiles, rt * (rt + 1) / 2);
     g.max_mp = std::max(g.max_mp, mp);
-    g.oz_tiles = std::max(g.oz_tiles, oz_offdiag_tiles(mp));
     g.oz_schur = std::max(g.oz_schur, oz_schur_tiles(mp));
     g.oz_schur_r = std::max(g.oz_schur_r, oz_schur_tiles_real(mp));
   }

@@ -103,16 +103,9 @@ void launch_extract(const double2* Y, const int64_t* entry_pos, int64_t nnz, dou
 void launch_scaled_imag(const double2* Y, const int64_t* entry_pos, int64_t nnz, double scale, double* out,
                         cudaStream_t st);
 
-// Split-precision Y[S,P] = -Y[S,S] L[S,P] and its mirror: slicing of A and
-// B (max_rows = max m_p), then the tcgen05 GEMM (max_tiles = max over fronts
-// of oz_offdiag_tiles(m_p), the 64-row output tiles).
-void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts,
-                             int nfronts, int max_rows, int p0, int b, int S, const OzScratch& oz, int nb,
-                             cudaStream_t st);
-void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
-                            int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
-// The same step with A = Y[S,S] sliced on the fly inside the GEMM: prep = true
-// computes the row exponents of A and slices B, prep = false runs the GEMM.
+// Split-precision Takahashi step Y[S,P] = -Y[S,S] L[S,P] and its mirror, with
+// A = Y[S,S] sliced on the fly inside the GEMM: prep = true computes the row
+// exponents of A and slices B, prep = false runs the GEMM.
 void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
                          int max_mp, int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool prep);
 // Split-precision Schur update F[S,S] -= L[S,P] W[S,P]^T (lower triangle):
@@ -123,7 +116,6 @@ void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t*
 void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
                           int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
 int oz_schur_tiles(int mp);
-int oz_offdiag_tiles(int mp);
 size_t oz_smem_bytes(int S);
 // Slice-tile scratch of one front per pole (both phases), for its largest m_p.
 int64_t oz_front_bytes_A(int64_t mp, int b, int S);

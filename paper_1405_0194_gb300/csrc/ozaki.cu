@@ -1,6 +1,8 @@
-// Split-precision (Ozaki-scheme) complex GEMMs on the tcgen05 tensor cores:
-// the Takahashi step Y[S,P] = -Y[S,S] L[S,P] of selected inversion and the
-// Schur update F[S,S] -= L[S,P] W[S,P]^T of the factorisation.
+// Split-precision (Ozaki-scheme) complex and real GEMMs on the tcgen05 tensor
+// cores: the Schur update F[S,S] -= L[S,P] W[S,P]^T and the panel solve
+// L[S,P] = W[S,P] D^-1 of the factorisation (short K = bb, persistent
+// kernel k_oz_gemm), and the Takahashi step Y[S,P] = -Y[S,S] L[S,P] of
+// selected inversion (long K = m_p, k_oz_tak_fused, which slices A itself).
 //
 // Error-free splitting (Ozaki, Ogita, Oishi and Rump 2012): each row i of A
 // and each row j of B (both stored K-major) is scaled by a power of two
@@ -38,12 +40,10 @@
 // one after another: 12 KiB each for A (Ar, Ai, -Ar), 8 KiB each for B
 // (Br, Bi); so one bulk async copy stages a slice of A or all slices of B.
 //
-// The GEMM CTA is warp-specialised: a producer warp streams slices of A
-// through a ring of eight shared-memory slots and B through two slots
-// (cp.async.bulk, mbarrier transaction counts); an MMA warp issues
-// tcgen05.mma from one thread and releases each slot with tcgen05.commit;
-// eight epilogue warps drain TMEM after every K chunk while the producer
-// keeps loading. Every wait is bounded (1 s of wall time); a wait that runs
+// The GEMM CTAs are warp-specialised: a producer streams slices (bulk async
+// copies with mbarrier transaction counts, or slices cut in shared memory by
+// worker warps); one thread issues tcgen05.mma and releases each slot with
+// tcgen05.commit; epilogue warps drain TMEM while the next slices load. Every wait is bounded (1 s of wall time); a wait that runs
 // out records where in a status word, lets the other roles stop, waits
 // (bounded) for its own copies and MMAs in flight, frees TMEM and returns,
 // and CTAs that start after a failure return at once.
@@ -59,7 +59,6 @@ namespace {
 
 constexpr int kOzRows = 64;   // complex rows of A (and of B) per tile
 constexpr int kOzK = 32;      // K per staged tile
-constexpr int kOzChunk = 8;   // K tiles per exact FP32 accumulation (256)
 constexpr int kOzFlush = 8;   // chunks per 64-bit integer partial sum
 constexpr int kBlk = kOzRows * kOzK * 2;  // bytes of one 64-row block of one slice (4 KiB)
 constexpr int kSliceA = 3 * kBlk;         // Ar, Ai, -Ar (12 KiB)
@@ -158,6 +157,39 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// 32 lanes x 16 / 32 consecutive TMEM columns of this warp's lane quarter.
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t addr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(addr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
 // Balanced base-2^7 digits of x 2^(-e), |x| < 2^e: X = the integer nearest to
 // x 2^(7 S - e), taken from the bit pattern (mantissa shifted right by
 // n >= 10 with rounding, no floating-point arithmetic); then d[S-1] ... d[1]
@@ -236,8 +268,6 @@ __device__ __forceinline__ bool panel_dims(const DevFronts& fr, const int32_t* f
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // ---------------------------------------------------------------- slicing
-// PHASE 0 (Takahashi): A = Y[S,S] (row i = column q0 + i of the symmetric
-//   trailing block, K = m_p), B = L[S,P] (row j = panel column p0 + j).
 // PHASE 1 (Schur): A = L[S,P] (row i = front row q0 + i, K = the panel's bb
 //   columns), B = W[S,P] (row j = column q0 + j of the stored W^T).
 // PHASE 2 (panel solve L = W D^-1): A = W[S,P] by rows (where L will be
@@ -250,7 +280,7 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 // at the place the MMA descriptors read them. Rows past the operand (inside
 // the last group) and K past its end are written as zeros.
 template <int PHASE>
-__global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y, double2* __restrict__ F,
+__global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*Y*/, double2* __restrict__ F,
                                                   DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
                                                   int S, int groupsA, OzScratch oz) {
   PanelDims d;
@@ -259,33 +289,10 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ Y,
   const bool isA = int(blockIdx.x) < groupsA;
   const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
   const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
-  const double2* src;
-  int64_t si, sk;
-  int rows, K;
-  if (PHASE == 0) {
-    K = d.mp;
-    si = d.m;
-    sk = 1;
-    if (isA) {
-      src = Y + fo + int64_t(d.q0) * d.m + d.q0;
-      rows = d.mp;
-    } else {
-      src = F + fo + int64_t(p0) * d.m + d.q0;
-      rows = d.bb;
-    }
-  } else {
-    K = d.bb;
-    rows = (PHASE == 2 && !isA) ? d.bb : d.mp;
-    if (isA) {
-      src = F + fo + d.q0 + int64_t(d.m) * p0;
-      si = 1;
-      sk = d.m;
-    } else {
-      src = F + fo + p0 + int64_t(d.m) * (PHASE == 2 ? p0 : d.q0);
-      si = d.m;
-      sk = 1;
-    }
-  }
+  const int K = d.bb;
+  const int rows = (PHASE == 2 && !isA) ? d.bb : d.mp;
+  const double2* src = isA ? F + fo + d.q0 + int64_t(d.m) * p0 : F + fo + p0 + int64_t(d.m) * (PHASE == 2 ? p0 : d.q0);
+  const int64_t si = isA ? 1 : d.m, sk = isA ? d.m : 1;
   const int nkt = ceil_div(K, kOzK);
   const int slice = isA ? kSliceA : kSliceB;
   uint8_t* dst = isA ? oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f]
@@ -448,83 +455,84 @@ __device__ __forceinline__ void record_fail(int* s_fail, int site, int kt) {
   atomicCAS(s_fail, 0, site + 16 * (kt & 63));
 }
 
-// ---------------------------------------------------------------- GEMM
-// MODE 0, Takahashi: one CTA per (64-row tile of S, front, pole); the panel's
-//   bb <= 64 columns are one N tile. Y[S,P] = -A B^T with A = Y[S,S],
-//   B = L[S,P]^T, and its mirror Y[P,S].
-// MODE 1, Schur: one CTA per lower-triangle output tile (64 x 64 complex) of
-//   the trailing block; F[S,S] -= A B^T with A = L[S,P], B = W[S,P] (K = bb).
-// MODE 2, panel solve: one CTA per row tile of S; L[S,P] = W[S,P] D^-1 with
-//   A = W[S,P], B = D^-1 (K = bb), written where W was.
-// CPLX = false (MODES 1 and 2): the real LDL^T of the inertia counts, 128 x 64
-//   output tiles, one MMA per slice pair and K step.
-// Warps 0-7 epilogue, warp 8 producer, warp 9 MMA issuer (and TMEM owner).
+// ---------------------------------------------------------------- GEMM (short K)
+// Output tiles of one front at the active panel (m_p rows below it).
+template <int MODE, bool CPLX>
+__device__ __forceinline__ int front_tiles(int mp) {
+  if (mp <= 0) return 0;
+  if (MODE == 2) return ceil_div(mp, CPLX ? kOzRows : 2 * kOzRows);
+  if (CPLX) {
+    const int n = ceil_div(mp, kOzRows);
+    return n * (n + 1) / 2;  // 64 x 64 tiles on and below the diagonal
+  }
+  const int nmt = ceil_div(mp, 2 * kOzRows), nnt = ceil_div(mp, kOzRows);
+  return nmt * (nmt + 1) - (2 * nmt - nnt);  // 128 x 64 tiles: 2r + 2 in row r, fewer in the last
+}
+
+// Row tile mt and column tile nt of tile t of a front.
+template <int MODE, bool CPLX>
+__device__ __forceinline__ void tile_coords(int t, int& mt, int& nt) {
+  if (MODE == 2) {
+    mt = t;
+    nt = 0;
+  } else if (CPLX) {  // t = mt (mt + 1) / 2 + nt, nt <= mt
+    mt = int((sqrtf(8.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
+    while (mt * (mt + 1) / 2 > t) --mt;
+    while ((mt + 1) * (mt + 2) / 2 <= t) ++mt;
+    nt = t - mt * (mt + 1) / 2;
+  } else {  // t = mt (mt + 1) + nt, nt <= 2 mt + 1
+    mt = int((sqrtf(4.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
+    while (mt * (mt + 1) > t) --mt;
+    while ((mt + 1) * (mt + 2) <= t) ++mt;
+    nt = t - mt * (mt + 1);
+  }
+}
+
+// MODE 1, Schur update F[S,S] -= A B^T on the lower triangle, A = L[S,P],
+//   B = W[S,P] (K = bb <= 64); complex 64 x 64 tiles or real 128 x 64 tiles.
+// MODE 2, panel solve L[S,P] = A B^T with A = W[S,P] and B = D^-1, written
+//   where W was; one tile per row tile of S.
+// Persistent: each CTA walks the (pole, front, tile) items of the launch with
+// stride gridDim.x. The slot rings run on across items, so the next tile's
+// slices load during this tile's MMAs; the epilogue warps drain TMEM into
+// registers and release it at once, so the next tile's MMAs overlap this
+// tile's global read-modify-write. Warps 0-7 epilogue, warp 8 producer, warp
+// 9 MMA issuer (and TMEM owner).
 template <int MODE, bool CPLX>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ Yv, DevFronts fr,
-                                                             const int32_t* __restrict__ fronts, int p0, int b,
-                                                             int S, OzScratch oz) {
+                                                             const int32_t* __restrict__ fronts, int nfronts, int p0,
+                                                             int b, int S, int nb, OzScratch oz) {
   extern __shared__ __align__(128) uint8_t osm[];
   __shared__ __align__(8) uint64_t full_a[kSlotsA], empty_a[kSlotsA], full_b[kSlotsB], empty_b[kSlotsB];
   __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
-  __shared__ int s_ea[2 * kOzRows], s_eb[kOzRows];  // exponents of the tile's rows of A and of B
-  constexpr int TR = CPLX ? kOzRows : 2 * kOzRows;     // output rows per tile
-  constexpr int SA = CPLX ? kSliceA : 2 * kBlk;        // bytes of one slice of A (one K tile)
-  constexpr int SB = CPLX ? kSliceB : kBlk;            // bytes of one slice of B (one K tile)
-  PanelDims d;
-  if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
+  constexpr int TR = CPLX ? kOzRows : 2 * kOzRows;  // output rows per tile
+  constexpr int SA = CPLX ? kSliceA : 2 * kBlk;     // bytes of one slice of A (one K tile)
+  constexpr int SB = CPLX ? kSliceB : kBlk;         // bytes of one slice of B (one K tile)
   if (*static_cast<volatile int*>(oz.fail)) return;  // an earlier CTA gave up: the result is void anyway
-  int mt, nt, nkt;
-  if (MODE == 0 || MODE == 2) {
-    if (int(blockIdx.x) >= ceil_div(d.mp, TR)) return;
-    mt = blockIdx.x;
-    nt = 0;
-    nkt = ceil_div(MODE == 0 ? d.mp : d.bb, kOzK);
-  } else if (CPLX) {
-    // lower-triangle tiles in row order: tile t of row tile mt has nt = t - mt (mt + 1) / 2
-    const int t = blockIdx.x;
-    const int nmt = ceil_div(d.mp, kOzRows);
-    if (t >= nmt * (nmt + 1) / 2) return;
-    mt = int((sqrtf(8.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
-    while (mt * (mt + 1) / 2 > t) --mt;
-    while ((mt + 1) * (mt + 2) / 2 <= t) ++mt;
-    nt = t - mt * (mt + 1) / 2;
-    nkt = ceil_div(d.bb, kOzK);
-  } else {
-    // 128-row tiles mt, 64-column tiles nt = 0 .. min(2 mt + 1, nnt - 1)
-    const int nmt = ceil_div(d.mp, 2 * kOzRows), nnt = ceil_div(d.mp, kOzRows);
-    int t = blockIdx.x;
-    mt = -1;
-    for (int r = 0; r < nmt; ++r) {
-      const int c = min(2 * r + 2, nnt);
-      if (t < c) {
-        mt = r;
-        break;
-      }
-      t -= c;
-    }
-    if (mt < 0) return;
-    nt = t;
-    nkt = ceil_div(d.bb, kOzK);
-  }
-  const int pole = blockIdx.z;
-  const int nchunks = ceil_div(nkt, kOzChunk);
-  uint8_t* sA = osm;                         // kSlotsA x one slice of A (Ar, Ai, -Ar; or Ar)
-  uint8_t* sB = osm + kSlotsA * kSliceA;     // kSlotsB x S slices of B (Br, Bi; or Br)
-  const uint8_t* gA = oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f] + int64_t(mt) * nkt * S * SA;
-  const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + int64_t(nt) * nkt * S * SB;
+  uint8_t* sA = osm;                                 // kSlotsA x one slice of A (Ar, Ai, -Ar; or Ar)
+  uint8_t* sB = osm + kSlotsA * kSliceA;             // kSlotsB x S slices of B (Br, Bi; or Br)
+  int* s_pref = reinterpret_cast<int*>(osm + kSlotsA * kSliceA + kSlotsB * 6 * kSliceB);  // tiles before front f
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* fail = &s_fail;
 
-  if (threadIdx.x < TR + kOzRows) {  // staged once, read by the epilogue without global round trips
-    if (threadIdx.x < TR) {
-      const int i = mt * TR + threadIdx.x;
-      s_ea[threadIdx.x] = i < d.mp ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
-    } else {
-      const int t = threadIdx.x - TR;
-      const int j = nt * kOzRows + t;
-      s_eb[t] = j < (MODE == 1 ? d.mp : d.bb) ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + j] : 0;
+  if (warp == 0) {  // prefix sums of the fronts' tile counts
+    int carry = 0;
+    if (lane == 0) s_pref[0] = 0;
+    for (int f0 = 0; f0 < nfronts; f0 += 32) {
+      int v = 0;
+      if (f0 + lane < nfronts) {
+        PanelDims d;
+        v = panel_dims(fr, fronts, f0 + lane, p0, b, d) ? front_tiles<MODE, CPLX>(d.mp) : 0;
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (f0 + lane < nfronts) s_pref[f0 + lane + 1] = carry + v;
+      carry += __shfl_sync(0xFFFFFFFFu, v, 31);
     }
   }
   if (threadIdx.x == 0) {
@@ -551,46 +559,59 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
+  const int T = s_pref[nfronts];
+  const int items = T * nb;
 
-  // epilogue state: TMEM lanes 32 q .. 32 q + 31 (real rows; rows < 64 are
-  // real parts, rows >= 64 imaginary parts), columns 32 h .. 32 h + 31
-  const int q = warp & 3, h = (warp >> 2) & 1;
-  unsigned long long acc[32];
-  double dacc[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    acc[c] = 0ull;
-    dacc[c] = 0.0;
-  }
-  const bool multi = MODE == 0 && nchunks > kOzFlush;  // more than one 64-bit partial sum (K > 2048)
+  // item -> (pole, front, tile): binary search of the prefix sums
+  auto decode = [&](int it, int& pole, PanelDims& d, int& mt, int& nt) -> bool {
+    pole = it / T;
+    const int t = it - pole * T;
+    int lo = 0, hi = nfronts;  // largest f with s_pref[f] <= t
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_pref[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    if (!panel_dims(fr, fronts, lo, p0, b, d)) return false;
+    tile_coords<MODE, CPLX>(t - s_pref[lo], mt, nt);
+    return true;
+  };
 
   if (warp == kEpiWarps) {
     if (lane == 0) {  // ---- producer
       int na = 0, nbf = 0;
-      for (int kt = 0; kt < nkt && !*fail; ++kt) {
-        const int sb = kt % kSlotsB, ub = kt / kSlotsB;
-        if (ub > 0 && !bar_wait(smem_u32(&empty_b[sb]), (ub - 1) & 1, fail)) {
-          record_fail(&s_fail, 1, kt);
-          break;
-        }
-        bar_expect(smem_u32(&full_b[sb]), uint32_t(S * SB));
-        bulk_load(smem_u32(sB + sb * S * kSliceB), gB + int64_t(kt) * S * SB, uint32_t(S * SB),
-                  smem_u32(&full_b[sb]));
-        ++nbf;
-        bool ok = true;
-        for (int s = 0; s < S; ++s) {
-          const int sa = na % kSlotsA, ua = na / kSlotsA;
-          if (ua > 0 && !bar_wait(smem_u32(&empty_a[sa]), (ua - 1) & 1, fail)) {
-            record_fail(&s_fail, 2, kt);
+      bool ok = true;
+      for (int it = blockIdx.x; it < items && ok && !*fail; it += gridDim.x) {
+        int pole, mt, nt;
+        PanelDims d;
+        if (!decode(it, pole, d, mt, nt)) continue;
+        const int nkt = ceil_div(d.bb, kOzK);
+        const uint8_t* gA = oz.A + int64_t(pole) * oz.A_stride + oz.A_off[d.f] + int64_t(mt) * nkt * S * SA;
+        const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + int64_t(nt) * nkt * S * SB;
+        for (int kt = 0; kt < nkt && ok; ++kt) {
+          const int sb = nbf % kSlotsB, ub = nbf / kSlotsB;
+          if (ub > 0 && !bar_wait(smem_u32(&empty_b[sb]), (ub - 1) & 1, fail)) {
+            record_fail(&s_fail, 1, kt);
             ok = false;
             break;
           }
-          bar_expect(smem_u32(&full_a[sa]), uint32_t(SA));
-          bulk_load(smem_u32(sA + sa * kSliceA), gA + (int64_t(kt) * S + s) * SA, uint32_t(SA),
-                    smem_u32(&full_a[sa]));
-          ++na;
+          bar_expect(smem_u32(&full_b[sb]), uint32_t(S * SB));
+          bulk_load(smem_u32(sB + sb * 6 * kSliceB), gB + int64_t(kt) * S * SB, uint32_t(S * SB),
+                    smem_u32(&full_b[sb]));
+          ++nbf;
+          for (int s = 0; s < S; ++s) {
+            const int sa = na % kSlotsA, ua = na / kSlotsA;
+            if (ua > 0 && !bar_wait(smem_u32(&empty_a[sa]), (ua - 1) & 1, fail)) {
+              record_fail(&s_fail, 2, kt);
+              ok = false;
+              break;
+            }
+            bar_expect(smem_u32(&full_a[sa]), uint32_t(SA));
+            bulk_load(smem_u32(sA + sa * kSliceA), gA + (int64_t(kt) * S + s) * SA, uint32_t(SA),
+                      smem_u32(&full_a[sa]));
+            ++na;
+          }
         }
-        if (!ok) break;
       }
       // every copy issued has landed before the CTA leaves (bounded)
       for (int j = 0; j < kSlotsA; ++j)
@@ -601,150 +622,141 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   } else if (warp == kEpiWarps + 1) {
     if (lane == 0) {  // ---- MMA issuer
       const uint32_t id_pos = idesc(false), id_neg = idesc(true);
-      int na = 0;
-      for (int kt = 0; kt < nkt; ++kt) {
-        const int c = kt / kOzChunk, in_chunk = kt % kOzChunk;
-        if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail)) {
-          record_fail(&s_fail, 4, kt);
+      int na = 0, nbf = 0, ti = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int pole, mt, nt;
+        PanelDims d;
+        if (!decode(it, pole, d, mt, nt)) continue;
+        const int nkt = ceil_div(d.bb, kOzK);
+        if (ti > 0 && !bar_wait(smem_u32(&acc_empty), (ti - 1) & 1, fail)) {  // previous tile drained
+          record_fail(&s_fail, 4, 0);
           break;
         }
-        const int sb = kt % kSlotsB;
-        if (!bar_wait(smem_u32(&full_b[sb]), (kt / kSlotsB) & 1, fail)) {
-          record_fail(&s_fail, 5, kt);
-          break;
-        }
-        bool ok = true;
-        for (int s = 1; s <= S; ++s) {
-          const int sa = na % kSlotsA;
-          if (!bar_wait(smem_u32(&full_a[sa]), (na / kSlotsA) & 1, fail)) {
-            record_fail(&s_fail, 6, kt);
+        for (int kt = 0; kt < nkt && ok; ++kt) {
+          const int sb = nbf % kSlotsB;
+          if (!bar_wait(smem_u32(&full_b[sb]), (nbf / kSlotsB) & 1, fail)) {
+            record_fail(&s_fail, 5, kt);
             ok = false;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t a1 = smem_u32(sA + sa * kSliceA), a2 = a1 + kBlk;  // [Ar; Ai], [Ai; -Ar]
-          for (int t = 1; s + t <= S + 1; ++t) {
-            const uint32_t acc_d = tmem + uint32_t((s + t - 2) * 64);  // diagonal D = s + t
-            const uint32_t br = smem_u32(sB + sb * S * kSliceB + (t - 1) * SB), bi = br + kBlk;
-#pragma unroll
-            for (int ks = 0; ks < kOzK / 16; ++ks) {
-              const uint32_t ko = uint32_t(ks * 256);  // two core matrices along K
-              // the first product into each accumulator of a chunk overwrites
-              // it: for diagonal D that is the pair (1, D - 1) at ks = 0
-              const uint32_t first = (in_chunk == 0 && ks == 0 && s == 1) ? 0u : 1u;
-              mma(acc_d, sdesc(a1 + ko), sdesc(br + ko), id_pos, first);
-              if (CPLX) mma(acc_d, sdesc(a2 + ko), sdesc(bi + ko), id_neg, 1u);
+          for (int s = 1; s <= S; ++s) {
+            const int sa = na % kSlotsA;
+            if (!bar_wait(smem_u32(&full_a[sa]), (na / kSlotsA) & 1, fail)) {
+              record_fail(&s_fail, 6, kt);
+              ok = false;
+              break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a1 = smem_u32(sA + sa * kSliceA), a2 = a1 + kBlk;  // [Ar; Ai], [Ai; -Ar] (or real rows)
+            for (int t = 1; s + t <= S + 1; ++t) {
+              const uint32_t acc_d = tmem + uint32_t((s + t - 2) * 64);  // diagonal D = s + t
+              const uint32_t br = smem_u32(sB + sb * 6 * kSliceB + (t - 1) * SB), bi = br + kBlk;
+#pragma unroll
+              for (int ks = 0; ks < kOzK / 16; ++ks) {
+                const uint32_t ko = uint32_t(ks * 256);  // two core matrices along K
+                // the first product into each accumulator of a tile overwrites
+                // it: for diagonal D that is the pair (1, D - 1) at ks = 0
+                const uint32_t first = (kt == 0 && ks == 0 && s == 1) ? 0u : 1u;
+                mma(acc_d, sdesc(a1 + ko), sdesc(br + ko), id_pos, first);
+                if (CPLX) mma(acc_d, sdesc(a2 + ko), sdesc(bi + ko), id_neg, 1u);
+              }
+            }
+            mma_commit(smem_u32(&empty_a[sa]));
+            ++na;
           }
-          mma_commit(smem_u32(&empty_a[sa]));
-          ++na;
+          if (!ok) break;
+          mma_commit(smem_u32(&empty_b[sb]));
+          ++nbf;
         }
         if (!ok) break;
-        mma_commit(smem_u32(&empty_b[sb]));
-        if (in_chunk == kOzChunk - 1 || kt == nkt - 1) mma_commit(smem_u32(&acc_full));
+        mma_commit(smem_u32(&acc_full));
+        ++ti;
       }
       // every MMA issued has completed before TMEM is read for the last time or freed
       mma_commit(smem_u32(&mma_done));
       if (!bar_wait_all(smem_u32(&mma_done), 0)) record_fail(&s_fail, 7, 0);
     }
-  } else {  // ---- epilogue: exact FP32 integers -> 64-bit integers
-    int pending = 0;
-    for (int ch = 0; ch < nchunks; ++ch) {
+  } else {  // ---- epilogue: exact FP32 integers -> 64-bit integers -> FP64 outputs
+    const int q = warp & 3, h = (warp >> 2) & 1;
+    // complex: lanes 0-63 hold real parts, 64-127 imaginary parts of the
+    // tile's 64 complex rows; real: lane = row of the 128-row tile
+    const int ri = CPLX ? (q & 1) * 32 + lane : q * 32 + lane;
+    const int part = CPLX ? q >> 1 : 0;
+    constexpr int ES = CPLX ? 2 : 1;  // doubles per element
+    int ti = 0;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      int pole, mt, nt;
+      PanelDims d;
+      if (!decode(it, pole, d, mt, nt)) continue;
       bool ok = true;
-      if (lane == 0) ok = bar_wait(smem_u32(&acc_full), ch & 1, fail);
+      if (lane == 0) ok = bar_wait(smem_u32(&acc_full), ti & 1, fail);
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
       if (!ok) {
-        if (lane == 0) record_fail(&s_fail, 8, ch * kOzChunk);
+        if (lane == 0) record_fail(&s_fail, 8, ti);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
+      unsigned long long acc[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] = 0ull;
       for (int D = 2; D <= S + 1; ++D) {
         const int sh = 7 * (S + 1 - D);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int hh = 0; hh < 2; ++hh) {
           uint32_t v[16];
-          const uint32_t addr = tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + half * 16);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15])
-              : "r"(addr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 16), v);
 #pragma unroll
           for (int c = 0; c < 16; ++c)
-            acc[half * 16 + c] +=
+            acc[hh * 16 + c] +=
                 static_cast<unsigned long long>(static_cast<long long>(__float2int_rn(__uint_as_float(v[c])))) << sh;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
-      if (lane == 0) bar_arrive(smem_u32(&acc_empty));
-      if (multi && (++pending == kOzFlush || ch == nchunks - 1)) {
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          dacc[c] += i64_scaled(static_cast<long long>(acc[c]), 0);
-          acc[c] = 0ull;
-        }
-        pending = 0;
-      }
-    }
-  }
-
-  __syncthreads();
-  if (s_fail) {
-    if (threadIdx.x == 0)  // where the wait gave up: mode, site + 16 * K tile, tile
-      atomicMax(oz.fail, 1 + (MODE << 30) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
-  } else if (warp < kEpiWarps) {
-    // complex: lanes 0-63 hold real parts, 64-127 imaginary parts of the
-    // tile's 64 complex rows; real: lane = row of the 128-row tile
-    const int ri = CPLX ? (q & 1) * 32 + lane : q * 32 + lane;
-    const int part = CPLX ? q >> 1 : 0;
-    const int i = mt * TR + ri;  // row of the trailing block
-    if (i < d.mp) {
-      const int ea = s_ea[ri];
-      constexpr int ES = CPLX ? 2 : 1;  // doubles per element
+      if (lane == 0) bar_arrive(smem_u32(&acc_empty));  // TMEM free for the next tile
+      ++ti;
+      const int i = mt * TR + ri;  // row of the trailing block
+      const bool row_in = i < d.mp;
+      // exponent of column h*32 + lane of this tile, broadcast by shuffles below
+      // (every lane takes part; the row test only guards memory accesses)
+      const int jl = nt * kOzRows + h * 32 + lane;
+      const int eb_lane =
+          jl < (MODE == 1 ? d.mp : d.bb) ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + jl] : 0;
+      const int ea = row_in ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
       double* Yb = static_cast<double*>(Yv) + ES * (int64_t(pole) * fr.pool + fr.off[d.f]) + part;
       // Schur: the old values of 16 columns are loaded before any of them is
       // stored, so that their loads are in flight together
 #pragma unroll
       for (int c0 = 0; c0 < 32; c0 += 16) {
         double old[16];
-        if (MODE == 1) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int j = nt * kOzRows + h * 32 + c0 + c;
-            old[c] = (j <= i && j < d.mp) ? Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] : 0.0;
-          }
+        for (int c = 0; c < 16; ++c) {
+          const int j = nt * kOzRows + h * 32 + c0 + c;
+          const bool in = row_in && (MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb));
+          old[c] = (MODE == 1 && in) ? Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] : 0.0;
         }
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int j = nt * kOzRows + h * 32 + c0 + c;
-          const bool in = MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb);
+          const bool in = row_in && (MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb));
+          const int ebc = __shfl_sync(0xFFFFFFFFu, eb_lane, c0 + c);
           if (in) {
-            const int eb = s_eb[h * 32 + c0 + c];
-            const int sc = ea + eb - 7 * (S + 1);
-            double v;
-            if (ea == kNanExp || eb == kNanExp)
-              v = __longlong_as_double(0x7FF8000000000000LL);
-            else if (multi)
-              v = ldexp(dacc[c0 + c], sc);
-            else
-              v = i64_scaled(static_cast<long long>(acc[c0 + c]), sc);
-            if (MODE == 1) {
+            double v = i64_scaled(static_cast<long long>(acc[c0 + c]), ea + ebc - 7 * (S + 1));
+            if (ea == kNanExp || ebc == kNanExp) v = __longlong_as_double(0x7FF8000000000000LL);
+            if (MODE == 1)
               Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] = old[c] - v;
-            } else if (MODE == 2) {
+            else
               Yb[ES * ((d.q0 + i) + int64_t(d.m) * (p0 + j))] = v;
-            } else {
-              Yb[ES * ((d.q0 + i) + int64_t(d.m) * (p0 + j))] = -v;
-              Yb[ES * ((p0 + j) + int64_t(d.m) * (d.q0 + i))] = -v;
-            }
           }
         }
       }
     }
   }
+
+  __syncthreads();
+  if (s_fail && threadIdx.x == 0)  // where the wait gave up: mode, site + 16 * K tile, CTA
+    atomicMax(oz.fail, 1 + (MODE << 28) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -774,39 +786,6 @@ constexpr int kFThreads = (kFWorkers + 1) * 32;
 __device__ __forceinline__ uint64_t sdesc16(uint32_t saddr) {
   return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(256 >> 4) << 32) |
          (uint64_t(1) << 46);
-}
-
-// 32 lanes x 16 / 32 consecutive TMEM columns of this warp's lane quarter.
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t addr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(addr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-      : "memory");
 }
 
 // The integer nearest to x 2^(7 S - e) (|x| < 2^e), from the bit pattern.
@@ -1181,26 +1160,30 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
 
 }  // namespace
 
-size_t oz_smem_bytes(int S) { return size_t(kSlotsA) * kSliceA + size_t(kSlotsB) * S * kSliceB; }
+constexpr int kMaxPersistFronts = 4096;  // fronts per launch of the persistent GEMM (prefix sums in smem)
+
+size_t oz_smem_bytes(int /*S*/) {
+  return size_t(kSlotsA) * kSliceA + size_t(kSlotsB) * 6 * kSliceB + sizeof(int) * (kMaxPersistFronts + 1);
+}
 
 // Scratch bytes of one front (per pole) whose first panel leaves mp rows
-// below it, for both phases: Takahashi A = Y[S,S] (mp x mp), B = L[S,P]
-// (bb x mp); Schur A = L[S,P] (mp x bb), B = W[S,P] (mp x bb).
+// below it, for the phases that stage slices in HBM: Schur A = L[S,P]
+// (mp x bb) and B = W[S,P] (mp x bb); panel solve A = W[S,P], B = D^-1;
+// the fused Takahashi step stages only B = L[S,P] (bb x mp, 16-deep tiles).
 int64_t oz_front_bytes_A(int64_t mp, int b, int S) {
   const int64_t rt = (mp + kOzRows - 1) / kOzRows;
-  return rt * std::max<int64_t>((mp + kOzK - 1) / kOzK, (b + kOzK - 1) / kOzK) * S * kSliceA;
+  return rt * ((b + kOzK - 1) / kOzK) * S * kSliceA;
 }
 
 int64_t oz_front_bytes_B(int64_t mp, int b, int S) {
-  const int64_t tak = ((b + kOzRows - 1) / kOzRows) * ((mp + kOzK - 1) / kOzK);
-  const int64_t sch = ((mp + kOzRows - 1) / kOzRows) * ((b + kOzK - 1) / kOzK);
-  return std::max(tak, sch) * S * kSliceB;
+  const int64_t tak = ((mp + kFK - 1) / kFK) * S * kFSliceB;
+  const int64_t sch = ((mp + kOzRows - 1) / kOzRows) * ((b + kOzK - 1) / kOzK) * S * kSliceB;
+  return std::max(tak, sch);
 }
 
 cudaError_t oz_configure(int S) {
   const int smem = int(oz_smem_bytes(S));
-  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1217,11 +1200,44 @@ int64_t oz_front_bytes_B_real(int64_t mp, int b, int S) {
   return ((mp + kOzRows - 1) / kOzRows) * ((b + kOzK - 1) / kOzK) * S * kBlk;
 }
 
+namespace {
+
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 148;
+  }
+  return cached[dev];
+}
+
+// One persistent launch per group of at most kMaxPersistFronts fronts; the
+// grid is one CTA per SM (fewer when the launch holds fewer tiles).
+template <int MODE, bool CPLX>
+void launch_persistent(void* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0, int b,
+                       int S, const OzScratch& oz, int nb, cudaStream_t st) {
+  if (nfronts <= 0 || max_tiles <= 0) return;
+  for (int f0 = 0; f0 < nfronts; f0 += kMaxPersistFronts) {
+    const int nf = std::min(kMaxPersistFronts, nfronts - f0);
+    const int64_t bound = int64_t(max_tiles) * nf * nb;
+    const int grid = int(std::min<int64_t>(sm_count(), bound));
+    k_oz_gemm<MODE, CPLX><<<grid, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts + f0, nf, p0, b, S, nb, oz);
+  }
+}
+
+}  // namespace
+
 int oz_schur_tiles_real(int mp) {
   const int nmt = ceil_div(mp, 2 * kOzRows), nnt = ceil_div(mp, kOzRows);
-  int t = 0;
-  for (int r = 0; r < nmt; ++r) t += min(2 * r + 2, nnt);
-  return t;
+  return mp > 0 ? nmt * (nmt + 1) - (2 * nmt - nnt) : 0;
+}
+
+int oz_schur_tiles(int mp) {
+  const int nmt = ceil_div(mp, kOzRows);
+  return nmt * (nmt + 1) / 2;
 }
 
 void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
@@ -1234,16 +1250,7 @@ void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int3
 
 void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
-  if (nfronts <= 0 || max_tiles <= 0) return;
-  dim3 gg(max_tiles, nfronts, nb);
-  k_oz_gemm<1, false><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
-}
-
-int oz_offdiag_tiles(int mp) { return ceil_div(mp, kOzRows); }
-
-int oz_schur_tiles(int mp) {
-  const int nmt = ceil_div(mp, kOzRows);
-  return nmt * (nmt + 1) / 2;
+  launch_persistent<1, false>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st);
 }
 
 void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
@@ -1256,25 +1263,7 @@ void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t*
 
 void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
                           int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
-  if (nfronts <= 0 || max_tiles <= 0) return;
-  dim3 gg(max_tiles, nfronts, nb);
-  k_oz_gemm<1, true><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
-}
-
-void launch_oz_slice_offdiag(const double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts,
-                             int nfronts, int max_rows, int p0, int b, int S, const OzScratch& oz, int nb,
-                             cudaStream_t st) {
-  if (nfronts <= 0 || max_rows <= 0) return;
-  const int groupsA = (max_rows + 7) / 8, groupsB = (b + 7) / 8;
-  dim3 g(groupsA + groupsB, nfronts, nb);
-  k_oz_slice<0><<<g, 256, 0, st>>>(Y, const_cast<double2*>(F), fr, fronts, p0, b, S, groupsA, oz);
-}
-
-void launch_oz_gemm_offdiag(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
-                            int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
-  if (nfronts <= 0 || max_tiles <= 0) return;
-  dim3 gg(max_tiles, nfronts, nb);
-  k_oz_gemm<0, true><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(Y, fr, fronts, p0, b, S, oz);
+  launch_persistent<1, true>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st);
 }
 
 // Split-precision panel solve L[S,P] = W[S,P] D^-1 (complex poles and real
@@ -1288,8 +1277,7 @@ void launch_oz_panel(double2* F, const DevFronts& fr, const int32_t* fronts, int
     dim3 g(groupsA + groupsB, nfronts, nb);
     k_oz_slice<2><<<g, 256, 0, st>>>(nullptr, F, fr, fronts, p0, b, S, groupsA, oz);
   } else {
-    dim3 gg(ceil_div(max_mp, kOzRows), nfronts, nb);
-    k_oz_gemm<2, true><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
+    launch_persistent<2, true>(F, fr, fronts, nfronts, ceil_div(max_mp, kOzRows), p0, b, S, oz, nb, st);
   }
 }
 
@@ -1301,8 +1289,7 @@ void launch_oz_panel_real(double* F, const DevFronts& fr, const int32_t* fronts,
     dim3 g(groupsA + groupsB, nfronts, nb);
     k_oz_slice_real<2><<<g, 256, 0, st>>>(F, fr, fronts, p0, b, S, groupsA, oz);
   } else {
-    dim3 gg(ceil_div(max_mp, 2 * kOzRows), nfronts, nb);
-    k_oz_gemm<2, false><<<gg, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts, p0, b, S, oz);
+    launch_persistent<2, false>(F, fr, fronts, nfronts, ceil_div(max_mp, 2 * kOzRows), p0, b, S, oz, nb, st);
   }
 }
 
