@@ -67,11 +67,15 @@ typedef struct pexsi_opts {
   int32_t leaf_cols;       /* nested-dissection leaf size in columns (default 96)    */
   int32_t amalgamate;      /* 1: relaxed supernode amalgamation (default), 0: off    */
   int32_t max_batch;       /* poles / shifts per device batch, 0 = automatic         */
-  int32_t split_slices;    /* 0: FP64 GEMMs (default). 2..6: split-precision
-                              Takahashi GEMM Y[S,P] = -Y[S,S] L[S,P] on the tcgen05
-                              tensor cores with this many bf16 slices per operand
-                              (Ozaki scheme; 6 slices ~ 43 bits); the diagonal-block
-                              inverses, the Schur updates and the pole sum stay FP64 */
+  int32_t split_slices;    /* 0: FP64 GEMMs (default). 2..6: the supernode GEMMs
+                              (panel solve L = W D^-1, Schur update F -= L W^T,
+                              Takahashi step Y[S,P] = -Y[S,S] L[S,P] and Y[P,P] =
+                              D^-1 - L[S,P]^T Y[S,P]; real ones of the inertia
+                              LDL^T too) run on the tcgen05 tensor cores as exact
+                              products of this many bf16 slices per operand (Ozaki
+                              scheme; 6 slices ~ 42 bits), FP64 in and out; the
+                              diagonal-block inverses and the pole sum stay FP64.
+                              Requires panel = 64; other values are INVALID_ARG. */
   int64_t hbm_budget;      /* bytes of device workspace the batch may use, 0 = auto  */
 } pexsi_opts;
 

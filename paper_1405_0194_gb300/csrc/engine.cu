@@ -299,13 +299,30 @@ void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Pro
         launch_selinv_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
         pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by);
       }
-      a = pf.begin(st);
-      launch_selinv_diag_partial(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.row_tiles,
-                                 p0, b, sh, st);
-      pf.end(a, P_DPART, st, nb * w.dpart_fl, nb * w.dpart_by);
-      a = pf.begin(st);
-      launch_selinv_diag_reduce(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, p0, b, sh, st);
-      pf.end(a, P_DRED, st, 0.0, nb * w.dred_by);
+      if (p->oz_slices > 0) {
+        const int S = p->oz_slices;
+        OzScratch oz = split_scratch(p, ws, false);
+        a = pf.begin(st);
+        launch_oz_dpart(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.max_mp, p0, b, S, oz,
+                        sh.nb, st, 0);
+        pf.end(a, P_SLICE, st, 0.0, nb * w.dpart_by / 2);
+        a = pf.begin(st);
+        launch_oz_dpart(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.max_mp, p0, b, S, oz,
+                        sh.nb, st, 1);
+        pf.end(a, P_DPART, st, nb * w.dpart_fl, nb * w.dpart_by, 1, nb * w.dpart_fl * S * (S + 1) / 2.0);
+        a = pf.begin(st);
+        launch_oz_dpart(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.max_mp, p0, b, S, oz,
+                        sh.nb, st, 2);
+        pf.end(a, P_DRED, st, 0.0, nb * w.dred_by);
+      } else {
+        a = pf.begin(st);
+        launch_selinv_diag_partial(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.row_tiles,
+                                   p0, b, sh, st);
+        pf.end(a, P_DPART, st, nb * w.dpart_fl, nb * w.dpart_by);
+        a = pf.begin(st);
+        launch_selinv_diag_reduce(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, p0, b, sh, st);
+        pf.end(a, P_DRED, st, 0.0, nb * w.dred_by);
+      }
     }
   }
   ck(cudaGetLastError(), "selinv kernels");
@@ -607,7 +624,7 @@ void build_split_layout(pexsi_plan* p, std::vector<int64_t>& a_off, std::vector<
       sb += oz_front_bytes_B(mp, b, p->oz_slices);
       sar += oz_front_bytes_A_real(mp, b, p->oz_slices);
       sbr += oz_front_bytes_B_real(mp, b, p->oz_slices);
-      xa += mp;
+      xa += std::max<int64_t>(b, mp);  // rows of A, or the panel columns (Y[S,P] exponents)
       xb += std::max<int64_t>(b, mp);
     }
     p->ozA_stride = std::max(p->ozA_stride, sa);
@@ -762,8 +779,9 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
       if (p->opts.panel <= 0) p->opts.panel = def.panel;
       if (p->opts.leaf_cols <= 0) p->opts.leaf_cols = def.leaf_cols;
     }
+    // the split-precision path tiles the panel as one 64-wide block
     if (p->opts.panel < 16 || p->opts.panel > 64 || p->opts.split_slices < 0 || p->opts.split_slices > 6 ||
-        p->opts.split_slices == 1) {
+        p->opts.split_slices == 1 || (p->opts.split_slices > 0 && p->opts.panel != 64)) {
       delete p;
       return PEXSI_ERR_INVALID_ARG;
     }

@@ -108,6 +108,12 @@ void launch_scaled_imag(const double2* Y, const int64_t* entry_pos, int64_t nnz,
 // exponents of A and slices B, prep = false runs the GEMM.
 void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
                          int max_mp, int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool prep);
+// Split-precision Y[P,P] = D^-1 - L[S,P]^T Y[S,P] (panel width 64): stage 0
+// exponents of the Y[S,P] columns, stage 1 split-K GEMM into `part` (exact
+// int64 sums per 256-deep K range), stage 2 reduction and symmetrisation.
+void launch_oz_dpart(double2* Y, const double2* F, double2* part, const int64_t* part_off, int64_t part_stride,
+                     const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp, int p0, int b, int S,
+                     const OzScratch& oz, int nb, cudaStream_t st, int stage);
 // Split-precision Schur update F[S,S] -= L[S,P] W[S,P]^T (lower triangle):
 // slicing of L rows and W rows, then the tcgen05 GEMM with an FP64
 // read-modify-write (max_tiles = max over fronts of oz_schur_tiles(m_p)).

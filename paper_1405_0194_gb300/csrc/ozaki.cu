@@ -880,13 +880,23 @@ __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__
   }
 }
 
-// One CTA per 64-row tile of S (front, pole). Warps 0-7: workers (warps 0-3
-// produce the even K tiles, 4-7 the odd ones: thread (row r, octet o) cuts
-// 8 entries of row r of A into S x 3 words; every warp also drains its part
-// of TMEM after each chunk); warp 8: TMEM owner and MMA issuer.
+// KIND 0, Takahashi step: one CTA per 64-row tile of S (front, pole); A =
+//   Y[S,S] rows cut on the fly, B = L[S,P] slices staged by k_oz_tak_prep.
+// KIND 1, the product L[S,P]^T Y[S,P] of Y[P,P] = D^-1 - L[S,P]^T Y[S,P]:
+//   one CTA per 256-deep K range (front, pole); A = L[S,P] columns and B =
+//   Y[S,P] columns both cut on the fly; the exact int64 sums of the range go
+//   to `part` and k_oz_dpart_reduce adds the ranges.
+// Warps 0-7: workers (warps 0-3 produce the even K tiles, 4-7 the odd ones:
+// thread (row r, octet o) cuts 8 entries of row r into S x 3 words of A (and
+// for KIND 1, S x 2 words of B); every warp also drains its part of TMEM
+// after each chunk); warp 8: TMEM owner and MMA issuer.
+template <int KIND>
 __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restrict__ Y, DevFronts fr,
                                                               const int32_t* __restrict__ fronts, int p0, int b,
-                                                              int S, OzScratch oz) {
+                                                              int S, OzScratch oz, const double2* __restrict__ F,
+                                                              long long* __restrict__ part,
+                                                              const int64_t* __restrict__ part_off, int64_t part_stride) {
+  constexpr bool DP = KIND == 1;
   extern __shared__ __align__(128) uint8_t osm[];
   __shared__ __align__(8) uint64_t full_a[kFSlots], full_b[kFSlots], empty[kFSlots];
   __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
@@ -897,22 +907,26 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
   PanelDims d;
   if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
   if (*static_cast<volatile int*>(oz.fail)) return;
-  const int mt = blockIdx.x;
-  if (mt >= ceil_div(d.mp, kOzRows)) return;
+  const int mt = DP ? 0 : int(blockIdx.x);
+  if (DP ? int(blockIdx.x) * kFChunk >= ceil_div(d.mp, kFK) : mt >= ceil_div(d.mp, kOzRows)) return;
   const int pole = blockIdx.z;
-  const int nkt = ceil_div(d.mp, kFK);
+  // K tiles kt0 .. kt0 + nkt - 1 (KIND 1: one 256-deep range per CTA)
+  const int kt0 = DP ? int(blockIdx.x) * kFChunk : 0;
+  const int nkt = DP ? min(kFChunk, ceil_div(d.mp, kFK) - kt0) : ceil_div(d.mp, kFK);
   const int nchunks = ceil_div(nkt, kFChunk);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* fail = &s_fail;
   const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f];
 
   if (threadIdx.x < 2 * kOzRows) {
-    if (threadIdx.x < kOzRows) {
+    const int* exa = oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f];
+    const int* exb = oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];
+    if (threadIdx.x < kOzRows) {  // rows of A: Y[S,S] rows, or L[S,P] columns
       const int i = mt * kOzRows + threadIdx.x;
-      s_ea[threadIdx.x] = i < d.mp ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
-    } else {
+      s_ea[threadIdx.x] = DP ? (i < d.bb ? exb[i] : 0) : (i < d.mp ? exa[i] : 0);
+    } else {  // rows of B: L[S,P] columns, or Y[S,P] columns
       const int j = threadIdx.x - kOzRows;
-      s_eb[j] = j < d.bb ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + j] : 0;
+      s_eb[j] = j < d.bb ? (DP ? exa[j] : exb[j]) : 0;
     }
   }
   if (threadIdx.x == 0) {
@@ -937,7 +951,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const bool multi = nchunks > kOzFlush;
+  const bool multi = !DP && nchunks > kOzFlush;
 
   const int q = warp & 3, h = (warp >> 2) & 1;
   // this warp's exact int64 partial sums live in TMEM columns 384 + 64 h ..
@@ -958,7 +972,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         }
         const int slot = kt % kFSlots;
         const uint32_t par = (kt / kFSlots) & 1;
-        if (!bar_wait(smem_u32(&full_a[slot]), par, fail) || !bar_wait(smem_u32(&full_b[slot]), par, fail)) {
+        if (!bar_wait(smem_u32(&full_a[slot]), par, fail) || (!DP && !bar_wait(smem_u32(&full_b[slot]), par, fail))) {
           record_fail(&s_fail, 6, kt);
           break;
         }
@@ -985,9 +999,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
     const int item = q * 32 + lane;        // 0..127
     const int r = item & (kOzRows - 1), oct = item >> 6;
     const int i = mt * kOzRows + r;
-    const bool rowok = i < d.mp;
-    const int e = s_ea[r];
-    const double2* col = Y + int64_t(pole) * fr.pool + fr.off[d.f] + int64_t(d.q0 + (rowok ? i : 0)) * d.m + d.q0;
+    const bool rowok = DP ? r < d.bb : i < d.mp;
+    const int e = s_ea[r], eB = s_eb[r];
+    const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
+    // A row: KIND 0 column q0 + i of Y (rows q0..), KIND 1 panel column p0 + r of L
+    const double2* col = DP ? F + fo + int64_t(p0 + (rowok ? r : 0)) * d.m + d.q0
+                            : Y + fo + int64_t(d.q0 + (rowok ? i : 0)) * d.m + d.q0;
+    // B row (KIND 1): panel column p0 + r of Y, rows q0..
+    const double2* colB = Y + fo + int64_t(p0 + (rowok ? r : 0)) * d.m + d.q0;
     const uint32_t wbase = uint32_t((r >> 3) * 256 + oct * 128 + (r & 7) * 16);
     int drained = 0, pending = 0;
     bool ok = true;
@@ -1065,17 +1084,54 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         break;
       }
       uint8_t* sbase = osm + slot * kFSlot;
-      if (item == 0) {  // B: all S slices of this K tile, one bulk copy
+      if (!DP && item == 0) {  // B: all S slices of this K tile, one bulk copy
         bar_expect(smem_u32(&full_b[slot]), uint32_t(S * kFSliceB));
         bulk_load(smem_u32(sbase + kFSlotA), gB + int64_t(kt) * S * kFSliceB, uint32_t(S * kFSliceB),
                   smem_u32(&full_b[slot]));
         atomicMax(&s_last_b[slot], kt);
       }
+      if (DP) {  // B: 8 entries of Y[S,P] column r, cut into Br, Bi words
+        long long XB[16];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int k = (kt0 + kt) * kFK + oct * 8 + u;
+          double2 v = make_double2(0.0, 0.0);
+          if (rowok && k < d.mp) v = colB[k];
+          XB[2 * u] = fixed_point(v.x, eB, S);
+          XB[2 * u + 1] = fixed_point(v.y, eB, S);
+        }
+#pragma unroll
+        for (int sl = 5; sl >= 0; --sl) {
+          if (sl >= S) continue;
+          int dg[16];
+#pragma unroll
+          for (int t = 0; t < 16; ++t) {
+            if (sl > 0) {
+              dg[t] = int((XB[t] + 64) & 127) - 64;
+              XB[t] = (XB[t] - dg[t]) >> 7;
+            } else {
+              dg[t] = int(XB[t]);
+            }
+          }
+          uint4 wre, wim;
+          wre.x = bf16_bits(dg[0]) | (bf16_bits(dg[2]) << 16);
+          wre.y = bf16_bits(dg[4]) | (bf16_bits(dg[6]) << 16);
+          wre.z = bf16_bits(dg[8]) | (bf16_bits(dg[10]) << 16);
+          wre.w = bf16_bits(dg[12]) | (bf16_bits(dg[14]) << 16);
+          wim.x = bf16_bits(dg[1]) | (bf16_bits(dg[3]) << 16);
+          wim.y = bf16_bits(dg[5]) | (bf16_bits(dg[7]) << 16);
+          wim.z = bf16_bits(dg[9]) | (bf16_bits(dg[11]) << 16);
+          wim.w = bf16_bits(dg[13]) | (bf16_bits(dg[15]) << 16);
+          uint8_t* pb = sbase + kFSlotA + sl * kFSliceB + wbase;
+          *reinterpret_cast<uint4*>(pb) = wre;
+          *reinterpret_cast<uint4*>(pb + kFBlk) = wim;
+        }
+      }
       // A: 8 entries of row r at k = 16 kt + 8 oct .. + 7, as fixed-point integers
       long long X[16];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int k = kt * kFK + oct * 8 + u;
+        const int k = (kt0 + kt) * kFK + oct * 8 + u;
         double2 v = make_double2(0.0, 0.0);
         if (rowok && k < d.mp) v = col[k];
         X[2 * u] = fixed_point(v.x, e, S);
@@ -1128,7 +1184,21 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
   if (s_fail) {
     if (threadIdx.x == 0)
       atomicMax(oz.fail, 1 + (3 << 28) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
-  } else if (warp < kFWorkers) {
+  } else if (DP && warp < kFWorkers) {
+    // the range's exact sums: lane row (0-63 real, 64-127 imaginary parts of
+    // row p of the product), 64 columns q, as int64 in `part`
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    long long* pp = part + (int64_t(pole) * part_stride + part_off[d.f]) * 2 +
+                    int64_t(blockIdx.x) * (2 * kOzRows * kOzRows) + int64_t(q * 32 + lane) * kOzRows + h * 32;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      uint32_t w[32];
+      tmem_ld32(tsum + hh * 32, w);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        pp[hh * 16 + c] = static_cast<long long>((static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c]);
+    }
+  } else if (!DP && warp < kFWorkers) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int ea = orow < d.mp ? s_ea[orow - mt * kOzRows] : 0;
 #pragma unroll
@@ -1156,6 +1226,80 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == kFWorkers) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// Exponents of the panel columns of Y[S,P] (rows q0..m-1) into exA[0..bb):
+// one warp per column; grid (ceil(b / 8), fronts, poles).
+__global__ void __launch_bounds__(256) k_oz_col_exp(const double2* __restrict__ Y, DevFronts fr,
+                                                    const int32_t* __restrict__ fronts, int p0, int b, OzScratch oz) {
+  PanelDims d;
+  if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (j >= d.bb) return;
+  const int pole = blockIdx.z;
+  const double2* col = Y + int64_t(pole) * fr.pool + fr.off[d.f] + int64_t(p0 + j) * d.m + d.q0;
+  uint32_t mx = 0;
+  for (int k = lane; k < d.mp; k += 32) {
+    const double2 v = col[k];
+    mx = max(mx, max(uint32_t(__double2hiint(v.x)) & 0x7FFFFFFFu, uint32_t(__double2hiint(v.y)) & 0x7FFFFFFFu));
+  }
+  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  if (lane == 0)
+    oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + j] =
+        mx >= 0x7FF00000u ? kNanExp : (mx != 0 ? int(mx >> 20) - 1022 : 0);
+}
+
+// (double) of an exact 128-bit sum: high and low parts, each rounded once.
+__device__ __forceinline__ double i128_scaled(__int128 v, int sc) {
+  const long long hi = static_cast<long long>(v >> 62);
+  const long long lo = static_cast<long long>(v - (static_cast<__int128>(hi) << 62));
+  return i64_scaled(hi, sc + 62) + i64_scaled(lo, sc);
+}
+
+// Y[P,P] = D^-1 - L[S,P]^T Y[S,P]: the K ranges' exact int64 sums added in
+// 128-bit integers (order-free, hence deterministic), scaled by the row and
+// column exponents, subtracted from D^-1 (in the diagonal block of F) and
+// symmetrised; one CTA per (front, pole).
+__global__ void __launch_bounds__(256) k_oz_dpart_reduce(double2* __restrict__ Y, const double2* __restrict__ F,
+                                                         const long long* __restrict__ part,
+                                                         const int64_t* __restrict__ part_off, int64_t part_stride,
+                                                         DevFronts fr, const int32_t* __restrict__ fronts, int p0,
+                                                         int b, int S, OzScratch oz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tmp = reinterpret_cast<double2*>(smem_raw);  // bb x bb
+  PanelDims d;
+  panel_dims(fr, fronts, blockIdx.x, p0, b, d);  // m_p = 0 still needs Y[P,P] = D^-1
+  if (p0 >= d.s) return;
+  const int pole = blockIdx.y;
+  const int nsplit = d.mp > 0 ? ceil_div(ceil_div(d.mp, kFK), kFChunk) : 0;
+  const int64_t base = int64_t(pole) * fr.pool + fr.off[d.f];
+  const long long* pp = part + (int64_t(pole) * part_stride + part_off[d.f]) * 2;
+  const int* exa = oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f];  // Y[S,P] columns
+  const int* exb = oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];  // L[S,P] columns
+  for (int idx = threadIdx.x; idx < d.bb * d.bb; idx += blockDim.x) {
+    const int r = idx % d.bb, c = idx / d.bb;
+    __int128 re = 0, im = 0;
+    for (int t = 0; t < nsplit; ++t) {
+      re += pp[int64_t(t) * 2 * kOzRows * kOzRows + int64_t(r) * kOzRows + c];
+      im += pp[int64_t(t) * 2 * kOzRows * kOzRows + int64_t(kOzRows + r) * kOzRows + c];
+    }
+    const int ea = exb[r], eb = exa[c];
+    double2 v = F[base + (p0 + r) + int64_t(d.m) * (p0 + c)];
+    if (ea == kNanExp || eb == kNanExp) {
+      v = make_double2(__longlong_as_double(0x7FF8000000000000LL), __longlong_as_double(0x7FF8000000000000LL));
+    } else {
+      const int sc = ea + eb - 7 * (S + 1);
+      v.x -= i128_scaled(re, sc);
+      v.y -= i128_scaled(im, sc);
+    }
+    tmp[r + d.bb * c] = v;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < d.bb * d.bb; idx += blockDim.x) {
+    const int r = idx % d.bb, c = idx / d.bb;
+    const double2 a = tmp[r + d.bb * c], t = tmp[c + d.bb * r];
+    Y[base + (p0 + r) + int64_t(d.m) * (p0 + c)] = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y + t.y));
+  }
 }
 
 }  // namespace
@@ -1188,7 +1332,12 @@ cudaError_t oz_configure(int S) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_oz_tak_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSlots * kFSlot));
+    e = cudaFuncSetAttribute(k_oz_tak_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSlots * kFSlot));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_oz_tak_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSlots * kFSlot));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_oz_dpart_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(double2) * kOzRows * kOzRows));
   return e;
 }
 
@@ -1304,7 +1453,29 @@ void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, cons
     k_oz_tak_prep<<<g, 256, 0, st>>>(Y, F, fr, fronts, p0, b, S, groupsA, oz);
   } else {
     dim3 gg(ceil_div(max_mp, kOzRows), nfronts, nb);
-    k_oz_tak_fused<<<gg, kFThreads, size_t(kFSlots) * kFSlot, st>>>(Y, fr, fronts, p0, b, S, oz);
+    k_oz_tak_fused<0><<<gg, kFThreads, size_t(kFSlots) * kFSlot, st>>>(Y, fr, fronts, p0, b, S, oz, nullptr,
+                                                                      nullptr, nullptr, 0);
+  }
+}
+
+// Split-precision Y[P,P] = D^-1 - L[S,P]^T Y[S,P]: stage 0 finds the
+// exponents of the Y[S,P] columns, stage 1 runs the split-K GEMM into
+// `part` (int64 sums per 256-deep range), stage 2 reduces and symmetrises.
+void launch_oz_dpart(double2* Y, const double2* F, double2* part, const int64_t* part_off, int64_t part_stride,
+                     const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp, int p0, int b, int S,
+                     const OzScratch& oz, int nb, cudaStream_t st, int stage) {
+  if (nfronts <= 0 || (stage < 2 && max_mp <= 0)) return;
+  if (stage == 0) {
+    dim3 g(ceil_div(b, 8), nfronts, nb);
+    k_oz_col_exp<<<g, 256, 0, st>>>(Y, fr, fronts, p0, b, oz);
+  } else if (stage == 1) {
+    dim3 g(ceil_div(ceil_div(max_mp, kFK), kFChunk), nfronts, nb);
+    k_oz_tak_fused<1><<<g, kFThreads, size_t(kFSlots) * kFSlot, st>>>(
+        Y, fr, fronts, p0, b, S, oz, F, reinterpret_cast<long long*>(part), part_off, part_stride);
+  } else {
+    dim3 g(nfronts, nb);
+    k_oz_dpart_reduce<<<g, 256, sizeof(double2) * kOzRows * kOzRows, st>>>(
+        Y, F, reinterpret_cast<const long long*>(part), part_off, part_stride, fr, fronts, p0, b, S, oz);
   }
 }
 

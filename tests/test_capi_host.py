@@ -74,6 +74,17 @@ def test_setup_rejects_bad_patterns():
     assert e.value.code == -1
 
 
+def test_setup_rejects_bad_split_options():
+    s = ns.make_chain(natoms=8)
+    for split, panel in ((1, 64), (7, 64), (-1, 64), (6, 32), (2, 48)):
+        with pytest.raises(px.PexsiError) as e:
+            px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=-1, split_slices=split,
+                                                                                panel=panel))
+        assert e.value.code == -1
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=-1, split_slices=6))
+    px.pexsi_plan_destroy(plan)
+
+
 def test_host_only_plan_refuses_numeric_calls():
     s = ns.make_chain(natoms=8)
     plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=host_opts())

@@ -89,16 +89,16 @@ def test_split_selinv_error_falls_with_slices(cases):
 
 def test_split_matches_fp64_gpu_path_at_full_size():
     """fluid512 (n = 11,776) in the benchmark's launch configuration (a
-    10-pole batch): split-precision DM against the FP64 GPU path."""
+    20-pole batch): split-precision DM against the FP64 GPU path."""
     s = ns.make_fluid(nmol=512, seed=0)
-    mu, dE = 0.0, 2.5
+    mu, dE = ns.mu_and_delta_e(s)
     dH = torch.from_numpy(s.H).cuda(); dS = torch.from_numpy(s.S).cuda()
     outs = []
     for k in (0, 6):
-        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(max_batch=10, split_slices=k))
+        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(max_batch=20, split_slices=k))
         out = torch.zeros(3, s.nnz, dtype=torch.float64, device="cuda")
         st = torch.cuda.current_stream().cuda_stream
-        info = px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, 60, dE, 0, 10, 0,
+        info = px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, 60, dE, 0, 20, 0,
                                   out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), st, want_info=True)
         px.pexsi_plan_destroy(plan)
         outs.append((out.cpu().numpy(), info))
