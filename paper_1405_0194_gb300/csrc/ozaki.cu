@@ -17,8 +17,11 @@
 // [Ai; -Ar] (P2); with B = Br + i Bi (64 complex columns as 64 real rows),
 //   P1 Br^T + P2 (-Bi)^T = [Ar Br - Ai Bi; Ai Br + Ar Bi] = [Re; Im],
 // the -Bi coming from the MMA's negate-B bit. So each slice pair (s, t) is
-// two M = 128, N = 64 MMAs per 16-deep K step into ONE accumulator, and the
-// slice tile of A stores the three 64-row blocks Ar, Ai, -Ar back to back.
+// two M = 128, N = 64 products per 16-deep K step into ONE accumulator, and
+// the slice tile of A stores the three 64-row blocks Ar, Ai, -Ar back to
+// back. The B slices of a K tile are stored Br of slices 1..S, then Bi of
+// slices 1..S, so the products of slice s of A with up to four consecutive
+// B slices are one MMA of N = 64 g.
 //
 // A product of two slices is exact in FP32; the tensor core adds them in FP32
 // accumulators in TMEM, one accumulator (64 columns) per "diagonal"
@@ -37,8 +40,9 @@
 // core-matrix layout the MMA descriptors read: a block of R rows x 32 k of
 // one slice stores element (r, k) at byte (r/8)*512 + (k/8)*128 + (r%8)*16 +
 // (k%8)*2 (LBO 128 B, SBO 512 B). One (row tile, K tile) holds the S slices
-// one after another: 12 KiB each for A (Ar, Ai, -Ar), 8 KiB each for B
-// (Br, Bi); so one bulk async copy stages a slice of A or all slices of B.
+// one after another: 12 KiB each for A (Ar, Ai, -Ar); for B the S blocks of
+// Br, then the S blocks of Bi (4 KiB each); so one bulk async copy stages a
+// slice of A or all slices of B.
 //
 // The GEMM CTAs are warp-specialised: a producer streams slices (bulk async
 // copies with mbarrier transaction counts, or slices cut in shared memory by
@@ -81,10 +85,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
          (uint64_t(1) << 46);
 }
 
+// The same for 16-deep K tiles: SBO = 256 B.
+__device__ __forceinline__ uint64_t sdesc16(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(256 >> 4) << 32) |
+         (uint64_t(1) << 46);
+}
+
 // Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major,
-// N = 64, M = 128; optionally B negated.
-__device__ __forceinline__ uint32_t idesc(bool negate_b) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_b ? (1u << 14) : 0u) | (uint32_t(64 >> 3) << 17) |
+// M = 128, N = 64 g; optionally B negated.
+__host__ __device__ constexpr uint32_t idesc(int g, bool negate_b) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (negate_b ? (1u << 14) : 0u) | (uint32_t(64 * g >> 3) << 17) |
          (uint32_t(128 >> 4) << 24);
 }
 
@@ -155,6 +165,57 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
 // Arrives on `bar` once every tcgen05.mma this thread issued so far is done.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Products of one slice of A with the B slices T0 + 1 .. T0 + G of a K tile
+// (KSTEPS steps of 16): the G slices of Br (and of Bi) are consecutive 64-row
+// blocks of BLK bytes, and the accumulators of their diagonals consecutive
+// 64-column blocks of TMEM, so one MMA with N = 64 G covers all G diagonals.
+// a1, a2, br, bi: descriptors of [Ar; Ai], [Ai; -Ar], Br slice 1, Bi slice 1
+// (real operands: a1 and br only); acc: the TMEM column of diagonal s + 1.
+template <bool CPLX, int KSTEPS, int BLK, int T0, int G>
+__device__ __forceinline__ void mma_group(uint32_t acc, uint64_t a1, uint64_t a2, uint64_t br, uint64_t bi,
+                                          uint32_t first) {
+#pragma unroll
+  for (int ks = 0; ks < KSTEPS; ++ks) {
+    const uint64_t ko = uint64_t(ks * 16);  // two core matrices along K (256 B, in 16-byte units)
+    const uint64_t bo = uint64_t(T0 * BLK / 16) + ko;
+    mma(acc + uint32_t(T0 * 64), a1 + ko, br + bo, idesc(G, false), ks == 0 ? first : 1u);
+    if (CPLX) mma(acc + uint32_t(T0 * 64), a2 + ko, bi + bo, idesc(G, true), 1u);
+  }
+}
+
+// All products of slice s of A with the B slices t = 1 .. c (c = S + 1 - s,
+// the pairs s + t <= S + 1), c diagonals in groups of at most four. The MMA
+// of N = 64 is bound by its operand fetch from shared memory (6 KiB in 48
+// cycles, against 32 cycles of math), N >= 128 runs at the tensor rate; and
+// one straight-line issue per slice keeps the issuing thread ahead of the
+// tensor pipe.
+template <bool CPLX, int KSTEPS, int BLK>
+__device__ __forceinline__ void mma_slice(int c, uint32_t acc, uint64_t a1, uint64_t a2, uint64_t br, uint64_t bi,
+                                          uint32_t first) {
+  switch (c) {
+    case 6:
+      mma_group<CPLX, KSTEPS, BLK, 0, 4>(acc, a1, a2, br, bi, first);
+      mma_group<CPLX, KSTEPS, BLK, 4, 2>(acc, a1, a2, br, bi, first);
+      break;
+    case 5:
+      mma_group<CPLX, KSTEPS, BLK, 0, 3>(acc, a1, a2, br, bi, first);
+      mma_group<CPLX, KSTEPS, BLK, 3, 2>(acc, a1, a2, br, bi, first);
+      break;
+    case 4:
+      mma_group<CPLX, KSTEPS, BLK, 0, 4>(acc, a1, a2, br, bi, first);
+      break;
+    case 3:
+      mma_group<CPLX, KSTEPS, BLK, 0, 3>(acc, a1, a2, br, bi, first);
+      break;
+    case 2:
+      mma_group<CPLX, KSTEPS, BLK, 0, 2>(acc, a1, a2, br, bi, first);
+      break;
+    default:
+      mma_group<CPLX, KSTEPS, BLK, 0, 1>(acc, a1, a2, br, bi, first);
+      break;
+  }
 }
 
 // 32 lanes x 16 / 32 consecutive TMEM columns of this warp's lane quarter.
@@ -361,10 +422,15 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*
 #pragma unroll
     for (int s = 0; s < 6; ++s)
       if (s < S) {
-        uint8_t* q = p + s * slice;
-        *reinterpret_cast<uint4*>(q) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
-        *reinterpret_cast<uint4*>(q + kBlk) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
-        if (isA) *reinterpret_cast<uint4*>(q + 2 * kBlk) = make_uint4(wn[s][0], wn[s][1], wn[s][2], wn[s][3]);
+        if (isA) {  // slice s: Ar, Ai, -Ar
+          uint8_t* q = p + s * slice;
+          *reinterpret_cast<uint4*>(q) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+          *reinterpret_cast<uint4*>(q + kBlk) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+          *reinterpret_cast<uint4*>(q + 2 * kBlk) = make_uint4(wn[s][0], wn[s][1], wn[s][2], wn[s][3]);
+        } else {  // Br of slices 1..S, then Bi of slices 1..S
+          *reinterpret_cast<uint4*>(p + s * kBlk) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
+          *reinterpret_cast<uint4*>(p + (S + s) * kBlk) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
+        }
       }
   }
 }
@@ -509,7 +575,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   __shared__ int s_fail;
   constexpr int TR = CPLX ? kOzRows : 2 * kOzRows;  // output rows per tile
   constexpr int SA = CPLX ? kSliceA : 2 * kBlk;     // bytes of one slice of A (one K tile)
-  constexpr int SB = CPLX ? kSliceB : kBlk;         // bytes of one slice of B (one K tile)
+  constexpr int SB = CPLX ? kSliceB : kBlk;         // bytes of one slice of B (one K tile: Br, Bi; or Br)
   if (*static_cast<volatile int*>(oz.fail)) return;  // an earlier CTA gave up: the result is void anyway
   uint8_t* sA = osm;                                 // kSlotsA x one slice of A (Ar, Ai, -Ar; or Ar)
   uint8_t* sB = osm + kSlotsA * kSliceA;             // kSlotsB x S slices of B (Br, Bi; or Br)
@@ -621,7 +687,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
     }
   } else if (warp == kEpiWarps + 1) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t id_pos = idesc(false), id_neg = idesc(true);
       int na = 0, nbf = 0, ti = 0;
       bool ok = true;
       for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
@@ -648,20 +713,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a1 = smem_u32(sA + sa * kSliceA), a2 = a1 + kBlk;  // [Ar; Ai], [Ai; -Ar] (or real rows)
-            for (int t = 1; s + t <= S + 1; ++t) {
-              const uint32_t acc_d = tmem + uint32_t((s + t - 2) * 64);  // diagonal D = s + t
-              const uint32_t br = smem_u32(sB + sb * 6 * kSliceB + (t - 1) * SB), bi = br + kBlk;
-#pragma unroll
-              for (int ks = 0; ks < kOzK / 16; ++ks) {
-                const uint32_t ko = uint32_t(ks * 256);  // two core matrices along K
-                // the first product into each accumulator of a tile overwrites
-                // it: for diagonal D that is the pair (1, D - 1) at ks = 0
-                const uint32_t first = (kt == 0 && ks == 0 && s == 1) ? 0u : 1u;
-                mma(acc_d, sdesc(a1 + ko), sdesc(br + ko), id_pos, first);
-                if (CPLX) mma(acc_d, sdesc(a2 + ko), sdesc(bi + ko), id_neg, 1u);
-              }
-            }
+            const uint32_t a1 = smem_u32(sA + sa * kSliceA);  // [Ar; Ai], then [Ai; -Ar] (or 128 real rows)
+            const uint32_t br = smem_u32(sB + sb * 6 * kSliceB);  // Br slices 1..S, then Bi slices 1..S
+            // the first product into each accumulator of a tile overwrites
+            // it: for diagonal D that is the pair (1, D - 1) at the first K step
+            mma_slice<CPLX, kOzK / 16, kBlk>(S + 1 - s, tmem + uint32_t((s - 1) * 64), sdesc(a1), sdesc(a1 + kBlk),
+                                             sdesc(br), sdesc(br + S * kBlk), (kt == 0 && s == 1) ? 0u : 1u);
             mma_commit(smem_u32(&empty_a[sa]));
             ++na;
           }
@@ -770,7 +827,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
 // (16 B per complex entry read once, instead of 16 B read, 36 B written and
 // 36 B read again). Row exponents of A and the slices of B = L[S,P] come from
 // k_oz_tak_prep. K tiles of 16; a ring of three slots, each holding all S
-// slices of A (6 KiB each: Ar, Ai, -Ar) and of B (4 KiB each: Br, Bi).
+// slices of A (6 KiB each: Ar, Ai, -Ar) and of B (Br of slices 1..S, then
+// Bi of slices 1..S, 2 KiB each).
 constexpr int kFK = 16;                     // K per tile
 constexpr int kFBlk = kOzRows * kFK * 2;    // one 64-row block of one slice (2 KiB)
 constexpr int kFSliceA = 3 * kFBlk;
@@ -781,12 +839,6 @@ constexpr int kFSlot = kFSlotA + 6 * kFSliceB;
 constexpr int kFChunk = 256 / kFK;          // K tiles per exact chunk
 constexpr int kFWorkers = 8;
 constexpr int kFThreads = (kFWorkers + 1) * 32;
-
-// K-major no-swizzle descriptor for 16-deep tiles: SBO = 256 B.
-__device__ __forceinline__ uint64_t sdesc16(uint32_t saddr) {
-  return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(128 >> 4) << 16) | (uint64_t(256 >> 4) << 32) |
-         (uint64_t(1) << 46);
-}
 
 // The integer nearest to x 2^(7 S - e) (|x| < 2^e), from the bit pattern.
 __device__ __forceinline__ long long fixed_point(double x, int e, int S) {
@@ -874,8 +926,8 @@ __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__
 #pragma unroll
     for (int q = 0; q < 6; ++q)
       if (q < S) {
-        *reinterpret_cast<uint4*>(p + q * kFSliceB) = make_uint4(wr[q][0], wr[q][1], wr[q][2], wr[q][3]);
-        *reinterpret_cast<uint4*>(p + q * kFSliceB + kFBlk) = make_uint4(wi[q][0], wi[q][1], wi[q][2], wi[q][3]);
+        *reinterpret_cast<uint4*>(p + q * kFBlk) = make_uint4(wr[q][0], wr[q][1], wr[q][2], wr[q][3]);
+        *reinterpret_cast<uint4*>(p + (S + q) * kFBlk) = make_uint4(wi[q][0], wi[q][1], wi[q][2], wi[q][3]);
       }
   }
 }
@@ -963,7 +1015,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
 
   if (warp == kFWorkers) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t id_pos = idesc(false), id_neg = idesc(true);
       for (int kt = 0; kt < nkt; ++kt) {
         const int c = kt / kFChunk, in_chunk = kt % kFChunk;
         if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail)) {
@@ -978,15 +1029,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t base = smem_u32(osm + slot * kFSlot);
+        const uint64_t br = sdesc16(base + kFSlotA), bi = sdesc16(base + kFSlotA + S * kFBlk);  // Br 1..S, Bi 1..S
         for (int s = 1; s <= S; ++s) {
-          const uint32_t a1 = base + (s - 1) * kFSliceA, a2 = a1 + kFBlk;  // [Ar; Ai], [Ai; -Ar]
-          for (int t = 1; s + t <= S + 1; ++t) {
-            const uint32_t acc_d = tmem + uint32_t((s + t - 2) * 64);
-            const uint32_t br = base + kFSlotA + (t - 1) * kFSliceB, bi = br + kFBlk;
-            const uint32_t first = (in_chunk == 0 && s == 1) ? 0u : 1u;
-            mma(acc_d, sdesc16(a1), sdesc16(br), id_pos, first);
-            mma(acc_d, sdesc16(a2), sdesc16(bi), id_neg, 1u);
-          }
+          const uint32_t a1 = base + (s - 1) * kFSliceA;  // [Ar; Ai], then [Ai; -Ar]
+          mma_slice<true, 1, kFBlk>(S + 1 - s, tmem + uint32_t((s - 1) * 64), sdesc16(a1), sdesc16(a1 + kFBlk), br, bi,
+                                    (in_chunk == 0 && s == 1) ? 0u : 1u);
         }
         mma_commit(smem_u32(&empty[slot]));
         if (in_chunk == kFChunk - 1 || kt == nkt - 1) mma_commit(smem_u32(&acc_full));
@@ -1122,9 +1169,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
           wim.y = bf16_bits(dg[5]) | (bf16_bits(dg[7]) << 16);
           wim.z = bf16_bits(dg[9]) | (bf16_bits(dg[11]) << 16);
           wim.w = bf16_bits(dg[13]) | (bf16_bits(dg[15]) << 16);
-          uint8_t* pb = sbase + kFSlotA + sl * kFSliceB + wbase;
+          uint8_t* pb = sbase + kFSlotA + sl * kFBlk + wbase;  // Br slices 1..S, then Bi slices 1..S
           *reinterpret_cast<uint4*>(pb) = wre;
-          *reinterpret_cast<uint4*>(pb + kFBlk) = wim;
+          *reinterpret_cast<uint4*>(pb + S * kFBlk) = wim;
         }
       }
       // A: 8 entries of row r at k = 16 kt + 8 oct .. + 7, as fixed-point integers
