@@ -53,6 +53,7 @@
 // and CTAs that start after a failure return at once.
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -251,11 +252,10 @@ __device__ __forceinline__ void tmem_st32(uint32_t addr, const uint32_t* v) {
       : "memory");
 }
 
-// Balanced base-2^7 digits of x 2^(-e), |x| < 2^e: X = the integer nearest to
-// x 2^(7 S - e), taken from the bit pattern (mantissa shifted right by
-// n >= 10 with rounding, no floating-point arithmetic); then d[S-1] ... d[1]
-// in [-64, 63] from the low end, d[0] = the rest, |d[0]| <= 128.
-__device__ __forceinline__ void digits(double x, int e, int S, int (&d)[6]) {
+// The integer X nearest to x 2^(7 S - e) (|x| < 2^e, so |X| <= 2^(7 S)),
+// from the bit pattern: the mantissa shifted right by n >= 10 with rounding,
+// no floating-point arithmetic.
+__device__ __forceinline__ long long fixed_point(double x, int e, int S) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
   const int E = int((bits >> 52) & 0x7FF);
   unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
@@ -267,25 +267,83 @@ __device__ __forceinline__ void digits(double x, int e, int S, int (&d)[6]) {
   const int n = 1075 - Ee - 7 * S + e;
   long long X = 0;
   if (n > 0 && n < 54) X = static_cast<long long>((mant + (1ull << (n - 1))) >> n);
-  if (bits >> 63) X = -X;
-#pragma unroll
-  for (int s = 5; s >= 1; --s) {
-    if (s < S) {
-      const int dd = int((X + 64) & 127) - 64;
-      d[s] = dd;
-      X = (X - dd) >> 7;
-    } else {
-      d[s] = 0;
-    }
-  }
-  d[0] = int(X);
+  return (bits >> 63) ? -X : X;
 }
 
-// bfloat16 bit pattern of a small integer (|d| <= 2^8, exact): the float
-// 1.5 * 2^23 + d has d in its low mantissa bits, and subtracting 1.5 * 2^23
-// gives d exactly.
-__device__ __forceinline__ uint32_t bf16_bits(int d) {
-  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+// Balanced base-128 digits of X: X = d_0 128^(S-1) + ... + d_(S-1), the
+// lower digits in [-64, 63] and |d_0| <= 128. Without a carry chain: the
+// digits of Y = X + C, C = 64 (1 + 128 + ... + 128^(S-2)), below the top one
+// are d_s + 64 in [0, 127] (the representation is unique), so each is a
+// shift and a mask, and the top digit d_0 is Y >> 7 (S - 1) itself.
+__host__ __device__ constexpr long long digit_bias(int S) {
+  long long c = 0;
+  for (int k = 1; k < S; ++k) c = 128 * c + 64;
+  return c;
+}
+
+// Slice sl (0 = the most significant) of Y = X + digit_bias(S) as a float
+// holding the digit exactly: (1.5 2^23 + u) - (1.5 2^23 + 64) = u - 64 for
+// the masked digit u, 1.5 2^23 + d_0 - 1.5 2^23 for the top one.
+template <int S>
+__device__ __forceinline__ float slice_digit(long long Y, int sl) {
+  if (sl == 0) return __int_as_float(0x4B400000 + int(Y >> (7 * (S - 1)))) - 12582912.0f;
+  return __int_as_float(0x4B400000 | (uint32_t(Y >> (7 * (S - 1 - sl))) & 127u)) - 12582976.0f;
+}
+
+// 32-bit word of two bfloat16 values (a in the low half, b in the high half)
+// from floats holding integers of at most 8 significant bits (exact in bf16).
+__device__ __forceinline__ uint32_t bf16x2_of(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
+// The S slice words of 8 complex entries along K (Y[2u], Y[2u + 1]: real and
+// imaginary part of entry u as X + digit_bias(S)): slice sl of the real parts
+// goes to re + sl * step, of the imaginary parts to im + sl * step, and when
+// neg is given, of the negated real parts to neg + sl * step (sign bits
+// flipped: -0 for a zero digit, an exact zero).
+template <int S>
+__device__ __forceinline__ void store_slices_c(const long long (&Y)[16], uint8_t* re, uint8_t* im, uint8_t* neg,
+                                               int step) {
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) {
+    float f[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) f[t] = slice_digit<S>(Y[t], sl);
+    const uint4 wre = make_uint4(bf16x2_of(f[0], f[2]), bf16x2_of(f[4], f[6]), bf16x2_of(f[8], f[10]),
+                                 bf16x2_of(f[12], f[14]));
+    const uint4 wim = make_uint4(bf16x2_of(f[1], f[3]), bf16x2_of(f[5], f[7]), bf16x2_of(f[9], f[11]),
+                                 bf16x2_of(f[13], f[15]));
+    *reinterpret_cast<uint4*>(re + sl * step) = wre;
+    *reinterpret_cast<uint4*>(im + sl * step) = wim;
+    if (neg != nullptr)
+      *reinterpret_cast<uint4*>(neg + sl * step) =
+          make_uint4(wre.x ^ 0x80008000u, wre.y ^ 0x80008000u, wre.z ^ 0x80008000u, wre.w ^ 0x80008000u);
+  }
+}
+
+// The same for 8 real entries: slice sl to dst + sl * step.
+template <int S>
+__device__ __forceinline__ void store_slices_r(const long long (&Y)[8], uint8_t* dst, int step) {
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) {
+    float f[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) f[t] = slice_digit<S>(Y[t], sl);
+    *reinterpret_cast<uint4*>(dst + sl * step) =
+        make_uint4(bf16x2_of(f[0], f[1]), bf16x2_of(f[2], f[3]), bf16x2_of(f[4], f[5]), bf16x2_of(f[6], f[7]));
+  }
+}
+
+// Calls f(std::integral_constant<int, S>) for the slice count S in 2..6.
+template <typename Fn>
+__device__ __forceinline__ void with_slices(int S, Fn&& f) {
+  switch (S) {
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    default: f(std::integral_constant<int, 6>{}); break;
+  }
 }
 
 // v 2^sc rounded to the nearest double (ties to even) with integer
@@ -391,47 +449,27 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*
   // row tile i / 64; inside it, the 8-row group of i and row i % 8
   uint8_t* rowbase = dst + int64_t(i / kOzRows) * nkt * S * slice + ((i % kOzRows) >> 3) * 512 + r * 16;
   const double2* row = src + int64_t(i) * si;
+  const long long bias = digit_bias(S);
   for (int o = threadIdx.x >> 3; o < nkt * (kOzK / 8); o += 32) {
-    uint32_t wr[6][4], wi[6][4], wn[6][4];
+    long long Y[16];
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      const int k0 = o * 8 + u;
-      double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
-      if (i < rows) {
-        if (k0 < K) v0 = row[int64_t(k0) * sk];
-        if (k0 + 1 < K) v1 = row[int64_t(k0 + 1) * sk];
-        if (PHASE == 2 && isA) {  // W^T into the upper triangle (rows p0.., column q0 + i)
-          double2* wt = F + fo + p0 + int64_t(d.m) * (d.q0 + i);
-          if (k0 < K) wt[k0] = v0;
-          if (k0 + 1 < K) wt[k0 + 1] = v1;
-        }
+    for (int u = 0; u < 8; ++u) {
+      const int k = o * 8 + u;
+      double2 v = make_double2(0.0, 0.0);
+      if (i < rows && k < K) {
+        v = row[int64_t(k) * sk];
+        if (PHASE == 2 && isA) F[fo + p0 + int64_t(d.m) * (d.q0 + i) + k] = v;  // W^T (rows p0.., column q0 + i)
       }
-      int r0[6], i0[6], r1[6], i1[6];
-      digits(v0.x, e, S, r0);
-      digits(v0.y, e, S, i0);
-      digits(v1.x, e, S, r1);
-      digits(v1.y, e, S, i1);
-#pragma unroll
-      for (int s = 0; s < 6; ++s) {
-        wr[s][u / 2] = bf16_bits(r0[s]) | (bf16_bits(r1[s]) << 16);
-        wi[s][u / 2] = bf16_bits(i0[s]) | (bf16_bits(i1[s]) << 16);
-        wn[s][u / 2] = bf16_bits(-r0[s]) | (bf16_bits(-r1[s]) << 16);
-      }
+      Y[2 * u] = fixed_point(v.x, e, S) + bias;
+      Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
     }
     uint8_t* p = rowbase + int64_t(o >> 2) * S * slice + (o & 3) * 128;
-#pragma unroll
-    for (int s = 0; s < 6; ++s)
-      if (s < S) {
-        if (isA) {  // slice s: Ar, Ai, -Ar
-          uint8_t* q = p + s * slice;
-          *reinterpret_cast<uint4*>(q) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
-          *reinterpret_cast<uint4*>(q + kBlk) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
-          *reinterpret_cast<uint4*>(q + 2 * kBlk) = make_uint4(wn[s][0], wn[s][1], wn[s][2], wn[s][3]);
-        } else {  // Br of slices 1..S, then Bi of slices 1..S
-          *reinterpret_cast<uint4*>(p + s * kBlk) = make_uint4(wr[s][0], wr[s][1], wr[s][2], wr[s][3]);
-          *reinterpret_cast<uint4*>(p + (S + s) * kBlk) = make_uint4(wi[s][0], wi[s][1], wi[s][2], wi[s][3]);
-        }
-      }
+    with_slices(S, [&](auto SC) {
+      if (isA)  // slice s: Ar, Ai, -Ar
+        store_slices_c<decltype(SC)::value>(Y, p, p + kBlk, p + 2 * kBlk, slice);
+      else  // Br of slices 1..S, then Bi of slices 1..S
+        store_slices_c<decltype(SC)::value>(Y, p, p + S * kBlk, nullptr, kBlk);
+    });
   }
 }
 
@@ -488,31 +526,21 @@ __global__ void __launch_bounds__(256) k_oz_slice_real(double* __restrict__ F, D
   const int e = s_e[r];
   uint8_t* rowbase = dst + int64_t(i / R) * nkt * S * slice + ((i % R) >> 3) * 512 + r * 16;
   const double* row = src + int64_t(i) * si;
+  const long long bias = digit_bias(S);
   for (int o = threadIdx.x >> 3; o < nkt * (kOzK / 8); o += 32) {
-    uint32_t w[6][4];
+    long long Y[8];
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      const int k0 = o * 8 + u;
-      double v0 = 0.0, v1 = 0.0;
-      if (i < rows) {
-        if (k0 < K) v0 = row[int64_t(k0) * sk];
-        if (k0 + 1 < K) v1 = row[int64_t(k0 + 1) * sk];
-        if (PHASE == 2 && isA) {  // W^T into the upper triangle
-          double* wt = F + fo + p0 + int64_t(d.m) * (d.q0 + i);
-          if (k0 < K) wt[k0] = v0;
-          if (k0 + 1 < K) wt[k0 + 1] = v1;
-        }
+    for (int u = 0; u < 8; ++u) {
+      const int k = o * 8 + u;
+      double v = 0.0;
+      if (i < rows && k < K) {
+        v = row[int64_t(k) * sk];
+        if (PHASE == 2 && isA) F[fo + p0 + int64_t(d.m) * (d.q0 + i) + k] = v;  // W^T into the upper triangle
       }
-      int d0[6], d1[6];
-      digits(v0, e, S, d0);
-      digits(v1, e, S, d1);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) w[q][u / 2] = bf16_bits(d0[q]) | (bf16_bits(d1[q]) << 16);
+      Y[u] = fixed_point(v, e, S) + bias;
     }
     uint8_t* p = rowbase + int64_t(o >> 2) * S * slice + (o & 3) * 128;
-#pragma unroll
-    for (int q = 0; q < 6; ++q)
-      if (q < S) *reinterpret_cast<uint4*>(p + q * slice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    with_slices(S, [&](auto SC) { store_slices_r<decltype(SC)::value>(Y, p, slice); });
   }
 }
 
@@ -840,22 +868,6 @@ constexpr int kFChunk = 256 / kFK;          // K tiles per exact chunk
 constexpr int kFWorkers = 8;
 constexpr int kFThreads = (kFWorkers + 1) * 32;
 
-// The integer nearest to x 2^(7 S - e) (|x| < 2^e), from the bit pattern.
-__device__ __forceinline__ long long fixed_point(double x, int e, int S) {
-  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
-  const int E = int((bits >> 52) & 0x7FF);
-  unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
-  int Ee = 1;
-  if (E != 0) {
-    mant |= 1ull << 52;
-    Ee = E;
-  }
-  const int n = 1075 - Ee - 7 * S + e;
-  long long X = 0;
-  if (n > 0 && n < 54) X = static_cast<long long>((mant + (1ull << (n - 1))) >> n);
-  return (bits >> 63) ? -X : X;
-}
-
 // Row exponents of A = Y[S,S] (A groups) and the slices of B = L[S,P] in the
 // 16-deep tile layout (B groups); grid (groups of A, then of B; fronts; poles).
 __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__ Y, const double2* __restrict__ F,
@@ -901,34 +913,18 @@ __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__
   const int nkt = ceil_div(K, kFK);
   uint8_t* rowbase = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + (j >> 3) * 256 + r * 16;
   const double2* row = src + int64_t(j) * d.m;
+  const long long bias = digit_bias(S);
   for (int o = threadIdx.x >> 3; o < nkt * (kFK / 8); o += 32) {
-    uint32_t wr[6][4], wi[6][4];
+    long long Y[16];
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      const int k0 = o * 8 + u;
-      double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
-      if (j < rows) {
-        if (k0 < K) v0 = row[k0];
-        if (k0 + 1 < K) v1 = row[k0 + 1];
-      }
-      int r0[6], i0[6], r1[6], i1[6];
-      digits(v0.x, e, S, r0);
-      digits(v0.y, e, S, i0);
-      digits(v1.x, e, S, r1);
-      digits(v1.y, e, S, i1);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        wr[q][u / 2] = bf16_bits(r0[q]) | (bf16_bits(r1[q]) << 16);
-        wi[q][u / 2] = bf16_bits(i0[q]) | (bf16_bits(i1[q]) << 16);
-      }
+    for (int u = 0; u < 8; ++u) {
+      const int k = o * 8 + u;
+      const double2 v = (j < rows && k < K) ? row[k] : make_double2(0.0, 0.0);
+      Y[2 * u] = fixed_point(v.x, e, S) + bias;
+      Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
     }
-    uint8_t* p = rowbase + int64_t(o >> 1) * S * kFSliceB + (o & 1) * 128;
-#pragma unroll
-    for (int q = 0; q < 6; ++q)
-      if (q < S) {
-        *reinterpret_cast<uint4*>(p + q * kFBlk) = make_uint4(wr[q][0], wr[q][1], wr[q][2], wr[q][3]);
-        *reinterpret_cast<uint4*>(p + (S + q) * kFBlk) = make_uint4(wi[q][0], wi[q][1], wi[q][2], wi[q][3]);
-      }
+    uint8_t* p = rowbase + int64_t(o >> 1) * S * kFSliceB + (o & 1) * 128;  // Br slices 1..S, then Bi
+    with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(Y, p, p + S * kFBlk, nullptr, kFBlk); });
   }
 }
 
@@ -1055,6 +1051,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
     // B row (KIND 1): panel column p0 + r of Y, rows q0..
     const double2* colB = Y + fo + int64_t(p0 + (rowok ? r : 0)) * d.m + d.q0;
     const uint32_t wbase = uint32_t((r >> 3) * 256 + oct * 128 + (r & 7) * 16);
+    const long long bias = digit_bias(S);
     int drained = 0, pending = 0;
     bool ok = true;
     auto drain = [&](int ch) -> bool {
@@ -1138,84 +1135,28 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         atomicMax(&s_last_b[slot], kt);
       }
       if (DP) {  // B: 8 entries of Y[S,P] column r, cut into Br, Bi words
-        long long XB[16];
+        long long YB[16];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int k = (kt0 + kt) * kFK + oct * 8 + u;
-          double2 v = make_double2(0.0, 0.0);
-          if (rowok && k < d.mp) v = colB[k];
-          XB[2 * u] = fixed_point(v.x, eB, S);
-          XB[2 * u + 1] = fixed_point(v.y, eB, S);
+          const double2 v = (rowok && k < d.mp) ? colB[k] : make_double2(0.0, 0.0);
+          YB[2 * u] = fixed_point(v.x, eB, S) + bias;
+          YB[2 * u + 1] = fixed_point(v.y, eB, S) + bias;
         }
-#pragma unroll
-        for (int sl = 5; sl >= 0; --sl) {
-          if (sl >= S) continue;
-          int dg[16];
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            if (sl > 0) {
-              dg[t] = int((XB[t] + 64) & 127) - 64;
-              XB[t] = (XB[t] - dg[t]) >> 7;
-            } else {
-              dg[t] = int(XB[t]);
-            }
-          }
-          uint4 wre, wim;
-          wre.x = bf16_bits(dg[0]) | (bf16_bits(dg[2]) << 16);
-          wre.y = bf16_bits(dg[4]) | (bf16_bits(dg[6]) << 16);
-          wre.z = bf16_bits(dg[8]) | (bf16_bits(dg[10]) << 16);
-          wre.w = bf16_bits(dg[12]) | (bf16_bits(dg[14]) << 16);
-          wim.x = bf16_bits(dg[1]) | (bf16_bits(dg[3]) << 16);
-          wim.y = bf16_bits(dg[5]) | (bf16_bits(dg[7]) << 16);
-          wim.z = bf16_bits(dg[9]) | (bf16_bits(dg[11]) << 16);
-          wim.w = bf16_bits(dg[13]) | (bf16_bits(dg[15]) << 16);
-          uint8_t* pb = sbase + kFSlotA + sl * kFBlk + wbase;  // Br slices 1..S, then Bi slices 1..S
-          *reinterpret_cast<uint4*>(pb) = wre;
-          *reinterpret_cast<uint4*>(pb + S * kFBlk) = wim;
-        }
+        uint8_t* pb = sbase + kFSlotA + wbase;  // Br slices 1..S, then Bi slices 1..S
+        with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(YB, pb, pb + S * kFBlk, nullptr, kFBlk); });
       }
-      // A: 8 entries of row r at k = 16 kt + 8 oct .. + 7, as fixed-point integers
-      long long X[16];
+      // A: 8 entries of row r at k = 16 kt + 8 oct .. + 7, cut into Ar, Ai, -Ar words
+      long long Y[16];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int k = (kt0 + kt) * kFK + oct * 8 + u;
-        double2 v = make_double2(0.0, 0.0);
-        if (rowok && k < d.mp) v = col[k];
-        X[2 * u] = fixed_point(v.x, e, S);
-        X[2 * u + 1] = fixed_point(v.y, e, S);
+        const double2 v = (rowok && k < d.mp) ? col[k] : make_double2(0.0, 0.0);
+        Y[2 * u] = fixed_point(v.x, e, S) + bias;
+        Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
       }
-      // balanced base-128 digits from the low end: slice S-1 first
-#pragma unroll
-      for (int sl = 5; sl >= 0; --sl) {
-        if (sl >= S) continue;
-        int dg[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          if (sl > 0) {
-            dg[t] = int((X[t] + 64) & 127) - 64;
-            X[t] = (X[t] - dg[t]) >> 7;
-          } else {
-            dg[t] = int(X[t]);
-          }
-        }
-        uint4 wre, wim, wneg;
-        wre.x = bf16_bits(dg[0]) | (bf16_bits(dg[2]) << 16);
-        wre.y = bf16_bits(dg[4]) | (bf16_bits(dg[6]) << 16);
-        wre.z = bf16_bits(dg[8]) | (bf16_bits(dg[10]) << 16);
-        wre.w = bf16_bits(dg[12]) | (bf16_bits(dg[14]) << 16);
-        wim.x = bf16_bits(dg[1]) | (bf16_bits(dg[3]) << 16);
-        wim.y = bf16_bits(dg[5]) | (bf16_bits(dg[7]) << 16);
-        wim.z = bf16_bits(dg[9]) | (bf16_bits(dg[11]) << 16);
-        wim.w = bf16_bits(dg[13]) | (bf16_bits(dg[15]) << 16);
-        wneg.x = wre.x ^ 0x80008000u;  // -d: flip the sign bits (zero becomes -0, an exact zero)
-        wneg.y = wre.y ^ 0x80008000u;
-        wneg.z = wre.z ^ 0x80008000u;
-        wneg.w = wre.w ^ 0x80008000u;
-        uint8_t* ps = sbase + sl * kFSliceA + wbase;
-        *reinterpret_cast<uint4*>(ps) = wre;
-        *reinterpret_cast<uint4*>(ps + kFBlk) = wim;
-        *reinterpret_cast<uint4*>(ps + 2 * kFBlk) = wneg;
-      }
+      uint8_t* ps = sbase + wbase;
+      with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(Y, ps, ps + kFBlk, ps + 2 * kFBlk, kFSliceA); });
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_arrive(smem_u32(&full_a[slot]));
     }
