@@ -156,6 +156,14 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared through L2; zero-filled when
+// !valid (no bytes are read then).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -166,6 +174,15 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
 // Arrives on `bar` once every tcgen05.mma this thread issued so far is done.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Descriptor d moved by off 16-byte units: the start address field is the
+// low 14 bits and shared-memory addresses stay below 2^18, so the low word
+// takes the add without a carry.
+__device__ __forceinline__ uint64_t desc_off(uint64_t d, uint32_t off) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(uint32_t(d) + off), "r"(uint32_t(d >> 32)));
+  return r;
 }
 
 // Products of one slice of A with the B slices T0 + 1 .. T0 + G of a K tile
@@ -179,10 +196,10 @@ __device__ __forceinline__ void mma_group(uint32_t acc, uint64_t a1, uint64_t a2
                                           uint32_t first) {
 #pragma unroll
   for (int ks = 0; ks < KSTEPS; ++ks) {
-    const uint64_t ko = uint64_t(ks * 16);  // two core matrices along K (256 B, in 16-byte units)
-    const uint64_t bo = uint64_t(T0 * BLK / 16) + ko;
-    mma(acc + uint32_t(T0 * 64), a1 + ko, br + bo, idesc(G, false), ks == 0 ? first : 1u);
-    if (CPLX) mma(acc + uint32_t(T0 * 64), a2 + ko, bi + bo, idesc(G, true), 1u);
+    const uint32_t ko = uint32_t(ks * 16);  // two core matrices along K (256 B, in 16-byte units)
+    const uint32_t bo = uint32_t(T0 * BLK / 16) + ko;
+    mma(acc + uint32_t(T0 * 64), desc_off(a1, ko), desc_off(br, bo), idesc(G, false), ks == 0 ? first : 1u);
+    if (CPLX) mma(acc + uint32_t(T0 * 64), desc_off(a2, ko), desc_off(bi, bo), idesc(G, true), 1u);
   }
 }
 
@@ -227,6 +244,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16]) {
         "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(addr));
   asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+// The same without the wait: tcgen05.wait::ld before any register is read.
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t addr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Adds v_c 2^sh to the 64-bit integers (w[2c + 1], w[2c]) for 16 FP32
+// accumulators v_c holding exact integers (|v_c| <= 2^24). When every |v_c|
+// of the warp is below 2^22, 1.5 2^23 + v_c is exact with v_c in its low
+// mantissa bits (one add, one integer subtract); otherwise the conversion
+// instruction takes them.
+__device__ __forceinline__ void acc_add16(uint32_t* w, const uint32_t (&v)[16], int sh) {
+  float mx = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) mx = fmaxf(mx, fabsf(__uint_as_float(v[c])));
+  int iv[16];
+  if (__all_sync(0xFFFFFFFFu, mx < 4194304.0f)) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) iv[c] = __float_as_int(__uint_as_float(v[c]) + 12582912.0f) - 0x4B400000;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) iv[c] = __float2int_rn(__uint_as_float(v[c]));
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    unsigned long long a64 = (static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c];
+    a64 += static_cast<unsigned long long>(static_cast<long long>(iv[c])) << sh;
+    w[2 * c] = uint32_t(a64);
+    w[2 * c + 1] = uint32_t(a64 >> 32);
+  }
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t* v) {
@@ -867,6 +921,8 @@ constexpr int kFSlot = kFSlotA + 6 * kFSliceB;
 constexpr int kFChunk = 256 / kFK;          // K tiles per exact chunk
 constexpr int kFWorkers = 8;
 constexpr int kFThreads = (kFWorkers + 1) * 32;
+constexpr int kFStage = 4 * 32 * 8 * 16;  // FP64 entries of A for one half's next tile (16 KiB)
+constexpr int kFSmem = kFSlots * kFSlot + 2 * kFStage;
 
 // Row exponents of A = Y[S,S] (A groups) and the slices of B = L[S,P] in the
 // 16-deep tile layout (B groups); grid (groups of A, then of B; fronts; poles).
@@ -1011,29 +1067,33 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
 
   if (warp == kFWorkers) {
     if (lane == 0) {  // ---- MMA issuer
-      for (int kt = 0; kt < nkt; ++kt) {
-        const int c = kt / kFChunk, in_chunk = kt % kFChunk;
-        if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail)) {
-          record_fail(&s_fail, 4, kt);
-          break;
+      // one instance per slice count: every descriptor offset is a constant
+      with_slices(S, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        for (int kt = 0; kt < nkt; ++kt) {
+          const int c = kt / kFChunk, in_chunk = kt % kFChunk;
+          if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail)) {
+            record_fail(&s_fail, 4, kt);
+            break;
+          }
+          const int slot = kt % kFSlots;
+          const uint32_t par = (kt / kFSlots) & 1;
+          if (!bar_wait(smem_u32(&full_a[slot]), par, fail) || (!DP && !bar_wait(smem_u32(&full_b[slot]), par, fail))) {
+            record_fail(&s_fail, 6, kt);
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint64_t da = sdesc16(smem_u32(osm + slot * kFSlot)), db = desc_off(da, kFSlotA / 16);
+#pragma unroll
+          for (int s = 1; s <= SS; ++s) {  // [Ar; Ai], then [Ai; -Ar] of slice s; Br 1..S, then Bi 1..S
+            const uint64_t a1 = desc_off(da, (s - 1) * kFSliceA / 16);
+            mma_slice<true, 1, kFBlk>(SS + 1 - s, tmem + uint32_t((s - 1) * 64), a1, desc_off(a1, kFBlk / 16), db,
+                                      desc_off(db, SS * kFBlk / 16), (in_chunk == 0 && s == 1) ? 0u : 1u);
+          }
+          mma_commit(smem_u32(&empty[slot]));
+          if (in_chunk == kFChunk - 1 || kt == nkt - 1) mma_commit(smem_u32(&acc_full));
         }
-        const int slot = kt % kFSlots;
-        const uint32_t par = (kt / kFSlots) & 1;
-        if (!bar_wait(smem_u32(&full_a[slot]), par, fail) || (!DP && !bar_wait(smem_u32(&full_b[slot]), par, fail))) {
-          record_fail(&s_fail, 6, kt);
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t base = smem_u32(osm + slot * kFSlot);
-        const uint64_t br = sdesc16(base + kFSlotA), bi = sdesc16(base + kFSlotA + S * kFBlk);  // Br 1..S, Bi 1..S
-        for (int s = 1; s <= S; ++s) {
-          const uint32_t a1 = base + (s - 1) * kFSliceA;  // [Ar; Ai], then [Ai; -Ar]
-          mma_slice<true, 1, kFBlk>(S + 1 - s, tmem + uint32_t((s - 1) * 64), sdesc16(a1), sdesc16(a1 + kFBlk), br, bi,
-                                    (in_chunk == 0 && s == 1) ? 0u : 1u);
-        }
-        mma_commit(smem_u32(&empty[slot]));
-        if (in_chunk == kFChunk - 1 || kt == nkt - 1) mma_commit(smem_u32(&acc_full));
-      }
+      });
       mma_commit(smem_u32(&mma_done));
       if (!bar_wait_all(smem_u32(&mma_done), 0)) record_fail(&s_fail, 7, 0);
     }
@@ -1072,17 +1132,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
 #pragma unroll
           for (int c = 0; c < 32; ++c) w[c] = 0u;
         }
-        for (int D = 2; D <= S + 1; ++D) {
-          const int sh = 7 * (S + 1 - D);
-          uint32_t v[16];
-          tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 16), v);
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            unsigned long long a64 = (static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c];
-            a64 += static_cast<unsigned long long>(static_cast<long long>(__float2int_rn(__uint_as_float(v[c])))) << sh;
-            w[2 * c] = uint32_t(a64);
-            w[2 * c + 1] = uint32_t(a64 >> 32);
-          }
+        for (int D = 2; D <= S + 1; D += 2) {  // two diagonals per TMEM round trip
+          const uint32_t ta = tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 16);
+          uint32_t v0[16], v1[16];
+          tmem_ld16_nw(ta, v0);
+          if (D + 1 <= S + 1) tmem_ld16_nw(ta + 64, v1);
+          tmem_wait_ld();
+          acc_add16(w, v0, 7 * (S + 1 - D));
+          if (D + 1 <= S + 1) acc_add16(w, v1, 7 * (S - D));
         }
         if (multi && pending + 1 == kOzFlush && ch != nchunks - 1) {
           // K > 2048: move the exact partial sum into this thread's own
@@ -1111,6 +1168,22 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
       pending = (multi && pending + 1 == kOzFlush && ch != nchunks - 1) ? 0 : pending + 1;
       return true;
     };
+    // the FP64 entries of A for this half's next tile are copied into
+    // shared memory one tile ahead (entry u of thread `item` at u * 2 KiB +
+    // 16 item), so that their latency hides behind the cutting of the current
+    // one; each thread reads back only what it copied
+    const uint32_t stage = smem_u32(osm + kFSlots * kFSlot + half * kFStage) + uint32_t(item * 16);
+    auto load_a = [&](int kt) {
+      if (kt >= nkt) return;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = (kt0 + kt) * kFK + oct * 8 + u;
+        const bool in = rowok && k < d.mp;
+        cp_async16(stage + uint32_t(u * 2048), col + (in ? k : 0), in);
+      }
+      cp_async_commit();
+    };
+    load_a(half);
     for (int kt = half; kt < nkt && ok; kt += 2) {
       // the slot of tile kt is freed only by MMAs of the next chunk, which
       // wait for the drain of the previous one: drain it first
@@ -1147,14 +1220,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(YB, pb, pb + S * kFBlk, nullptr, kFBlk); });
       }
       // A: 8 entries of row r at k = 16 kt + 8 oct .. + 7, cut into Ar, Ai, -Ar words
+      cp_async_wait_all();
       long long Y[16];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int k = (kt0 + kt) * kFK + oct * 8 + u;
-        const double2 v = (rowok && k < d.mp) ? col[k] : make_double2(0.0, 0.0);
+        double2 v;
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(stage + uint32_t(u * 2048)) : "memory");
         Y[2 * u] = fixed_point(v.x, e, S) + bias;
         Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
       }
+      load_a(kt + 2);  // after this thread's reads of the buffer, in program order
       uint8_t* ps = sbase + wbase;
       with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(Y, ps, ps + kFBlk, ps + 2 * kFBlk, kFSliceA); });
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1320,9 +1395,9 @@ cudaError_t oz_configure(int S) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_oz_tak_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSlots * kFSlot));
+    e = cudaFuncSetAttribute(k_oz_tak_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSmem));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_oz_tak_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSlots * kFSlot));
+    e = cudaFuncSetAttribute(k_oz_tak_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSmem));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_oz_dpart_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(sizeof(double2) * kOzRows * kOzRows));
@@ -1441,7 +1516,7 @@ void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, cons
     k_oz_tak_prep<<<g, 256, 0, st>>>(Y, F, fr, fronts, p0, b, S, groupsA, oz);
   } else {
     dim3 gg(ceil_div(max_mp, kOzRows), nfronts, nb);
-    k_oz_tak_fused<0><<<gg, kFThreads, size_t(kFSlots) * kFSlot, st>>>(Y, fr, fronts, p0, b, S, oz, nullptr,
+    k_oz_tak_fused<0><<<gg, kFThreads, size_t(kFSmem), st>>>(Y, fr, fronts, p0, b, S, oz, nullptr,
                                                                       nullptr, nullptr, 0);
   }
 }
@@ -1458,7 +1533,7 @@ void launch_oz_dpart(double2* Y, const double2* F, double2* part, const int64_t*
     k_oz_col_exp<<<g, 256, 0, st>>>(Y, fr, fronts, p0, b, oz);
   } else if (stage == 1) {
     dim3 g(ceil_div(ceil_div(max_mp, kFK), kFChunk), nfronts, nb);
-    k_oz_tak_fused<1><<<g, kFThreads, size_t(kFSlots) * kFSlot, st>>>(
+    k_oz_tak_fused<1><<<g, kFThreads, size_t(kFSmem), st>>>(
         Y, fr, fronts, p0, b, S, oz, F, reinterpret_cast<long long*>(part), part_off, part_stride);
   } else {
     dim3 g(nfronts, nb);
