@@ -246,38 +246,71 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
-// The same without the wait: tcgen05.wait::ld before any register is read.
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t addr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(addr));
+// 32 lanes x 8 consecutive TMEM columns, without the wait: tcgen05.wait::ld
+// before any register is read.
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t addr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(addr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Adds v_c 2^sh to the 64-bit integers (w[2c + 1], w[2c]) for 16 FP32
-// accumulators v_c holding exact integers (|v_c| <= 2^24). When every |v_c|
-// of the warp is below 2^22, 1.5 2^23 + v_c is exact with v_c in its low
-// mantissa bits (one add, one integer subtract); otherwise the conversion
-// instruction takes them.
-__device__ __forceinline__ void acc_add16(uint32_t* w, const uint32_t (&v)[16], int sh) {
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          addr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+// w_c += v_c 2^sh on the 64-bit integers w_c = (w[2c + 1], w[2c]), c < 8,
+// for FP32 accumulators v_c holding exact integers (|v_c| <= 2^24). When
+// every |v_c| of the warp is below 2^22, 1.5 2^23 + v_c is exact with v_c in
+// its low mantissa bits (one add, one integer subtract); otherwise the
+// conversion instruction takes them.
+__device__ __forceinline__ void acc_add8(uint32_t (&w)[16], const uint32_t (&v)[8], int sh) {
   float mx = 0.0f;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) mx = fmaxf(mx, fabsf(__uint_as_float(v[c])));
-  int iv[16];
+  for (int c = 0; c < 8; ++c) mx = fmaxf(mx, fabsf(__uint_as_float(v[c])));
+  int iv[8];
   if (__all_sync(0xFFFFFFFFu, mx < 4194304.0f)) {
 #pragma unroll
-    for (int c = 0; c < 16; ++c) iv[c] = __float_as_int(__uint_as_float(v[c]) + 12582912.0f) - 0x4B400000;
+    for (int c = 0; c < 8; ++c) iv[c] = __float_as_int(__uint_as_float(v[c]) + 12582912.0f) - 0x4B400000;
   } else {
 #pragma unroll
-    for (int c = 0; c < 16; ++c) iv[c] = __float2int_rn(__uint_as_float(v[c]));
+    for (int c = 0; c < 8; ++c) iv[c] = __float2int_rn(__uint_as_float(v[c]));
   }
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
+  for (int c = 0; c < 8; ++c) {
     unsigned long long a64 = (static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c];
     a64 += static_cast<unsigned long long>(static_cast<long long>(iv[c])) << sh;
+    w[2 * c] = uint32_t(a64);
+    w[2 * c + 1] = uint32_t(a64 >> 32);
+  }
+}
+
+// w_c += (v0_c 2^7 + v1_c) 2^sh for the accumulators of two adjacent
+// diagonals. When every |v| of the warp is below 2^22 both convert exactly by
+// the add-and-subtract and the pair fits in 32 bits (below 2^30), so one
+// 64-bit shift-add serves two diagonals.
+__device__ __forceinline__ void acc_add_pair8(uint32_t (&w)[16], const uint32_t (&v0)[8], const uint32_t (&v1)[8],
+                                              int sh) {
+  float mx = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) mx = fmaxf(mx, fmaxf(fabsf(__uint_as_float(v0[c])), fabsf(__uint_as_float(v1[c]))));
+  if (!__all_sync(0xFFFFFFFFu, mx < 4194304.0f)) {
+    acc_add8(w, v0, sh + 7);
+    acc_add8(w, v1, sh);
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int a = __float_as_int(__uint_as_float(v0[c]) + 12582912.0f) - 0x4B400000;
+    const int b = __float_as_int(__uint_as_float(v1[c]) + 12582912.0f) - 0x4B400000;
+    unsigned long long a64 = (static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c];
+    a64 += static_cast<unsigned long long>(static_cast<long long>(a * 128 + b)) << sh;
     w[2 * c] = uint32_t(a64);
     w[2 * c + 1] = uint32_t(a64 >> 32);
   }
@@ -324,6 +357,31 @@ __device__ __forceinline__ long long fixed_point(double x, int e, int S) {
   return (bits >> 63) ? -X : X;
 }
 
+// The same rounded to nearest even by one FP64 fused multiply-add, for rows
+// whose scale 2^(7 S - e) is a normal double (fma_scale): x 2^(7 S - e) is
+// exact, and adding 1.5 2^52 leaves the integer (|X| <= 2^42) in the low
+// mantissa bits. One FP64 instruction instead of some 17 integer ones on the
+// busier integer pipe.
+__device__ __forceinline__ long long fixed_point_fma(double x, double scale) {
+  return __double_as_longlong(fma(x, scale, 6755399441055744.0)) - 0x4338000000000000LL;
+}
+
+// 2^(7 S - e) when it is a normal double and the row is finite, else 0.
+__device__ __forceinline__ double fma_scale(int e, int S) {
+  const int be = 1023 + 7 * S - e;
+  return (e != kNanExp && be >= 1 && be <= 2046) ? __longlong_as_double(static_cast<long long>(be) << 52) : 0.0;
+}
+
+// The fixed-point integer of x for a row of exponent e: by the FP64
+// multiply-add when the scale is a normal double (every row but those of
+// extreme range or holding Inf / NaN), else by the bit pattern. Both round to
+// nearest (ties to even, resp. away from zero). The cutting kernels send
+// half of the entries (real parts; even k of real operands) this way and
+// half by the bit pattern, which keeps the FP64 and integer pipes balanced.
+__device__ __forceinline__ long long fixed_of(double x, double scale, int e, int S) {
+  return scale != 0.0 ? fixed_point_fma(x, scale) : fixed_point(x, e, S);
+}
+
 // Balanced base-128 digits of X: X = d_0 128^(S-1) + ... + d_(S-1), the
 // lower digits in [-64, 63] and |d_0| <= 128. Without a carry chain: the
 // digits of Y = X + C, C = 64 (1 + 128 + ... + 128^(S-2)), below the top one
@@ -336,12 +394,18 @@ __host__ __device__ constexpr long long digit_bias(int S) {
 }
 
 // Slice sl (0 = the most significant) of Y = X + digit_bias(S) as a float
-// holding the digit exactly: (1.5 2^23 + u) - (1.5 2^23 + 64) = u - 64 for
-// the masked digit u, 1.5 2^23 + d_0 - 1.5 2^23 for the top one.
+// holding the digit exactly. A lower digit u sits at bit p <= 14 of the low
+// word (digits 0-2 from the low end) or of Y >> 21 (digits 3-4); under the
+// exponent field of 2^(23 - p) those bits make the float 2^(23 - p) + u, and
+// subtracting 2^(23 - p) + 64 leaves u - 64: one mask and one add, no shift.
+// The top digit is 1.5 2^23 + d_0 - 1.5 2^23.
 template <int S>
 __device__ __forceinline__ float slice_digit(long long Y, int sl) {
   if (sl == 0) return __int_as_float(0x4B400000 + int(Y >> (7 * (S - 1)))) - 12582912.0f;
-  return __int_as_float(0x4B400000 | (uint32_t(Y >> (7 * (S - 1 - sl))) & 127u)) - 12582976.0f;
+  const int k = S - 1 - sl;  // digit index from the low end, 0 .. 4
+  const int p = k <= 2 ? 7 * k : 7 * k - 21;
+  const uint32_t w = k <= 2 ? uint32_t(Y) : uint32_t(Y >> 21);
+  return __uint_as_float((uint32_t(150 - p) << 23) | (w & (127u << p))) - (float(1 << (23 - p)) + 64.0f);
 }
 
 // 32-bit word of two bfloat16 values (a in the low half, b in the high half)
@@ -504,6 +568,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*
   uint8_t* rowbase = dst + int64_t(i / kOzRows) * nkt * S * slice + ((i % kOzRows) >> 3) * 512 + r * 16;
   const double2* row = src + int64_t(i) * si;
   const long long bias = digit_bias(S);
+  const double scale = fma_scale(e, S);
   for (int o = threadIdx.x >> 3; o < nkt * (kOzK / 8); o += 32) {
     long long Y[16];
 #pragma unroll
@@ -514,7 +579,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*
         v = row[int64_t(k) * sk];
         if (PHASE == 2 && isA) F[fo + p0 + int64_t(d.m) * (d.q0 + i) + k] = v;  // W^T (rows p0.., column q0 + i)
       }
-      Y[2 * u] = fixed_point(v.x, e, S) + bias;
+      Y[2 * u] = fixed_of(v.x, scale, e, S) + bias;
       Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
     }
     uint8_t* p = rowbase + int64_t(o >> 2) * S * slice + (o & 3) * 128;
@@ -581,6 +646,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_real(double* __restrict__ F, D
   uint8_t* rowbase = dst + int64_t(i / R) * nkt * S * slice + ((i % R) >> 3) * 512 + r * 16;
   const double* row = src + int64_t(i) * si;
   const long long bias = digit_bias(S);
+  const double scale = fma_scale(e, S);
   for (int o = threadIdx.x >> 3; o < nkt * (kOzK / 8); o += 32) {
     long long Y[8];
 #pragma unroll
@@ -591,7 +657,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_real(double* __restrict__ F, D
         v = row[int64_t(k) * sk];
         if (PHASE == 2 && isA) F[fo + p0 + int64_t(d.m) * (d.q0 + i) + k] = v;  // W^T into the upper triangle
       }
-      Y[u] = fixed_point(v, e, S) + bias;
+      Y[u] = ((u & 1) ? fixed_point(v, e, S) : fixed_of(v, scale, e, S)) + bias;
     }
     uint8_t* p = rowbase + int64_t(o >> 2) * S * slice + (o & 3) * 128;
     with_slices(S, [&](auto SC) { store_slices_r<decltype(SC)::value>(Y, p, slice); });
@@ -970,13 +1036,14 @@ __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__
   uint8_t* rowbase = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + (j >> 3) * 256 + r * 16;
   const double2* row = src + int64_t(j) * d.m;
   const long long bias = digit_bias(S);
+  const double scale = fma_scale(e, S);
   for (int o = threadIdx.x >> 3; o < nkt * (kFK / 8); o += 32) {
     long long Y[16];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int k = o * 8 + u;
       const double2 v = (j < rows && k < K) ? row[k] : make_double2(0.0, 0.0);
-      Y[2 * u] = fixed_point(v.x, e, S) + bias;
+      Y[2 * u] = fixed_of(v.x, scale, e, S) + bias;
       Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
     }
     uint8_t* p = rowbase + int64_t(o >> 1) * S * kFSliceB + (o & 1) * 128;  // Br slices 1..S, then Bi
@@ -1112,6 +1179,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
     const double2* colB = Y + fo + int64_t(p0 + (rowok ? r : 0)) * d.m + d.q0;
     const uint32_t wbase = uint32_t((r >> 3) * 256 + oct * 128 + (r & 7) * 16);
     const long long bias = digit_bias(S);
+    const double scale = fma_scale(e, S);
     int drained = 0, pending = 0;
     bool ok = true;
     auto drain = [&](int ch) -> bool {
@@ -1123,32 +1191,35 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         return false;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {  // 16 output columns at a time
-        uint32_t w[32];
+      const bool flush = multi && pending + 1 == kOzFlush && ch != nchunks - 1;
+#pragma unroll 1
+      for (int hh = 0; hh < 4; ++hh) {  // 8 output columns at a time
+        uint32_t w[16];
         if (pending > 0) {
-          tmem_ld32(tsum + hh * 32, w);
+          tmem_ld16(tsum + hh * 16, w);
         } else {
 #pragma unroll
-          for (int c = 0; c < 32; ++c) w[c] = 0u;
+          for (int c = 0; c < 16; ++c) w[c] = 0u;
         }
         for (int D = 2; D <= S + 1; D += 2) {  // two diagonals per TMEM round trip
-          const uint32_t ta = tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 16);
-          uint32_t v0[16], v1[16];
-          tmem_ld16_nw(ta, v0);
-          if (D + 1 <= S + 1) tmem_ld16_nw(ta + 64, v1);
+          const uint32_t ta = tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 8);
+          uint32_t v0[8], v1[8];
+          tmem_ld8_nw(ta, v0);
+          if (D + 1 <= S + 1) tmem_ld8_nw(ta + 64, v1);
           tmem_wait_ld();
-          acc_add16(w, v0, 7 * (S + 1 - D));
-          if (D + 1 <= S + 1) acc_add16(w, v1, 7 * (S - D));
+          if (D + 1 <= S + 1)
+            acc_add_pair8(w, v0, v1, 7 * (S - D));
+          else
+            acc_add8(w, v0, 7 * (S + 1 - D));
         }
-        if (multi && pending + 1 == kOzFlush && ch != nchunks - 1) {
+        if (flush) {
           // K > 2048: move the exact partial sum into this thread's own
           // Y[S,P] entries (rounded once), which no operand of the launch reads
           if (orow < d.mp) {
             const int ea = s_ea[orow - mt * kOzRows];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int j = h * 32 + hh * 16 + c;
+            for (int c = 0; c < 8; ++c) {
+              const int j = h * 32 + hh * 8 + c;
               if (j < d.bb) {
                 double* o = Yout + 2 * ((d.q0 + orow) + int64_t(d.m) * (p0 + j));
                 const long long a64 = static_cast<long long>((static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c]);
@@ -1158,7 +1229,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
             }
           }
         } else {
-          tmem_st32(tsum + hh * 32, w);
+          tmem_st16(tsum + hh * 16, w);
         }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;");
@@ -1213,7 +1284,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         for (int u = 0; u < 8; ++u) {
           const int k = (kt0 + kt) * kFK + oct * 8 + u;
           const double2 v = (rowok && k < d.mp) ? colB[k] : make_double2(0.0, 0.0);
-          YB[2 * u] = fixed_point(v.x, eB, S) + bias;
+          YB[2 * u] = fixed_point(v.x, eB, S) + bias;  // A already loads the FP64 pipe here
           YB[2 * u + 1] = fixed_point(v.y, eB, S) + bias;
         }
         uint8_t* pb = sbase + kFSlotA + wbase;  // Br slices 1..S, then Bi slices 1..S
@@ -1226,7 +1297,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
       for (int u = 0; u < 8; ++u) {
         double2 v;
         asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(stage + uint32_t(u * 2048)) : "memory");
-        Y[2 * u] = fixed_point(v.x, e, S) + bias;
+        Y[2 * u] = fixed_of(v.x, scale, e, S) + bias;
         Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
       }
       load_a(kt + 2);  // after this thread's reads of the buffer, in program order
