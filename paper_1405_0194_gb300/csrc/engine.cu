@@ -139,15 +139,21 @@ namespace {
 
 struct PanelGeom {
   int nact = 0, row_tiles = 0, tri_tiles = 0, max_mp = 0, oz_schur = 0, oz_schur_r = 0;
+  int oz_blk = 0, oz_blk_r = 0;  // split path: most tiles of the update of the rest of the panel block (cb > 0)
 };
 
-PanelGeom panel_geom(const Level& lv, int p0, int b) {
+PanelGeom panel_geom(const Level& lv, int p0, int b, int cb = 0) {
   PanelGeom g;
   for (size_t t = 0; t < lv.fronts.size(); ++t) {
     if (lv.s[t] <= p0) break;
     ++g.nact;
     int bb = std::min(b, lv.s[t] - p0);
     int mp = lv.m[t] - p0 - bb;
+    if (cb > 0) {
+      const int cs = std::min(cb, lv.s[t]) - p0 - bb;
+      g.oz_blk = std::max(g.oz_blk, oz_block_tiles(mp, cs, true));
+      g.oz_blk_r = std::max(g.oz_blk_r, oz_block_tiles(mp, cs, false));
+    }
     int rt = (mp + kTile - 1) / kTile;
     g.row_tiles = std::max(g.row_tiles, rt);
     g.tri_tiles = std::max(g.tri_tiles, rt * (rt + 1) / 2);
@@ -164,6 +170,21 @@ struct PanelWork {
   double off_fl = 0, off_by = 0, dpart_fl = 0, dpart_by = 0, dred_by = 0;
   double slice_off_by = 0, slice_schur_by = 0;  // split path: read FP64, write bf16 planes (10 B / element / slice)
 };
+
+// Work of the update of the rest of a panel block (columns before min(cb, s)).
+void block_band_work(const Level& lv, int p0, int b, int cb, double es, double fma_fl, double& fl, double& by,
+                     double& slice_by) {
+  fl = by = slice_by = 0;
+  for (size_t t = 0; t < lv.fronts.size(); ++t) {
+    if (lv.s[t] <= p0) break;
+    const double bb = std::min(b, lv.s[t] - p0), mp = double(lv.m[t]) - p0 - bb;
+    const double cs = std::max(0.0, std::min(double(std::min(cb, lv.s[t])) - p0 - bb, mp));
+    const double area = cs * mp - cs * (cs - 1) / 2;  // lower-triangle entries of the column band
+    fl += fma_fl * area * bb;
+    by += (2 * area + (mp + cs) * bb) * es;
+    slice_by += (mp + cs) * bb * (es + 4.0 * 6);
+  }
+}
 
 PanelWork panel_work(const Level& lv, int p0, int b, double es, double fma_fl) {
   PanelWork w;
@@ -244,25 +265,58 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
         launch_panel_solve<T>(F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
         pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
       }
-      a = pf.begin(st);
-      if (sizeof(T) == sizeof(double2) && p->oz_slices > 0) {
-        OzScratch oz = split_scratch(p, ws, false);
-        double2* Fz = reinterpret_cast<double2*>(F);
-        launch_oz_slice_schur(Fz, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
-        pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by);
-        a = pf.begin(st);
-        launch_oz_gemm_schur(Fz, fr, dfr, g.nact, g.oz_schur, p0, b, S, oz, sh.nb, st);
-        pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by, 1, nb * w.schur_fl * 4.0 * S * (S + 1) / 2 / 8.0 * 2.0);
-      } else if (sizeof(T) == sizeof(double) && p->oz_slices > 0) {
-        OzScratch oz = split_scratch(p, ws, true);
-        double* Fr = reinterpret_cast<double*>(F);
-        launch_oz_slice_schur_real(Fr, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st);
-        pf.end(a, P_SLICE, st, 0.0, nb * w.slice_schur_by);
-        a = pf.begin(st);
-        launch_oz_gemm_schur_real(Fr, fr, dfr, g.nact, g.oz_schur_r, p0, b, S, oz, sh.nb, st);
-        // real: one product per slice pair instead of four (fl counts 2 flops per real multiply-add)
-        pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by, 1, nb * w.schur_fl * S * (S + 1) / 2.0);
+      if (S > 0) {
+        // Blocks of kOzBlockPanels panels: each panel updates the rest of its
+        // block (columns before min(cb, s)); after the block's last panel one
+        // update with K = the block width covers everything to its right, so
+        // that part of the front is read and written once per block instead
+        // of once per panel.
+        const bool cplx = sizeof(T) == sizeof(double2);
+        const int bw = kOzBlockPanels * b, blk0 = p0 / bw * bw, cb = blk0 + bw;
+        const PanelGeom gb = panel_geom(lv, p0, b, cb);
+        double band_fl, band_by, band_slice_by;
+        block_band_work(lv, p0, b, cb, es, fl, band_fl, band_by, band_slice_by);
+        OzScratch oz = split_scratch(p, ws, !cplx);
+        if ((cplx ? gb.oz_blk : gb.oz_blk_r) > 0) {  // none at the block's last panel
+          a = pf.begin(st);
+          if (cplx)
+            launch_oz_slice_schur(reinterpret_cast<double2*>(F), fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, cb);
+          else
+            launch_oz_slice_schur_real(reinterpret_cast<double*>(F), fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st,
+                                       cb);
+          pf.end(a, P_SLICE, st, 0.0, nb * band_slice_by);
+          a = pf.begin(st);
+          if (cplx)
+            launch_oz_gemm_schur(reinterpret_cast<double2*>(F), fr, dfr, g.nact, gb.oz_blk, p0, b, S, oz, sh.nb, st, cb);
+          else
+            launch_oz_gemm_schur_real(reinterpret_cast<double*>(F), fr, dfr, g.nact, gb.oz_blk_r, p0, b, S, oz, sh.nb,
+                                      st, cb);
+          // executed tensor flops: S(S+1)/2 slice pairs; a complex multiply-add
+          // is 4 real products (8 flops counted), a real one 1 (2 flops)
+          pf.end(a, P_SCHUR, st, nb * band_fl, nb * band_by, 1, nb * band_fl * tens);
+        }
+        if (p0 + b >= std::min(cb, lv.max_s)) {  // the level's last panel of the block
+          const PanelGeom gt = panel_geom(lv, blk0, bw);
+          const PanelWork wt = pf.on ? panel_work(lv, blk0, bw, es, fl) : PanelWork();
+          a = pf.begin(st);
+          if (cplx)
+            launch_oz_slice_schur(reinterpret_cast<double2*>(F), fr, dfr, gt.nact, gt.max_mp, blk0, bw, S, oz, sh.nb, st,
+                                  0);
+          else
+            launch_oz_slice_schur_real(reinterpret_cast<double*>(F), fr, dfr, gt.nact, gt.max_mp, blk0, bw, S, oz, sh.nb,
+                                       st, 0);
+          pf.end(a, P_SLICE, st, 0.0, nb * wt.slice_schur_by);
+          a = pf.begin(st);
+          if (cplx)
+            launch_oz_gemm_schur(reinterpret_cast<double2*>(F), fr, dfr, gt.nact, gt.oz_schur, blk0, bw, S, oz, sh.nb, st,
+                                 0);
+          else
+            launch_oz_gemm_schur_real(reinterpret_cast<double*>(F), fr, dfr, gt.nact, gt.oz_schur_r, blk0, bw, S, oz,
+                                      sh.nb, st, 0);
+          pf.end(a, P_SCHUR, st, nb * wt.schur_fl, nb * wt.schur_by, 1, nb * wt.schur_fl * tens);
+        }
       } else {
+        a = pf.begin(st);
         launch_trailing<T>(F, fr, dfr, g.nact, g.tri_tiles, p0, b, sh, st);
         pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by);
       }
@@ -620,10 +674,12 @@ void build_split_layout(pexsi_plan* p, std::vector<int64_t>& a_off, std::vector<
       eb_off[K] = xb;
       ar[K] = sar;
       br[K] = sbr;
-      sa += oz_front_bytes_A(mp, b, p->oz_slices);
-      sb += oz_front_bytes_B(mp, b, p->oz_slices);
-      sar += oz_front_bytes_A_real(mp, b, p->oz_slices);
-      sbr += oz_front_bytes_B_real(mp, b, p->oz_slices);
+      // the Schur update after a block of panels has K = the block width
+      const int kw = std::min(kOzBlockPanels * b, S.s(K));
+      sa += oz_front_bytes_A(mp, kw, p->oz_slices);
+      sb += oz_front_bytes_B(mp, kw, p->oz_slices);
+      sar += oz_front_bytes_A_real(mp, kw, p->oz_slices);
+      sbr += oz_front_bytes_B_real(mp, kw, p->oz_slices);
       xa += std::max<int64_t>(b, mp);  // rows of A, or the panel columns (Y[S,P] exponents)
       xb += std::max<int64_t>(b, mp);
     }

@@ -117,11 +117,18 @@ void launch_oz_dpart(double2* Y, const double2* F, double2* part, const int64_t*
 // Split-precision Schur update F[S,S] -= L[S,P] W[S,P]^T (lower triangle):
 // slicing of L rows and W rows, then the tcgen05 GEMM with an FP64
 // read-modify-write (max_tiles = max over fronts of oz_schur_tiles(m_p)).
+// The panels are taken in blocks of kOzBlockPanels: with cb > 0 (the end
+// column of the block) a panel updates only the columns before min(cb, s)
+// (max_tiles = max of oz_block_tiles), and after the block one call with
+// p0 = the block start, b = the block width and cb = 0 updates the rest with
+// K = the block width (at most 256, one exact chunk of the FP32 accumulators).
+constexpr int kOzBlockPanels = 4;
 void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
-                           int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+                           int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb);
 void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
-                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb);
 int oz_schur_tiles(int mp);
+int oz_block_tiles(int mp, int cs, bool cplx);
 size_t oz_smem_bytes(int S);
 // Slice-tile scratch of one front per pole (both phases), for its largest m_p.
 int64_t oz_front_bytes_A(int64_t mp, int b, int S);
@@ -139,9 +146,9 @@ void launch_oz_panel(double2* F, const DevFronts& fr, const int32_t* fronts, int
 void launch_oz_panel_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp, int p0,
                           int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool gemm);
 void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
-                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb);
 void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
-                               int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st);
+                               int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb);
 cudaError_t oz_configure(int S);
 
 // Raises the dynamic shared-memory limits the kernels need for panel width b.

@@ -519,7 +519,7 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 template <int PHASE>
 __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*Y*/, double2* __restrict__ F,
                                                   DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
-                                                  int S, int groupsA, OzScratch oz) {
+                                                  int S, int groupsA, OzScratch oz, int cb) {
   PanelDims d;
   if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
   const int pole = blockIdx.z;
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*
   const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
   const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
   const int K = d.bb;
-  const int rows = (PHASE == 2 && !isA) ? d.bb : d.mp;
+  const int rows = (PHASE == 2 && !isA) ? d.bb : (isA || cb <= 0) ? d.mp : min(d.mp, min(cb, d.s) - d.q0);
   const double2* src = isA ? F + fo + d.q0 + int64_t(d.m) * p0 : F + fo + p0 + int64_t(d.m) * (PHASE == 2 ? p0 : d.q0);
   const int64_t si = isA ? 1 : d.m, sk = isA ? d.m : 1;
   const int nkt = ceil_div(K, kOzK);
@@ -601,14 +601,15 @@ __global__ void __launch_bounds__(256) k_oz_slice(const double2* __restrict__ /*
 template <int PHASE>
 __global__ void __launch_bounds__(256) k_oz_slice_real(double* __restrict__ F, DevFronts fr,
                                                        const int32_t* __restrict__ fronts, int p0, int b, int S,
-                                                       int groupsA, OzScratch oz) {
+                                                       int groupsA, OzScratch oz, int cb) {
   PanelDims d;
   if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
   const int pole = blockIdx.z;
   const bool isA = int(blockIdx.x) < groupsA;
   const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
   const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
-  const int rows = (PHASE == 2 && !isA) ? d.bb : d.mp, K = d.bb, nkt = ceil_div(K, kOzK);
+  const int rows = (PHASE == 2 && !isA) ? d.bb : (isA || cb <= 0) ? d.mp : min(d.mp, min(cb, d.s) - d.q0);
+  const int K = d.bb, nkt = ceil_div(K, kOzK);
   const double* src = isA ? F + fo + d.q0 + int64_t(d.m) * p0 : F + fo + p0 + int64_t(d.m) * (PHASE == 2 ? p0 : d.q0);
   const int64_t si = isA ? 1 : d.m, sk = isA ? d.m : 1;
   const int R = isA ? 2 * kOzRows : kOzRows;
@@ -670,11 +671,20 @@ __device__ __forceinline__ void record_fail(int* s_fail, int site, int kt) {
 }
 
 // ---------------------------------------------------------------- GEMM (short K)
-// Output tiles of one front at the active panel (m_p rows below it).
+// Output tiles of one front at the active panel (m_p rows below it); MODE 3
+// only the first cs columns (the rest of the panel block).
 template <int MODE, bool CPLX>
-__device__ __forceinline__ int front_tiles(int mp) {
+__host__ __device__ inline int front_tiles(int mp, int cs) {
   if (mp <= 0) return 0;
   if (MODE == 2) return ceil_div(mp, CPLX ? kOzRows : 2 * kOzRows);
+  if (MODE == 3) {  // column tiles nt < nc, row tiles on and below the diagonal
+    const int nnt = ceil_div(mp, kOzRows), nc = cs <= 0 ? 0 : min(nnt, ceil_div(cs, kOzRows));
+    if (CPLX) return nc * nnt - nc * (nc - 1) / 2;
+    const int nmt = ceil_div(mp, 2 * kOzRows);
+    int t = 0;
+    for (int nt = 0; nt < nc; ++nt) t += nmt - nt / 2;
+    return t;
+  }
   if (CPLX) {
     const int n = ceil_div(mp, kOzRows);
     return n * (n + 1) / 2;  // 64 x 64 tiles on and below the diagonal
@@ -685,10 +695,19 @@ __device__ __forceinline__ int front_tiles(int mp) {
 
 // Row tile mt and column tile nt of tile t of a front.
 template <int MODE, bool CPLX>
-__device__ __forceinline__ void tile_coords(int t, int& mt, int& nt) {
+__device__ __forceinline__ void tile_coords(int t, int mp, int& mt, int& nt) {
   if (MODE == 2) {
     mt = t;
     nt = 0;
+  } else if (MODE == 3) {  // column by column: column nt holds the row tiles from the diagonal down
+    const int first_of = CPLX ? 0 : 1;  // real tiles: 128 rows, so row tile nt / 2 holds the diagonal
+    const int nrows = CPLX ? ceil_div(mp, kOzRows) : ceil_div(mp, 2 * kOzRows);
+    nt = 0;
+    while (t >= nrows - (first_of ? nt / 2 : nt)) {
+      t -= nrows - (first_of ? nt / 2 : nt);
+      ++nt;
+    }
+    mt = (first_of ? nt / 2 : nt) + t;
   } else if (CPLX) {  // t = mt (mt + 1) / 2 + nt, nt <= mt
     mt = int((sqrtf(8.0f * float(t) + 1.0f) - 1.0f) * 0.5f);
     while (mt * (mt + 1) / 2 > t) --mt;
@@ -706,6 +725,9 @@ __device__ __forceinline__ void tile_coords(int t, int& mt, int& nt) {
 //   B = W[S,P] (K = bb <= 64); complex 64 x 64 tiles or real 128 x 64 tiles.
 // MODE 2, panel solve L[S,P] = A B^T with A = W[S,P] and B = D^-1, written
 //   where W was; one tile per row tile of S.
+// MODE 3, MODE 1 restricted to the columns before min(cb, s): the update of
+//   the rest of a block of panels, whose update of the columns after the
+//   block waits for one MODE 1 launch over the whole block (K up to 256).
 // Persistent: each CTA walks the (pole, front, tile) items of the launch with
 // stride gridDim.x. The slot rings run on across items, so the next tile's
 // slices load during this tile's MMAs; the epilogue warps drain TMEM into
@@ -715,7 +737,7 @@ __device__ __forceinline__ void tile_coords(int t, int& mt, int& nt) {
 template <int MODE, bool CPLX>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ Yv, DevFronts fr,
                                                              const int32_t* __restrict__ fronts, int nfronts, int p0,
-                                                             int b, int S, int nb, OzScratch oz) {
+                                                             int b, int S, int nb, OzScratch oz, int cb) {
   extern __shared__ __align__(128) uint8_t osm[];
   __shared__ __align__(8) uint64_t full_a[kSlotsA], empty_a[kSlotsA], full_b[kSlotsB], empty_b[kSlotsB];
   __shared__ __align__(8) uint64_t acc_full, acc_empty, mma_done;
@@ -724,10 +746,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   constexpr int TR = CPLX ? kOzRows : 2 * kOzRows;  // output rows per tile
   constexpr int SA = CPLX ? kSliceA : 2 * kBlk;     // bytes of one slice of A (one K tile)
   constexpr int SB = CPLX ? kSliceB : kBlk;         // bytes of one slice of B (one K tile: Br, Bi; or Br)
+  constexpr bool SCHUR = MODE != 2;                  // read-modify-write of the trailing block
   if (*static_cast<volatile int*>(oz.fail)) return;  // an earlier CTA gave up: the result is void anyway
   uint8_t* sA = osm;                                 // kSlotsA x one slice of A (Ar, Ai, -Ar; or Ar)
   uint8_t* sB = osm + kSlotsA * kSliceA;             // kSlotsB x S slices of B (Br, Bi; or Br)
-  int* s_pref = reinterpret_cast<int*>(osm + kSlotsA * kSliceA + kSlotsB * 6 * kSliceB);  // tiles before front f
+  int* s_pref = reinterpret_cast<int*>(sB + kSlotsB * 6 * kSliceB);  // tiles before front f
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* fail = &s_fail;
 
@@ -738,7 +761,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
       int v = 0;
       if (f0 + lane < nfronts) {
         PanelDims d;
-        v = panel_dims(fr, fronts, f0 + lane, p0, b, d) ? front_tiles<MODE, CPLX>(d.mp) : 0;
+        v = panel_dims(fr, fronts, f0 + lane, p0, b, d) ? front_tiles<MODE, CPLX>(d.mp, min(cb, d.s) - d.q0) : 0;
       }
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -787,7 +810,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
       else hi = mid;
     }
     if (!panel_dims(fr, fronts, lo, p0, b, d)) return false;
-    tile_coords<MODE, CPLX>(t - s_pref[lo], mt, nt);
+    tile_coords<MODE, CPLX>(t - s_pref[lo], d.mp, mt, nt);
     return true;
   };
 
@@ -894,6 +917,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
       int pole, mt, nt;
       PanelDims d;
       if (!decode(it, pole, d, mt, nt)) continue;
+      const int i = mt * TR + ri;  // row of the trailing block
+      const bool row_in = i < d.mp;
+      double* Yb = static_cast<double*>(Yv) + ES * (int64_t(pole) * fr.pool + fr.off[d.f]) + part;
+      // the exponents are requested before the accumulators are ready; the
+      // exponent of column h*32 + lane is broadcast by shuffles below (every
+      // lane takes part; the row test only guards memory accesses)
+      const int jl = nt * kOzRows + h * 32 + lane;
+      // Schur columns: j <= i below the panel, MODE 3 only before the block end
+      const int jmax = MODE == 2 ? d.bb : MODE == 3 ? min(d.mp, min(cb, d.s) - d.q0) : d.mp;
+      const int eb_lane = jl < jmax ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + jl] : 0;
+      const int ea = row_in ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
       bool ok = true;
       if (lane == 0) ok = bar_wait(smem_u32(&acc_full), ti & 1, fail);
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
@@ -921,15 +955,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
       __syncwarp();
       if (lane == 0) bar_arrive(smem_u32(&acc_empty));  // TMEM free for the next tile
       ++ti;
-      const int i = mt * TR + ri;  // row of the trailing block
-      const bool row_in = i < d.mp;
-      // exponent of column h*32 + lane of this tile, broadcast by shuffles below
-      // (every lane takes part; the row test only guards memory accesses)
-      const int jl = nt * kOzRows + h * 32 + lane;
-      const int eb_lane =
-          jl < (MODE == 1 ? d.mp : d.bb) ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + jl] : 0;
-      const int ea = row_in ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
-      double* Yb = static_cast<double*>(Yv) + ES * (int64_t(pole) * fr.pool + fr.off[d.f]) + part;
       // Schur: the old values of 16 columns are loaded before any of them is
       // stored, so that their loads are in flight together
 #pragma unroll
@@ -938,18 +963,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int j = nt * kOzRows + h * 32 + c0 + c;
-          const bool in = row_in && (MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb));
-          old[c] = (MODE == 1 && in) ? Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] : 0.0;
+          const bool in = row_in && j < jmax && (!SCHUR || j <= i);
+          old[c] = (SCHUR && in) ? Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] : 0.0;
         }
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int j = nt * kOzRows + h * 32 + c0 + c;
-          const bool in = row_in && (MODE == 1 ? (j <= i && j < d.mp) : (j < d.bb));
+          const bool in = row_in && j < jmax && (!SCHUR || j <= i);
           const int ebc = __shfl_sync(0xFFFFFFFFu, eb_lane, c0 + c);
           if (in) {
             double v = i64_scaled(static_cast<long long>(acc[c0 + c]), ea + ebc - 7 * (S + 1));
             if (ea == kNanExp || ebc == kNanExp) v = __longlong_as_double(0x7FF8000000000000LL);
-            if (MODE == 1)
+            if (SCHUR)
               Yb[ES * ((d.q0 + i) + int64_t(d.m) * (d.q0 + j))] = old[c] - v;
             else
               Yb[ES * ((d.q0 + i) + int64_t(d.m) * (p0 + j))] = v;
@@ -1465,6 +1490,8 @@ cudaError_t oz_configure(int S) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz_gemm<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_oz_tak_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFSmem));
   if (e == cudaSuccess)
@@ -1501,13 +1528,13 @@ int sm_count() {
 // grid is one CTA per SM (fewer when the launch holds fewer tiles).
 template <int MODE, bool CPLX>
 void launch_persistent(void* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0, int b,
-                       int S, const OzScratch& oz, int nb, cudaStream_t st) {
+                       int S, const OzScratch& oz, int nb, cudaStream_t st, int cb = 0) {
   if (nfronts <= 0 || max_tiles <= 0) return;
   for (int f0 = 0; f0 < nfronts; f0 += kMaxPersistFronts) {
     const int nf = std::min(kMaxPersistFronts, nfronts - f0);
     const int64_t bound = int64_t(max_tiles) * nf * nb;
     const int grid = int(std::min<int64_t>(sm_count(), bound));
-    k_oz_gemm<MODE, CPLX><<<grid, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts + f0, nf, p0, b, S, nb, oz);
+    k_oz_gemm<MODE, CPLX><<<grid, kGemmThreads, oz_smem_bytes(S), st>>>(F, fr, fronts + f0, nf, p0, b, S, nb, oz, cb);
   }
 }
 
@@ -1524,29 +1551,39 @@ int oz_schur_tiles(int mp) {
 }
 
 void launch_oz_slice_schur_real(const double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
-                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
+                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb) {
   if (nfronts <= 0 || max_mp <= 0) return;
   const int groups = (max_mp + 7) / 8;
   dim3 g(2 * groups, nfronts, nb);
-  k_oz_slice_real<1><<<g, 256, 0, st>>>(const_cast<double*>(F), fr, fronts, p0, b, S, groups, oz);
+  k_oz_slice_real<1><<<g, 256, 0, st>>>(const_cast<double*>(F), fr, fronts, p0, b, S, groups, oz, cb);
 }
 
 void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
-                               int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
-  launch_persistent<1, false>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st);
+                               int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb) {
+  if (cb > 0)
+    launch_persistent<3, false>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st, cb);
+  else
+    launch_persistent<1, false>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st);
 }
 
 void launch_oz_slice_schur(const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_mp,
-                           int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
+                           int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb) {
   if (nfronts <= 0 || max_mp <= 0) return;
   const int groups = (max_mp + 7) / 8;
   dim3 g(2 * groups, nfronts, nb);
-  k_oz_slice<1><<<g, 256, 0, st>>>(F, const_cast<double2*>(F), fr, fronts, p0, b, S, groups, oz);
+  k_oz_slice<1><<<g, 256, 0, st>>>(F, const_cast<double2*>(F), fr, fronts, p0, b, S, groups, oz, cb);
 }
 
 void launch_oz_gemm_schur(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0,
-                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st) {
-  launch_persistent<1, true>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st);
+                          int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb) {
+  if (cb > 0)
+    launch_persistent<3, true>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st, cb);
+  else
+    launch_persistent<1, true>(F, fr, fronts, nfronts, max_tiles, p0, b, S, oz, nb, st);
+}
+
+int oz_block_tiles(int mp, int cs, bool cplx) {
+  return cplx ? front_tiles<3, true>(mp, cs) : front_tiles<3, false>(mp, cs);
 }
 
 // Split-precision panel solve L[S,P] = W[S,P] D^-1 (complex poles and real
@@ -1558,7 +1595,7 @@ void launch_oz_panel(double2* F, const DevFronts& fr, const int32_t* fronts, int
   if (!gemm) {
     const int groupsA = (max_mp + 7) / 8, groupsB = (b + 7) / 8;
     dim3 g(groupsA + groupsB, nfronts, nb);
-    k_oz_slice<2><<<g, 256, 0, st>>>(nullptr, F, fr, fronts, p0, b, S, groupsA, oz);
+    k_oz_slice<2><<<g, 256, 0, st>>>(nullptr, F, fr, fronts, p0, b, S, groupsA, oz, 0);
   } else {
     launch_persistent<2, true>(F, fr, fronts, nfronts, ceil_div(max_mp, kOzRows), p0, b, S, oz, nb, st);
   }
@@ -1570,7 +1607,7 @@ void launch_oz_panel_real(double* F, const DevFronts& fr, const int32_t* fronts,
   if (!gemm) {
     const int groupsA = (max_mp + 7) / 8, groupsB = (b + 7) / 8;
     dim3 g(groupsA + groupsB, nfronts, nb);
-    k_oz_slice_real<2><<<g, 256, 0, st>>>(F, fr, fronts, p0, b, S, groupsA, oz);
+    k_oz_slice_real<2><<<g, 256, 0, st>>>(F, fr, fronts, p0, b, S, groupsA, oz, 0);
   } else {
     launch_persistent<2, false>(F, fr, fronts, nfronts, ceil_div(max_mp, 2 * kOzRows), p0, b, S, oz, nb, st);
   }
