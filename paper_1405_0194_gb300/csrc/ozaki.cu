@@ -860,47 +860,55 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
     if (lane == 0) {  // ---- MMA issuer
       int na = 0, nbf = 0, ti = 0;
       bool ok = true;
-      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        int pole, mt, nt;
-        PanelDims d;
-        if (!decode(it, pole, d, mt, nt)) continue;
-        const int nkt = ceil_div(d.bb, kOzK);
-        if (ti > 0 && !bar_wait(smem_u32(&acc_empty), (ti - 1) & 1, fail)) {  // previous tile drained
-          record_fail(&s_fail, 4, 0);
-          break;
-        }
-        for (int kt = 0; kt < nkt && ok; ++kt) {
-          const int sb = nbf % kSlotsB;
-          if (!bar_wait(smem_u32(&full_b[sb]), (nbf / kSlotsB) & 1, fail)) {
-            record_fail(&s_fail, 5, kt);
+      // one instance per slice count: the slices of a K tile are issued as
+      // straight-line code with constant descriptor offsets
+      with_slices(S, [&](auto SC) {
+        constexpr int SS = decltype(SC)::value;
+        for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+          int pole, mt, nt;
+          PanelDims d;
+          if (!decode(it, pole, d, mt, nt)) continue;
+          const int nkt = ceil_div(d.bb, kOzK);
+          if (ti > 0 && !bar_wait(smem_u32(&acc_empty), (ti - 1) & 1, fail)) {  // previous tile drained
+            record_fail(&s_fail, 4, 0);
             ok = false;
             break;
           }
-          for (int s = 1; s <= S; ++s) {
-            const int sa = na % kSlotsA;
-            if (!bar_wait(smem_u32(&full_a[sa]), (na / kSlotsA) & 1, fail)) {
-              record_fail(&s_fail, 6, kt);
+          for (int kt = 0; kt < nkt && ok; ++kt) {
+            const int sb = nbf % kSlotsB;
+            if (!bar_wait(smem_u32(&full_b[sb]), (nbf / kSlotsB) & 1, fail)) {
+              record_fail(&s_fail, 5, kt);
               ok = false;
               break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a1 = smem_u32(sA + sa * kSliceA);  // [Ar; Ai], then [Ai; -Ar] (or 128 real rows)
-            const uint32_t br = smem_u32(sB + sb * 6 * kSliceB);  // Br slices 1..S, then Bi slices 1..S
-            // the first product into each accumulator of a tile overwrites
-            // it: for diagonal D that is the pair (1, D - 1) at the first K step
-            mma_slice<CPLX, kOzK / 16, kBlk>(S + 1 - s, tmem + uint32_t((s - 1) * 64), sdesc(a1), sdesc(a1 + kBlk),
-                                             sdesc(br), sdesc(br + S * kBlk), (kt == 0 && s == 1) ? 0u : 1u);
-            mma_commit(smem_u32(&empty_a[sa]));
-            ++na;
+            // Br slices 1..S, then Bi slices 1..S
+            const uint64_t br = sdesc(smem_u32(sB + sb * 6 * kSliceB)), bi = desc_off(br, SS * kBlk / 16);
+#pragma unroll
+            for (int s = 1; s <= SS; ++s) {
+              const int sa = na % kSlotsA;
+              if (!bar_wait(smem_u32(&full_a[sa]), (na / kSlotsA) & 1, fail)) {
+                record_fail(&s_fail, 6, kt);
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              const uint64_t a1 = sdesc(smem_u32(sA + sa * kSliceA));  // [Ar; Ai], then [Ai; -Ar] (or 128 real rows)
+              // the first product into each accumulator of a tile overwrites
+              // it: for diagonal D that is the pair (1, D - 1) at the first K step
+              mma_slice<CPLX, kOzK / 16, kBlk>(SS + 1 - s, tmem + uint32_t((s - 1) * 64), a1, desc_off(a1, kBlk / 16), br,
+                                               bi, (kt == 0 && s == 1) ? 0u : 1u);
+              mma_commit(smem_u32(&empty_a[sa]));
+              ++na;
+            }
+            if (!ok) break;
+            mma_commit(smem_u32(&empty_b[sb]));
+            ++nbf;
           }
           if (!ok) break;
-          mma_commit(smem_u32(&empty_b[sb]));
-          ++nbf;
+          mma_commit(smem_u32(&acc_full));
+          ++ti;
         }
-        if (!ok) break;
-        mma_commit(smem_u32(&acc_full));
-        ++ti;
-      }
+      });
       // every MMA issued has completed before TMEM is read for the last time or freed
       mma_commit(smem_u32(&mma_done));
       if (!bar_wait_all(smem_u32(&mma_done), 0)) record_fail(&s_fail, 7, 0);
