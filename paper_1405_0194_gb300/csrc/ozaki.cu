@@ -254,6 +254,14 @@ __device__ __forceinline__ void tmem_ld8_nw(uint32_t addr, uint32_t (&v)[8]) {
                : "r"(addr));
 }
 
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t addr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t (&v)[16]) {
@@ -1290,8 +1298,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
     load_a(half);
     for (int kt = half; kt < nkt && ok; kt += 2) {
       // the slot of tile kt is freed only by MMAs of the next chunk, which
-      // wait for the drain of the previous one: drain it first
-      while (ok && drained < nchunks && kt >= kFChunk * (drained + 1) + kFSlots) ok = drain(drained++);
+      // wait for the drain of the previous one: drain it first; and drain as
+      // soon as the chunk's MMAs are done once this half is past the chunk,
+      // so that the tensor pipe idles for the drain alone
+      if (drained < nchunks && kt >= kFChunk * (drained + 1)) {
+        bool now = kt >= kFChunk * (drained + 1) + kFSlots;
+        if (!now && lane == 0) now = bar_try(smem_u32(&acc_full), drained & 1);
+        if (__shfl_sync(0xFFFFFFFFu, now, 0)) ok = drain(drained++);
+      }
       if (!ok) break;
       const int slot = kt % kFSlots, use = kt / kFSlots;
       bool free_slot = true;
