@@ -72,7 +72,7 @@ void Profiler::destroy() {
 int64_t bytes_per_pole(const pexsi_plan* p) {
   return (2 * p->sym.front_elems + p->part_stride) * int64_t(sizeof(double2)) +
          std::max(p->ozA_stride, 2 * p->ozA_stride_r) + std::max(p->ozB_stride, 2 * p->ozB_stride_r) +
-         8 * (p->exA_stride + p->exB_stride);
+         8 * (p->exA_stride + p->exB_stride) + 4 * p->ymax_stride;
 }
 
 int64_t bytes_fixed(const pexsi_plan* p) {
@@ -112,6 +112,7 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
     wsalloc(&ws.exA, sizeof(int) * size_t(p->exA_stride) * 2 * batch, ws, "alloc(split exponents)");
     wsalloc(&ws.exB, sizeof(int) * size_t(p->exB_stride) * 2 * batch, ws, "alloc(split exponents)");
     wsalloc(&ws.ozfail, sizeof(int), ws, "alloc(status)");
+    wsalloc(&ws.ymax, sizeof(uint32_t) * size_t(p->ymax_stride) * batch, ws, "alloc(split row maxima)");
   }
   if (!ws.ev0) ck(cudaEventCreate(&ws.ev0), "cudaEventCreate");
   if (!ws.ev1) ck(cudaEventCreate(&ws.ev1), "cudaEventCreate");
@@ -119,7 +120,7 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
 
 void workspace_free(Workspace& ws) {
   void* ptrs[] = {ws.F,  ws.Y,        ws.part,  ws.H,    ws.S,   ws.out, ws.brk, ws.minpiv, ws.neg,
-                  ws.partials, ws.trace3, ws.ainv, ws.ozA, ws.ozB, ws.exA, ws.exB, ws.ozfail};
+                  ws.partials, ws.trace3, ws.ainv, ws.ozA, ws.ozB, ws.exA, ws.exB, ws.ozfail, ws.ymax};
   for (void* q : ptrs) {
     if (!q) continue;
     if (ws.async) cudaFreeAsync(q, ws.stream);
@@ -217,7 +218,8 @@ Profiler g_off;  // a profiler that is never switched on
 OzScratch split_scratch(const pexsi_plan* p, Workspace& ws, bool real) {
   return OzScratch{ws.ozA, real ? p->d_ozA_off_r : p->d_ozA_off, real ? p->ozA_stride_r : p->ozA_stride,
                    ws.ozB, real ? p->d_ozB_off_r : p->d_ozB_off, real ? p->ozB_stride_r : p->ozB_stride,
-                   ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail};
+                   ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail,
+                   ws.ymax, p->d_ymax_off, p->ymax_stride};
 }
 
 // Factor the batch in F (assembled), leaves to root.
@@ -336,6 +338,13 @@ void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Pro
     cudaEvent_t a = pf.begin(st);
     launch_gather(ws.Y, fr, dfr, int(lv.fronts.size()), int(lv.gather_tiles), sh, st);
     pf.end(a, P_GATHER, st, 0.0, nb * lv.gather_bytes);
+    if (p->oz_slices > 0) {
+      int max_m = 0;
+      for (int mk : lv.m) max_m = std::max(max_m, mk);
+      a = pf.begin(st);
+      launch_oz_rowmax_init(ws.Y, fr, dfr, int(lv.fronts.size()), max_m, split_scratch(p, ws, false), sh.nb, st);
+      pf.end(a, P_SLICE, st, 0.0, nb * lv.gather_bytes);
+    }
     int last = ((lv.max_s - 1) / b) * b;
     for (int p0 = last; p0 >= 0; p0 -= b) {
       PanelGeom g = panel_geom(lv, p0, b);
@@ -571,7 +580,8 @@ namespace {
 void free_plan_device(pexsi_plan* p) {
   void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
                   p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_ident,
-                  p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off, p->d_ozA_off_r, p->d_ozB_off_r};
+                  p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off, p->d_ozA_off_r, p->d_ozB_off_r,
+                  p->d_ymax_off};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   cudaStream_t st = p->ws.stream;
@@ -893,6 +903,12 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
       p->d_ozB_off_r = dev_upload(rb);
       p->d_exA_off = dev_upload(xa);
       p->d_exB_off = dev_upload(xb);
+      std::vector<int64_t> yo(S.nsuper);
+      for (int64_t K = 0; K < S.nsuper; ++K) {
+        yo[K] = p->ymax_stride;
+        p->ymax_stride += S.m(K);
+      }
+      p->d_ymax_off = dev_upload(yo);
     }
     {
       std::vector<double> ident(S.nnz, 0.0);  // S = I on the pattern

@@ -57,6 +57,12 @@ struct OzScratch {
   const int64_t* exB_off;
   int64_t exB_stride;
   int* fail;
+  // selected inversion: per front row r, the largest high word of |Re|, |Im|
+  // over the part of row r of Y already computed (columns from the current
+  // panel on), kept up to date by the kernels that write Y
+  uint32_t* ymax;
+  const int64_t* ymax_off;  // first row of each front
+  int64_t ymax_stride;      // rows per pole
 };
 
 // ---- launchers (T = double for real inertia, double2 for complex poles) ----
@@ -106,6 +112,12 @@ void launch_scaled_imag(const double2* Y, const int64_t* entry_pos, int64_t nnz,
 // Split-precision Takahashi step Y[S,P] = -Y[S,S] L[S,P] and its mirror, with
 // A = Y[S,S] sliced on the fly inside the GEMM: prep = true computes the row
 // exponents of A and slices B, prep = false runs the GEMM.
+// Row maxima of Y for the rows of each front when its selected inversion
+// starts (the update set from Y[U,U], the supernode rows 0); the Takahashi
+// kernel and the Y[P,P] reduction keep them up to date, and they give the
+// row exponents of A = Y[S,S] without reading Y[S,S] for every panel.
+void launch_oz_rowmax_init(const double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_m,
+                           const OzScratch& oz, int nb, cudaStream_t st);
 void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
                          int max_mp, int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool prep);
 // Split-precision Y[P,P] = D^-1 - L[S,P]^T Y[S,P] (panel width 64): stage 0

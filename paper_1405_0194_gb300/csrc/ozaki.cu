@@ -390,6 +390,14 @@ __device__ __forceinline__ long long fixed_of(double x, double scale, int e, int
   return scale != 0.0 ? fixed_point_fma(x, scale) : fixed_point(x, e, S);
 }
 
+// High word of |x|: ordered like |x| for finite x, >= 0x7FF00000 for Inf / NaN.
+__device__ __forceinline__ uint32_t abs_hi(double x) { return uint32_t(__double2hiint(x)) & 0x7FFFFFFFu; }
+
+// Row exponent e (2^e > every |entry|) from the largest high word of the row.
+__device__ __forceinline__ int exp_of_hi(uint32_t mx) {
+  return mx >= 0x7FF00000u ? kNanExp : mx != 0 ? int(mx >> 20) - 1022 : 0;
+}
+
 // Balanced base-128 digits of X: X = d_0 128^(S-1) + ... + d_(S-1), the
 // lower digits in [-64, 63] and |d_0| <= 128. Without a carry chain: the
 // digits of Y = X + C, C = 64 (1 + 128 + ... + 128^(S-2)), below the top one
@@ -1042,10 +1050,16 @@ __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__
   const bool isA = int(blockIdx.x) < groupsA;
   const int g = isA ? int(blockIdx.x) : int(blockIdx.x) - groupsA;
   const int64_t fo = int64_t(pole) * fr.pool + fr.off[d.f];
-  const double2* src = isA ? Y + fo + int64_t(d.q0) * d.m + d.q0 : F + fo + int64_t(p0) * d.m + d.q0;
-  const int rows = isA ? d.mp : d.bb, K = d.mp;
-  int* ex = isA ? oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f]
-                : oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];
+  if (isA) {  // rows of Y[S,S]: from the row maxima kept up to date as Y is written
+    const int i = g * 256 + int(threadIdx.x);
+    if (i < d.mp)
+      oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] =
+          exp_of_hi(oz.ymax[int64_t(pole) * oz.ymax_stride + oz.ymax_off[d.f] + d.q0 + i]);
+    return;
+  }
+  const double2* src = F + fo + int64_t(p0) * d.m + d.q0;
+  const int rows = d.bb, K = d.mp;
+  int* ex = oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];
   if (g * 8 >= rows) return;
   __shared__ int s_e[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1068,7 +1082,6 @@ __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__
       if (i < rows) ex[i] = e;
     }
   }
-  if (isA) return;
   __syncthreads();
   const int r = threadIdx.x & 7;
   const int j = g * 8 + r;
@@ -1090,6 +1103,30 @@ __global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__
     uint8_t* p = rowbase + int64_t(o >> 1) * S * kFSliceB + (o & 1) * 128;  // Br slices 1..S, then Bi
     with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(Y, p, p + S * kFBlk, nullptr, kFBlk); });
   }
+}
+
+// Row maxima of Y when a front's selected inversion starts: rows of the update
+// set U = [s, m) over the columns of U (Y[U,U] as gathered from the parent; Y
+// is symmetric, so row r is read as column r), 0 for the rows of the
+// supernode, whose columns are computed later. One warp per row; grid (rows /
+// 8, fronts, poles).
+__global__ void __launch_bounds__(256) k_oz_rowmax_init(const double2* __restrict__ Y, DevFronts fr,
+                                                        const int32_t* __restrict__ fronts, OzScratch oz) {
+  const int f = fronts[blockIdx.y];
+  const int s = fr.s[f], m = fr.m[f];
+  const int r = int(blockIdx.x) * 8 + int(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= m) return;  // whole warps
+  const int pole = blockIdx.z;
+  uint32_t mx = 0;
+  if (r >= s) {
+    const double2* col = Y + int64_t(pole) * fr.pool + fr.off[f] + int64_t(m) * r;
+    for (int c = s + lane; c < m; c += 32) {
+      const double2 v = col[c];
+      mx = max(mx, max(abs_hi(v.x), abs_hi(v.y)));
+    }
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  }
+  if (lane == 0) oz.ymax[int64_t(pole) * oz.ymax_stride + oz.ymax_off[f] + r] = mx;
 }
 
 // KIND 0, Takahashi step: one CTA per 64-row tile of S (front, pole); A =
@@ -1382,6 +1419,10 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
   } else if (!DP && warp < kFWorkers) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int ea = orow < d.mp ? s_ea[orow - mt * kOzRows] : 0;
+    // the largest high words of what is written, per row (this thread) and
+    // per column (a warp reduction; lane c keeps column h*32 + c), go into
+    // the row maxima: Y[S,P] extends rows S, and its columns are the rows P
+    uint32_t rmax = 0, cmax = 0;
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       uint32_t w[32];
@@ -1389,6 +1430,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int j = h * 32 + hh * 16 + c;
+        uint32_t hv = 0;
         if (orow < d.mp && j < d.bb) {
           const int eb = s_eb[j];
           double* o = Yout + 2 * ((d.q0 + orow) + int64_t(d.m) * (p0 + j));
@@ -1399,9 +1441,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
           if (ea == kNanExp || eb == kNanExp) v = __longlong_as_double(0x7FF8000000000000LL);
           *o = -v;
           Yout[2 * ((p0 + j) + int64_t(d.m) * (d.q0 + orow))] = -v;
+          hv = abs_hi(v);
         }
+        rmax = max(rmax, hv);
+        const uint32_t cm = __reduce_max_sync(0xFFFFFFFFu, hv);
+        if (lane == hh * 16 + c) cmax = cm;
       }
     }
+    uint32_t* ym = oz.ymax + int64_t(pole) * oz.ymax_stride + oz.ymax_off[d.f];
+    if (orow < d.mp) atomicMax(ym + d.q0 + orow, rmax);
+    if (h * 32 + lane < d.bb) atomicMax(ym + p0 + h * 32 + lane, cmax);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -1457,6 +1506,8 @@ __global__ void __launch_bounds__(256) k_oz_dpart_reduce(double2* __restrict__ Y
   const long long* pp = part + (int64_t(pole) * part_stride + part_off[d.f]) * 2;
   const int* exa = oz.exA + int64_t(pole) * oz.exA_stride + oz.exA_off[d.f];  // Y[S,P] columns
   const int* exb = oz.exB + int64_t(pole) * oz.exB_stride + oz.exB_off[d.f];  // L[S,P] columns
+  __shared__ uint32_t s_rmax[kOzRows];  // row maxima of Y[P,P] (high words)
+  if (threadIdx.x < kOzRows) s_rmax[threadIdx.x] = 0;
   for (int idx = threadIdx.x; idx < d.bb * d.bb; idx += blockDim.x) {
     const int r = idx % d.bb, c = idx / d.bb;
     __int128 re = 0, im = 0;
@@ -1479,8 +1530,13 @@ __global__ void __launch_bounds__(256) k_oz_dpart_reduce(double2* __restrict__ Y
   for (int idx = threadIdx.x; idx < d.bb * d.bb; idx += blockDim.x) {
     const int r = idx % d.bb, c = idx / d.bb;
     const double2 a = tmp[r + d.bb * c], t = tmp[c + d.bb * r];
-    Y[base + (p0 + r) + int64_t(d.m) * (p0 + c)] = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y + t.y));
+    const double2 v = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y + t.y));
+    Y[base + (p0 + r) + int64_t(d.m) * (p0 + c)] = v;
+    atomicMax(&s_rmax[r], max(abs_hi(v.x), abs_hi(v.y)));
   }
+  __syncthreads();
+  if (threadIdx.x < d.bb)  // the rows P of Y now extend over the columns P
+    atomicMax(oz.ymax + int64_t(pole) * oz.ymax_stride + oz.ymax_off[d.f] + p0 + threadIdx.x, s_rmax[threadIdx.x]);
 }
 
 }  // namespace
@@ -1637,11 +1693,18 @@ void launch_oz_panel_real(double* F, const DevFronts& fr, const int32_t* fronts,
 
 // Fused Takahashi step: exponents of A and slices of B (prep = true), then
 // the GEMM that slices A on the fly (prep = false).
+void launch_oz_rowmax_init(const double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_m,
+                           const OzScratch& oz, int nb, cudaStream_t st) {
+  if (nfronts <= 0 || max_m <= 0) return;
+  dim3 g(ceil_div(max_m, 8), nfronts, nb);
+  k_oz_rowmax_init<<<g, 256, 0, st>>>(Y, fr, fronts, oz);
+}
+
 void launch_oz_takahashi(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
                          int max_mp, int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, bool prep) {
   if (nfronts <= 0 || max_mp <= 0) return;
   if (prep) {
-    const int groupsA = (max_mp + 7) / 8, groupsB = (b + 7) / 8;
+    const int groupsA = (max_mp + 255) / 256, groupsB = (b + 7) / 8;
     dim3 g(groupsA + groupsB, nfronts, nb);
     k_oz_tak_prep<<<g, 256, 0, st>>>(Y, F, fr, fronts, p0, b, S, groupsA, oz);
   } else {

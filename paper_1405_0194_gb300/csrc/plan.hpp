@@ -84,6 +84,7 @@ struct Workspace {
   double2* ainv = nullptr;
   uint8_t *ozA = nullptr, *ozB = nullptr;  // split-precision slice tiles
   int *exA = nullptr, *exB = nullptr, *ozfail = nullptr;
+  uint32_t* ymax = nullptr;  // split path: row maxima of Y per pole
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool async = false;  // buffers from cudaMallocAsync on `stream`
@@ -112,6 +113,8 @@ struct pexsi_plan {
   // per batch member): slice tiles of A and B, exponents of A rows, B columns
   int oz_slices = 0;
   int64_t *d_ozA_off = nullptr, *d_ozB_off = nullptr, *d_exA_off = nullptr, *d_exB_off = nullptr;
+  int64_t* d_ymax_off = nullptr;  // first row of each front among all fronts' rows
+  int64_t ymax_stride = 0;        // sum of m_K
   int64_t ozA_stride = 0, ozB_stride = 0, exA_stride = 0, exB_stride = 0;
   // the same for the real Schur update of the inertia factorisation (twice
   // as many batch members share the scratch; exponents use the offsets above)
