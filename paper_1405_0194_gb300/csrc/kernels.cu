@@ -300,6 +300,7 @@ template <>
 __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* singular) {
   __shared__ int s_piv[3];  // kind (1 or 2), row r, flag
   __shared__ int s_neg;
+  __shared__ double s_u[64], s_w[64];  // the pivot columns times the pivot's inverse, per row j
   const double alpha = (1.0 + sqrt(17.0)) / 8.0;
   if (threadIdx.x == 0) s_neg = 0;
   __syncthreads();
@@ -358,9 +359,11 @@ __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* 
         if (d == 0.0) *singular = true;
       }
       double inv = d != 0.0 ? 1.0 / d : 0.0;
+      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) s_u[j] = Bm[j * ld + k] * inv;
+      __syncthreads();
       for (int idx = threadIdx.x; idx < (n - k - 1) * (n - k - 1); idx += blockDim.x) {
         int i = k + 1 + idx % (n - k - 1), j = k + 1 + idx / (n - k - 1);
-        Bm[i * ld + j] -= Bm[i * ld + k] * Bm[j * ld + k] * inv;
+        Bm[i * ld + j] = fma(-Bm[i * ld + k], s_u[j], Bm[i * ld + j]);
       }
       __syncthreads();
       k += 1;
@@ -374,13 +377,17 @@ __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* 
       }
       double id = det != 0.0 ? 1.0 / det : 0.0;
       int nn = n - k - 2;
+      // [xi0 xi1] E^{-1} [xj0; xj1], E^{-1} = [c -b; -b a] / det: the
+      // factor E^{-1} [xj0; xj1] = (u_j, w_j) once per row j
+      for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) {
+        const double xj0 = Bm[j * ld + k], xj1 = Bm[j * ld + k + 1];
+        s_u[j] = (c * xj0 - b * xj1) * id;
+        s_w[j] = (-b * xj0 + a * xj1) * id;
+      }
+      __syncthreads();
       for (int idx = threadIdx.x; idx < nn * nn; idx += blockDim.x) {
         int i = k + 2 + idx % nn, j = k + 2 + idx / nn;
-        double xi0 = Bm[i * ld + k], xi1 = Bm[i * ld + k + 1];
-        double xj0 = Bm[j * ld + k], xj1 = Bm[j * ld + k + 1];
-        // [xi0 xi1] E^{-1} [xj0; xj1], E^{-1} = [c -b; -b a] / det
-        double v = (xi0 * (c * xj0 - b * xj1) + xi1 * (-b * xj0 + a * xj1)) * id;
-        Bm[i * ld + j] -= v;
+        Bm[i * ld + j] = fma(-Bm[i * ld + k], s_u[j], fma(-Bm[i * ld + k + 1], s_w[j], Bm[i * ld + j]));
       }
       __syncthreads();
       k += 2;
@@ -390,8 +397,12 @@ __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* 
   __syncthreads();
 }
 
+// Threads of a block inversion (8 warps; 16 measured slower: the FP64 pipe
+// of each SM is the bound, not the latency of its multiply-adds).
+constexpr int kDiagThreads = 256;
+
 template <typename T>
-__global__ void k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
+__global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
                            DevStatus st, int count_inertia) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Aug = reinterpret_cast<T*>(smem_raw);  // bb x bb, row-major, stride b+1, inverted in place
@@ -773,7 +784,7 @@ void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfron
   if (nfronts <= 0) return;
   size_t smem = sizeof(T) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
-  k_diag_inv<T><<<grid, 256, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
+  k_diag_inv<T><<<grid, kDiagThreads, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
 }
 
 template <typename T>
