@@ -107,3 +107,21 @@ def test_split_matches_fp64_gpu_path_at_full_size():
     print(f"fluid512 split(6) vs FP64: max|dDM| = {err:.3e}, dTr = {abs(ia['trace_dm_s'] - ib['trace_dm_s']):.3e}, "
           f"ms {ia['ms_total']:.0f} -> {ib['ms_total']:.0f}")
     assert err <= TOL_SPLIT
+
+
+def test_split_inertia_matches_fp64_gpu_path_at_full_size():
+    """fluid512: the split real LDL^T, whose 5005-wide root supernode runs
+    many 4-panel blocks of the blocked Schur update, gives the same inertia
+    counts as the FP64 GPU path at shifts around mu (a count can differ only
+    if an eigenvalue lies within the split path's error, ~1e-10, of a shift)."""
+    s = ns.make_fluid(nmol=512, seed=0)
+    mu, _ = ns.mu_and_delta_e(s)
+    shifts = mu + np.array([-0.37, -0.11, -0.023, 0.0071, 0.041, 0.29])
+    counts = []
+    for k in (0, 6):
+        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(max_batch=8, split_slices=k))
+        counts.append(px.pexsi_inertia(plan, s.H, s.S, shifts))
+        px.pexsi_plan_destroy(plan)
+    print(f"fluid512 inertia counts: FP64 {counts[0].tolist()}, split(6) {counts[1].tolist()}")
+    assert np.all(np.diff(counts[0]) >= 0)
+    np.testing.assert_array_equal(counts[1], counts[0])
