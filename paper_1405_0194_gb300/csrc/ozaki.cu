@@ -8,9 +8,11 @@
 // and each row j of B (both stored K-major) is scaled by a power of two
 // 2^e > max |entry| and cut into S slices of small integers,
 //   x = A_ik / 2^e_i = sum_s a_s 2^(-7 s) + r,  |a_1| <= 128, |a_s| <= 64 (s > 1),
-// |r| <= 2^(-7 S - 1), each slice exact in bfloat16. The cut works on the
-// bit pattern of the double (round to a 7S-bit fixed-point integer, then
-// balanced base-128 digits), so no FP64 instruction is spent on it.
+// |r| <= 2^(-7 S - 1), each slice exact in bfloat16. The cut rounds to a
+// 7S-bit fixed-point integer (half of the entries by one FP64 fused
+// multiply-add, half from the bit pattern with integer operations, which
+// balances the two pipes) and takes its balanced base-128 digits without a
+// carry chain (one mask and one float add per digit).
 //
 // Complex products as real MMAs: a tile of 64 complex rows of A becomes the
 // 128 x K real operand [Ar; Ai] (P1) and, one slice block further on,
@@ -1039,9 +1041,10 @@ constexpr int kFThreads = (kFWorkers + 1) * 32;
 constexpr int kFStage = 4 * 32 * 8 * 16;  // FP64 entries of A for one half's next tile (16 KiB)
 constexpr int kFSmem = kFSlots * kFSlot + 2 * kFStage;
 
-// Row exponents of A = Y[S,S] (A groups) and the slices of B = L[S,P] in the
-// 16-deep tile layout (B groups); grid (groups of A, then of B; fronts; poles).
-__global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__ Y, const double2* __restrict__ F,
+// Row exponents of A = Y[S,S] from the row maxima of Y (A groups, 256 rows
+// each) and the slices of B = L[S,P] in the 16-deep tile layout (B groups, 8
+// rows each); grid (groups of A, then of B; fronts; poles).
+__global__ void __launch_bounds__(256) k_oz_tak_prep(const double2* __restrict__ /*Y*/, const double2* __restrict__ F,
                                                      DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
                                                      int S, int groupsA, OzScratch oz) {
   PanelDims d;
