@@ -235,7 +235,8 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
     const int32_t* dfr = p->d_level_fronts + lv.front_off;
     for (size_t k = 0; k < lv.ea_off.size(); ++k) {
       cudaEvent_t a = pf.begin(st);
-      launch_extend_add<T>(F, fr, p->d_ea + lv.ea_off[k], lv.ea_count[k], lv.ea_tiles[k], sh, st);
+      launch_extend_add<T>(F, fr, p->d_ea + lv.ea_off[k], lv.ea_count[k], p->d_tile_pref + lv.ea_pref_off[k],
+                           lv.ea_total[k], sh, st);
       pf.end(a, P_EXTEND, st, 0.0, nb * lv.ea_elems[k] * es);
     }
     for (int p0 = 0; p0 < lv.max_s; p0 += b) {
@@ -336,7 +337,7 @@ void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Pro
     const Level& lv = p->levels[L];
     const int32_t* dfr = p->d_level_fronts + lv.front_off;
     cudaEvent_t a = pf.begin(st);
-    launch_gather(ws.Y, fr, dfr, int(lv.fronts.size()), int(lv.gather_tiles), sh, st);
+    launch_gather(ws.Y, fr, dfr, int(lv.fronts.size()), p->d_tile_pref + lv.gather_pref_off, lv.gather_total, sh, st);
     pf.end(a, P_GATHER, st, 0.0, nb * lv.gather_bytes);
     if (p->oz_slices > 0) {
       int max_m = 0;
@@ -579,7 +580,7 @@ namespace {
 
 void free_plan_device(pexsi_plan* p) {
   void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
-                  p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_part_off, p->d_ident,
+                  p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_tile_pref, p->d_part_off, p->d_ident,
                   p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off, p->d_ozA_off_r, p->d_ozB_off_r,
                   p->d_ymax_off};
   for (void* q : ptrs)
@@ -609,7 +610,8 @@ T* dev_upload(const std::vector<T>& h) {
 }
 
 void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector<int32_t>& ea,
-                  std::vector<int64_t>& part_off) {
+                  std::vector<int64_t>& part_off,
+                  std::vector<int32_t>& tile_pref) {
   const Symbolic& S = p->sym;
   const int b = p->b;
   p->levels.assign(S.nlevels, Level());
@@ -624,6 +626,8 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
     std::stable_sort(fr.begin(), fr.end(), [&](int32_t a, int32_t c) { return S.s(a) > S.s(c); });
     lv.front_off = int64_t(level_fronts.size());
     lv.fronts = fr;
+    lv.gather_pref_off = int64_t(tile_pref.size());
+    tile_pref.push_back(0);
     int64_t slots = 0;
     for (int32_t K : fr) {
       lv.s.push_back(S.s(K));
@@ -632,6 +636,8 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
       level_fronts.push_back(K);
       int64_t r = S.r(K);
       lv.gather_tiles = std::max<int64_t>(lv.gather_tiles, ((r + 31) / 32) * ((r + 31) / 32));
+      lv.gather_total += S.parent[K] >= 0 ? ((r + 31) / 32) * ((r + 31) / 32) : 0;
+      tile_pref.push_back(int32_t(lv.gather_total));
       if (S.parent[K] >= 0) lv.gather_bytes += 2.0 * 16.0 * double(r) * double(r);
       int64_t first_mp = S.m(K) - std::min(b, S.s(K));
       part_off[K] = slots * int64_t(b) * b;
@@ -642,6 +648,9 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
     for (int32_t K : fr) maxk = std::max(maxk, kids[K].size());
     for (size_t k = 0; k < maxk; ++k) {
       lv.ea_off.push_back(int64_t(ea.size()));
+      lv.ea_pref_off.push_back(int64_t(tile_pref.size()));
+      tile_pref.push_back(0);
+      int64_t total = 0;
       int32_t cnt = 0, tiles = 0;
       double elems = 0;
       for (int32_t K : fr) {
@@ -651,8 +660,11 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
         ++cnt;
         int32_t r = S.r(c), T = (r + 31) / 32;
         tiles = std::max(tiles, T * (T + 1) / 2);
+        total += T * (T + 1) / 2;
+        tile_pref.push_back(int32_t(total));
         elems += 3.0 * double(r) * (r + 1) / 2;
       }
+      lv.ea_total.push_back(total);
       lv.ea_elems.push_back(elems);
       lv.ea_count.push_back(cnt);
       lv.ea_tiles.push_back(tiles);
@@ -870,9 +882,9 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
     const Symbolic& S = p->sym;
     std::vector<int32_t> hs(S.nsuper), hm(S.nsuper);
     for (int32_t K = 0; K < S.nsuper; ++K) { hs[K] = S.s(K); hm[K] = S.m(K); }
-    std::vector<int32_t> level_fronts, ea;
+    std::vector<int32_t> level_fronts, ea, tile_pref;
     std::vector<int64_t> part_off;
-    build_levels(p, level_fronts, ea, part_off);
+    build_levels(p, level_fronts, ea, part_off, tile_pref);
     for (const Level& lv : p->levels)
       if (lv.fronts.size() > 65535) {  // grid.y limit of the per-level launches
         delete p;
@@ -893,6 +905,7 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
     p->d_entry_pos = dev_upload(S.entry_pos);
     p->d_level_fronts = dev_upload(level_fronts);
     p->d_ea = dev_upload(ea);
+    p->d_tile_pref = dev_upload(tile_pref);
     p->d_part_off = dev_upload(part_off);
     if (p->oz_slices > 0) {
       std::vector<int64_t> oa, ob, xa, xb, ra, rb;

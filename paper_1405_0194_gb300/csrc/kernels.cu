@@ -79,6 +79,18 @@ template <> __device__ __forceinline__ double2 make_shift<double2>(double h, dou
 }
 
 // lower-triangle tile index t -> (I, J), I >= J
+// Owner of tile t in a flat tile list: the largest item f with pref[f] <= t
+// (pref[0] = 0, pref[n] = the total; items without tiles repeat a value).
+__device__ __forceinline__ int tile_owner(const int32_t* __restrict__ pref, int n, int t) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pref[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
   int i = int((sqrt(8.0 * double(t) + 1.0) - 1.0) * 0.5);
   while (i * (i + 1) / 2 > t) --i;
@@ -259,18 +271,17 @@ __global__ void k_assemble(T* __restrict__ F, const double* __restrict__ H, cons
 
 // U_c (trailing r x r lower block of child c) added into the parent front.
 template <typename T>
-__global__ void k_extend_add(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ children, int nchild) {
-  const int ci = blockIdx.y;
-  if (ci >= nchild) return;
+__global__ void k_extend_add(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ children, int nchild,
+                             const int32_t* __restrict__ pref) {
+  // one block per lower-triangle 32x32 tile of some child's update block
+  const int ci = tile_owner(pref, nchild, int(blockIdx.x));
   const int c = children[ci];
   const int64_t base = int64_t(blockIdx.z) * fr.pool;
   const int s = fr.s[c], m = fr.m[c], r = m - s;
   const int P = fr.parent[c];
   const int mP = fr.m[P];
-  const int Tn = (r + 31) / 32;
-  if (int(blockIdx.x) >= Tn * (Tn + 1) / 2) return;
   int I, J;
-  tri_tile(blockIdx.x, I, J);
+  tri_tile(int(blockIdx.x) - pref[ci], I, J);
   const T* Fc = F + base + fr.off[c];
   T* Fp = F + base + fr.off[P];
   const int32_t* rel = fr.rel + fr.rptr[c];
@@ -580,14 +591,16 @@ __global__ void __launch_bounds__(256) k_trailing(T* __restrict__ F, DevFronts f
 }
 
 // ------------------------------------------------------------ selected inversion
-__global__ void k_gather(double2* __restrict__ Y, DevFronts fr, const int32_t* __restrict__ fronts) {
-  const int f = fronts[blockIdx.y];
+__global__ void k_gather(double2* __restrict__ Y, DevFronts fr, const int32_t* __restrict__ fronts, int nfronts,
+                         const int32_t* __restrict__ pref) {
+  // one block per 32x32 tile of some front's Y[C,C] (fronts without a parent have none)
+  const int fi = tile_owner(pref, nfronts, int(blockIdx.x));
+  const int f = fronts[fi];
   const int P = fr.parent[f];
-  if (P < 0) return;
   const int s = fr.s[f], m = fr.m[f], r = m - s, mP = fr.m[P];
   const int Tn = (r + 31) / 32;
-  if (int(blockIdx.x) >= Tn * Tn) return;
-  const int I = blockIdx.x % Tn, J = blockIdx.x / Tn;
+  const int t = int(blockIdx.x) - pref[fi];
+  const int I = t % Tn, J = t / Tn;
   const int64_t base = int64_t(blockIdx.z) * fr.pool;
   double2* Yf = Y + base + fr.off[f];
   const double2* Yp = Y + base + fr.off[P];
@@ -771,11 +784,11 @@ void launch_assemble(T* F, const double* H, const double* S, const int64_t* src,
 }
 
 template <typename T>
-void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int nchild, int max_tiles,
-                       const BatchShifts& sh, cudaStream_t st) {
-  if (nchild <= 0 || max_tiles <= 0) return;
-  dim3 grid(max_tiles, nchild, sh.nb), block(32, 8);
-  k_extend_add<T><<<grid, block, 0, st>>>(F, fr, children, nchild);
+void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int nchild, const int32_t* pref,
+                       int64_t total_tiles, const BatchShifts& sh, cudaStream_t st) {
+  if (nchild <= 0 || total_tiles <= 0) return;
+  dim3 grid(unsigned(total_tiles), 1, sh.nb), block(32, 8);
+  k_extend_add<T><<<grid, block, 0, st>>>(F, fr, children, nchild, pref);
 }
 
 template <typename T>
@@ -803,11 +816,11 @@ void launch_trailing(T* F, const DevFronts& fr, const int32_t* fronts, int nfron
   k_trailing<T><<<grid, 256, kSmem3m, st>>>(F, fr, fronts, p0, b);
 }
 
-void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
-                   const BatchShifts& sh, cudaStream_t st) {
-  if (nfronts <= 0 || max_tiles <= 0) return;
-  dim3 grid(max_tiles, nfronts, sh.nb), block(32, 8);
-  k_gather<<<grid, block, 0, st>>>(Y, fr, fronts);
+void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, const int32_t* pref,
+                   int64_t total_tiles, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || total_tiles <= 0) return;
+  dim3 grid(unsigned(total_tiles), 1, sh.nb), block(32, 8);
+  k_gather<<<grid, block, 0, st>>>(Y, fr, fronts, nfronts, pref);
 }
 
 void launch_selinv_offdiag(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
@@ -876,8 +889,8 @@ cudaError_t configure_kernels(int b) {
 #define PEXSI_INSTANTIATE(T)                                                                                        \
   template void launch_assemble<T>(T*, const double*, const double*, const int64_t*, const int64_t*, int64_t,    \
                                    int64_t, const BatchShifts&, cudaStream_t);                                   \
-  template void launch_extend_add<T>(T*, const DevFronts&, const int32_t*, int, int, const BatchShifts&,         \
-                                     cudaStream_t);                                                               \
+  template void launch_extend_add<T>(T*, const DevFronts&, const int32_t*, int, const int32_t*, int64_t,        \
+                                     const BatchShifts&, cudaStream_t);                                           \
   template void launch_diag_inv<T>(T*, const DevFronts&, const int32_t*, int, int, int, const BatchShifts&,      \
                                    DevStatus, bool, cudaStream_t);                                                \
   template void launch_panel_solve<T>(T*, const DevFronts&, const int32_t*, int, int, int, int,                  \

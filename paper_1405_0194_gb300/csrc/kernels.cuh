@@ -71,8 +71,8 @@ void launch_assemble(T* F, const double* H, const double* S, const int64_t* src,
                      int64_t pool, const BatchShifts& sh, cudaStream_t st);
 
 template <typename T>
-void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int nchild, int max_tiles,
-                       const BatchShifts& sh, cudaStream_t st);
+void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int nchild, const int32_t* pref,
+                       int64_t total_tiles, const BatchShifts& sh, cudaStream_t st);
 
 template <typename T>
 void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
@@ -86,8 +86,8 @@ template <typename T>
 void launch_trailing(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles, int p0, int b,
                      const BatchShifts& sh, cudaStream_t st);
 
-void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_tiles,
-                   const BatchShifts& sh, cudaStream_t st);
+void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, const int32_t* pref,
+                   int64_t total_tiles, const BatchShifts& sh, cudaStream_t st);
 
 void launch_selinv_offdiag(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
                            int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st);

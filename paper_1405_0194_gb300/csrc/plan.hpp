@@ -40,6 +40,10 @@ struct Level {
   std::vector<double> ea_elems;  // elements moved by each extend-add launch
   int64_t gather_tiles = 0;
   double gather_bytes = 0;
+  // flat tile lists: prefix sums of the fronts' (or children's) 32x32 tiles in
+  // the plan's d_tile_pref, so that a launch has exactly one block per tile
+  int64_t gather_pref_off = 0, gather_total = 0;
+  std::vector<int64_t> ea_pref_off, ea_total;
   int32_t max_s = 0;
 };
 
@@ -106,6 +110,7 @@ struct pexsi_plan {
   int64_t* d_entry_pos = nullptr;
   int32_t* d_level_fronts = nullptr;
   int32_t* d_ea = nullptr;
+  int32_t* d_tile_pref = nullptr;  // see Level::gather_pref_off / ea_pref_off
   int64_t* d_part_off = nullptr;
   int64_t part_stride = 0;  // partial-scratch elements per batch member
   double* d_ident = nullptr;
