@@ -237,6 +237,35 @@ def make_fluid(nmol: int = 512, seed: int = 0, cutoff: float = 10.0, lam: float 
                   dict(kind="fluid", nmol=nmol, box=box, cutoff=cutoff, lam=lam))
 
 
+def hermitian_from(sys: System, seed: int, imag_scale: float = 0.25):
+    """Complex Hermitian H and S on the pattern of `sys` (the k-point /
+    spin-orbit variant): H' = H + i A and S' = S + i B, with A and B real
+    antisymmetric (A_ij = -A_ji, zero diagonal) of magnitude imag_scale |H_ij|
+    and imag_scale |S_ij| / 2 times N(0,1). The diagonal of S' is reset to
+    1 + sum_{j != i} |S'_ij| + 0.1, so that S' is Hermitian, strictly
+    diagonally dominant with a positive diagonal, hence positive definite.
+    Returns (H', S') as complex128 arrays of nnz values in CSC order."""
+    rng = np.random.default_rng(seed)
+    n, colptr, rowind = sys.n, sys.colptr, sys.rowind
+    cols = np.repeat(np.arange(n), np.diff(colptr))
+    off = rowind != cols
+
+    def antisym(mag):
+        raw = np.where(off, mag * rng.standard_normal(sys.nnz), 0.0)
+        t = sp.csc_matrix((raw, rowind, colptr), shape=(n, n)).T.tocsc()
+        t.sort_indices()
+        # the pattern is symmetric, so the transpose has the same CSC structure
+        assert np.array_equal(t.indptr, colptr) and np.array_equal(t.indices, rowind)
+        return 0.5 * (raw - t.data)
+
+    Hc = sys.H + 1j * antisym(imag_scale * np.abs(sys.H))
+    Sc = sys.S + 1j * antisym(0.5 * imag_scale * np.abs(sys.S))
+    absrow = np.bincount(cols[off], weights=np.abs(Sc[off]), minlength=n)
+    diag = ~off
+    Sc[diag] = 1.0 + absrow[cols[diag]] + 0.1
+    return Hc.astype(np.complex128), Sc.astype(np.complex128)
+
+
 def spectral_interval(sys: System, dense_limit: int = 4096, margin: float = 0.05):
     """Bounds [E_min, E_max] of the generalised spectrum of (H, S).
 

@@ -16,8 +16,12 @@ Contents (all FP64 / complex128, plain numpy / scipy):
   (Sec. II.C, Sylvester's law of inertia).
 * :mod:`oracle.sampled` -- the same definitions evaluated column by column
   with a sparse LU solve, for sizes where a dense inverse is too slow.
+* :mod:`oracle.hermitian` -- complex Hermitian H and S (the k-point /
+  spin-orbit variant, Sec. IV): Gamma = sum_l (w_l G_l - conj(w_l) G_l^H) / 2i
+  on the pattern, and Tr[Gamma S].
 
-Every function is pinned by tests in ``tests/test_oracle_pins.py`` against
+Every function is pinned by tests in ``tests/test_oracle_pins.py`` (and
+``tests/test_oracle_hermitian.py`` for the Hermitian variant) against
 closed forms (generalised eigen-decomposition), invariants and special
 cases. No function here is "parity unpinned".
 """
