@@ -18,11 +18,12 @@ with H and S resident on the device; e2e = the same through the host-buffer
 call (H, S copied in and DM/EDM/FDM copied out every step, from pinned host
 memory).
 
-By default (--split 6) the two large complex supernode GEMMs (the Schur
-update and the Takahashi step) run as exact 6-slice bf16 products on the
-tcgen05 tensor cores with FP64 in and out; everything else is FP64. The
-plain FP64 path is timed after it on the same workload ("fp64_path"), with
-the largest difference between the two on one identical pole batch.
+By default (--split 6) all supernode GEMMs (panel solve, Schur update,
+Takahashi step, the Y[P,P] product, and the real ones of the inertia LDL^T)
+run as exact 6-slice bf16 products on the tcgen05 tensor cores with FP64 in
+and out; the D-block inverses and the pole sum are FP64. The plain FP64 path
+is timed after it on the same workload ("fp64_path"), with the largest
+difference between the two on one identical pole batch.
 
 With --impl reference the CPU oracle is timed instead on the same workload
 (a bounded sample per step: the dense LU of one shifted matrix plus a
