@@ -1114,7 +1114,9 @@ __global__ void __launch_bounds__(256) k_oz_rowmax_init(const double2* __restric
 }
 
 // KIND 0, Takahashi step: one CTA per 64-row tile of S (front, pole); A =
-//   Y[S,S] rows cut on the fly, B = L[S,P] slices staged by k_oz_tak_prep.
+//   Y[S,S] rows cut on the fly, B = L[S,P] slices staged by k_oz_tak_prep;
+//   its epilogue writes Y[S,P] and Y[P,S] and raises the row maxima of Y
+//   (rows S, and by a warp reduction over its rows, rows P).
 // KIND 1, the product L[S,P]^T Y[S,P] of Y[P,P] = D^-1 - L[S,P]^T Y[S,P]:
 //   one CTA per 256-deep K range (front, pole); A = L[S,P] columns and B =
 //   Y[S,P] columns both cut on the fly; the exact int64 sums of the range go
