@@ -1377,6 +1377,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
       bar_arrive(smem_u32(&full_a[slot]));
     }
     while (ok && drained < nchunks) ok = drain(drained++);
+    cp_async_wait_all();  // after a failure too: no staging copy outlives the CTA
   }
 
   __syncthreads();
