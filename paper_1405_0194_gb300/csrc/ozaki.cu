@@ -33,7 +33,7 @@
 // the accumulation is exact. After each chunk the epilogue warps convert the
 // accumulators to integers and combine them exactly in 64-bit integers,
 // sum_D acc_D 2^(7 (S + 1 - D)) (magnitude below 2^58.1 per chunk, so eight
-// chunks stay below 2^61); the final scaling by 2^(e_i + f_j - 7 (S + 1)) is
+// chunks stay below 2^61.1, inside int64); the final scaling by 2^(e_i + f_j - 7 (S + 1)) is
 // folded into an integer-only int64 -> double conversion. Pairs with
 // s + t > S + 1 are dropped (their contribution is below 2^(-7 (S + 2)) of
 // |A_i| |B_j|).
