@@ -92,3 +92,17 @@ def test_hermitian_inertia_sylvester(herm_chain):
     for sigma, want in zip(shifts, counts):
         _, Dm, _ = sla.ldl(Hd - sigma * Sd, hermitian=True)
         assert int(np.sum(np.linalg.eigvalsh(Dm) < 0)) == want
+
+
+def test_sampled_columns_match_dense(herm_chain):
+    """The sparse-LU column evaluation equals the dense definition."""
+    s, H, S, mu, dE = herm_chain
+    full = hermitian.density_matrices_hermitian(s.n, s.colptr, s.rowind, H, S, mu, s.beta, 40, dE)
+    tab = full[3]
+    cols = [0, 7, s.n // 2, s.n - 1]
+    got = hermitian.dm_columns_hermitian(s.n, s.colptr, s.rowind, H, S, tab, cols)
+    for j in cols:
+        lo, hi = s.colptr[j], s.colptr[j + 1]
+        for q in range(3):
+            ref = full[q][lo:hi]
+            assert np.max(np.abs(got[j][q] - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
