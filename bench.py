@@ -6,24 +6,27 @@ Workload (default, --workload fluid): the 3D periodic water-like fluid, 512
 pair cutoff, beta = 1000 / Ha, a 60-pole expansion, complex FP64; mu at the
 centre of the spectral interval and Delta E its half-width + 10%.
 
-One step = one pass of the whole hot path over one 20-pole batch: the pole
-table, assembly of H - (z_l + mu) S, supernodal LDL^T, selected inversion,
-the DM/EDM/FDM pole sum accumulated over the batch, the Tr[DM S] check, and
-the inertia counts of a share of the real shifts (16 shifts per 60 poles, so
-5 per step). All poles of a batch run in the same kernel launches; the batch
-is as large as HBM allows because the top of the elimination tree has one
-front per pole.
-Successive steps walk through the 60 poles. value = pole-solves / second
-with H and S resident on the device; e2e = the same through the host-buffer
-call (H, S copied in and DM/EDM/FDM copied out every step, from pinned host
-memory).
+One step = one pass of the whole hot path over one batch of poles (4 by
+default): the pole table, assembly of H - (z_l + mu) S, supernodal LDL^T,
+selected inversion, the DM/EDM/FDM pole sum accumulated over the batch, the
+Tr[DM S] check, and the step's share of the 16 real inertia shifts per 60
+poles (cumulatively rounded, so that 15 steps of 4 poles take all 16). All
+poles of a batch run in the same kernel launches. Successive steps walk
+through the 60 poles. value = pole-solves / second of the plain FP64 path
+with H and S resident on the device (no per-launch instrumentation in the
+timed region; per-kernel shares come from separate instrumented steps);
+e2e = the same steps through the host-buffer calls (H, S copied in and
+DM/EDM/FDM copied out every step, from pinned host memory); dm_latency =
+the full 60-pole pexsi_dm host call.
 
-By default (--split 6) all supernode GEMMs (panel solve, Schur update,
-Takahashi step, the Y[P,P] product, and the real ones of the inertia LDL^T)
-run as exact 6-slice bf16 products on the tcgen05 tensor cores with FP64 in
-and out; the D-block inverses and the pole sum are FP64. The plain FP64 path
-is timed after it on the same workload ("fp64_path"), with the largest
-difference between the two on one identical pole batch.
+Beside it ("split_path", --split-compare 6): all supernode GEMMs (panel
+solve, Schur update, Takahashi step, the Y[P,P] product, and the real ones of
+the inertia LDL^T) as exact 6-slice bf16 products on the tcgen05 tensor
+cores with FP64 in and out (the D-block inverses and the pole sum FP64), in
+20-pole steps, with its roofline, its 60-pole call latency, and its error
+against the FP64 path and the oracle on the poles that carry the DM.
+"oracle_error" states the error of each path against the eigen closed form
+of the oracle in sampled columns.
 
 With --impl reference the CPU oracle is timed instead on the same workload
 (a bounded sample per step: the dense LU of one shifted matrix plus a
@@ -171,47 +174,6 @@ def gemm_rate(kernels: dict) -> dict:
     return {"fp64_equivalent_tflops": tf, "fp64_peak_tflops": FP64_PEAK_TFLOPS, "vs_fp64_peak": tf / FP64_PEAK_TFLOPS}
 
 
-def fp64_path(px, s, mu, dE, device, dH, dS, stream, args, B, Q, all_shifts, split_dm):
-    """The plain FP64 path on the same workload and step (fewer timed steps),
-    and the split path's deviation from it on one identical pole batch."""
-    import torch
-    P = s.n_poles
-    plan = px.pexsi_setup(s.n, s.colptr, s.rowind,
-                          opts=px.pexsi_opts_default(device=device, max_batch=B, split_slices=0))
-    o = torch.zeros(3, s.nnz, dtype=torch.float64, device=dH.device)
-    px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, 0, B, 0,
-                       o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
-    ref = o.cpu().numpy()
-    px.pexsi_profile_reset(plan)
-    px.pexsi_profile_enable(plan, True)
-    torch.cuda.synchronize(dH.device)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(args.fp64_steps):
-        b0 = ((1 + i) * B) % P
-        px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, b0, min(P, b0 + B), 1,
-                           o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
-        sh = all_shifts[(i * Q) % 16:(i * Q) % 16 + Q]
-        px.pexsi_inertia_device(plan, dH.data_ptr(), dS.data_ptr(), sh, stream)
-    e1.record()
-    torch.cuda.synchronize(dH.device)
-    ms = e0.elapsed_time(e1)
-    prof = px.pexsi_profile_read(plan)
-    px.pexsi_plan_destroy(plan)
-    kern = {p["name"]: p for p in prof}
-    dom = max(prof, key=lambda p: p["ms"])
-    scale = [float(np.max(np.abs(ref[k]))) for k in range(3)]
-    dev = [float(np.max(np.abs(ref[k] - split_dm[k]))) for k in range(3)]
-    return {"value": B * args.fp64_steps / (ms / 1e3), "unit": "pole-solves/s", "steps": args.fp64_steps,
-            "ms_per_step": ms / args.fp64_steps, "dominant": roofline_of(dom, sum(p["ms"] for p in prof), {}, 0),
-            "gemm_rate": gemm_rate(kern),
-            "split_vs_fp64_same_batch": {"max_abs": {"dm": dev[0], "edm": dev[1], "fdm": dev[2]},
-                                         "max_abs_over_max_entry": {"dm": dev[0] / scale[0], "edm": dev[1] / scale[1],
-                                                                    "fdm": dev[2] / scale[2]},
-                                         "batch": f"poles 0..{B - 1}"}}
-
-
 def prepare(workload: str, seed: int):
     w = WORKLOADS[workload]
     s = w["make"](seed)
@@ -242,16 +204,16 @@ def run_reference(args):
     s, mu, dE = prepare(args.workload, args.seed)
     rng = np.random.default_rng(1)
     for i in range(args.warmup):
-        oracle_pole_sample(s, mu, dE, i, args.oracle_cols, rng)
+        oracle_pole_sample(s, mu, dE, i, args.cpu_cols, rng)
     per_pole = []
     wall = 0.0
     for i in range(args.steps):
-        est, w = oracle_pole_sample(s, mu, dE, args.warmup + i, args.oracle_cols, rng)
+        est, w = oracle_pole_sample(s, mu, dE, args.warmup + i, args.cpu_cols, rng)
         per_pole.append(est)
         wall += w
     v = 1.0 / float(np.mean(per_pole))
     cores = os.cpu_count()
-    sample = (f"per step: dense LU of one {s.n}x{s.n} shifted matrix + {args.oracle_cols} of {s.n} columns "
+    sample = (f"per step: dense LU of one {s.n}x{s.n} shifted matrix + {args.cpu_cols} of {s.n} columns "
               f"solved, extrapolated to all columns = one pole-solve")
     line = {"impl": "reference", "metric": "pole-solves/sec", "value": v, "unit": "pole-solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -265,6 +227,84 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def shifts_in_step(i: int, B: int, per60: int) -> tuple[int, int]:
+    """Inertia shifts [a, b) of the 16-shift grid that step i takes: the
+    shifts are spread over the steps in proportion to their poles (per60
+    shifts per 60 poles), cumulatively rounded, cycling through the grid."""
+    a = (i * B * per60) // 60
+    b = ((i + 1) * B * per60) // 60
+    return a, b
+
+
+def make_step(px, plan, s, mu, dE, dH, dS, out, stream, B, per60, all_shifts, world=1, rank=0):
+    """One step: a B-pole batch of the P-pole table (walking through the
+    table) into the accumulated outputs, with Tr[DM S], and its share of the
+    16 inertia shifts; device-resident H and S."""
+    P = s.n_poles
+
+    def step(i):
+        b0 = ((i * world + rank) * B) % P
+        b1 = min(P, b0 + B)
+        info = px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, b0, b1, 1,
+                                  out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), stream, want_info=True)
+        a, b = shifts_in_step(i, B, per60)
+        if b > a:
+            sh = np.array([all_shifts[k % 16] for k in range(a, b)])
+            px.pexsi_inertia_device(plan, dH.data_ptr(), dS.data_ptr(), sh, stream)
+        if info["breakdown_front"] != -1:
+            raise RuntimeError(f"breakdown in front {info['breakdown_front']}")
+        return b1 - b0
+
+    return step
+
+
+def instrumented(px, plan, step, first, n, dev):
+    """Per-kernel-class CUDA-event timings of n steps run after the timed
+    region (the timed region itself runs without per-launch events)."""
+    import torch
+    px.pexsi_profile_reset(plan)
+    px.pexsi_profile_enable(plan, True)
+    for i in range(n):
+        step(first + i)
+    torch.cuda.synchronize(dev)
+    prof = px.pexsi_profile_read(plan)
+    px.pexsi_profile_enable(plan, False)
+    return prof
+
+
+def dm_latency(px, plan, s, mu, dE, calls: int) -> dict:
+    """Latency of the full P-pole pexsi_dm host call (H, S in; DM, EDM, FDM
+    out; synchronous), p50 / p99 over `calls` calls."""
+    pin = lambda a: __import__("torch").from_numpy(a).pin_memory().numpy()
+    H, S = pin(s.H), pin(s.S)
+    lat = []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        px.pexsi_dm(plan, H, S, mu, s.beta, s.n_poles, dE)
+        lat.append(1e3 * (time.perf_counter() - t0))
+    lat = np.array(lat)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "calls": calls, "samples_ms": [round(float(x), 1) for x in lat], "n_poles": s.n_poles,
+            "call": "pexsi_dm (host buffers; H, S copied in, DM, EDM, FDM copied out)"}
+
+
+def oracle_error(s, mu, dE, got: np.ndarray, poles_idx, ncols: int, eig=None) -> dict:
+    """Largest error of DM / EDM / FDM in ncols sampled columns against the
+    oracle's eigen closed form C (Lambda - z)^-1 C^T summed over poles_idx
+    (absolute, and relative to the largest sampled entry)."""
+    from oracle import dense, poles
+    lam, C = eig if eig is not None else dense.eig_pencil(s.n, s.colptr, s.rowind, s.H, s.S)
+    tab = poles.pole_table(s.beta, dE, s.n_poles, mu)
+    cols = np.sort(np.random.default_rng(0).choice(s.n, ncols, replace=False))
+    ref = dense.dm_columns_eig(lam, C, s.colptr, s.rowind, tab, cols, poles_idx)
+    res = {}
+    for q, name in enumerate(("dm", "edm", "fdm")):
+        err = max(float(np.max(np.abs(got[q, s.colptr[j]:s.colptr[j + 1]] - ref[j][q]))) for j in cols)
+        big = max(float(np.max(np.abs(ref[j][q]))) for j in cols)
+        res[name] = {"max_abs": err, "rel_to_max_entry": err / big if big else None}
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -281,8 +321,9 @@ def run_ours(args):
 
     s, mu, dE = prepare(args.workload, args.seed)
     P = s.n_poles
-    plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=local,
-                                                                              max_batch=args.poles_per_step,
+    B = args.poles_per_step or (20 if args.split else 4)
+    per60 = WORKLOADS[args.workload]["shifts_per_60"]
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=local, max_batch=B,
                                                                               split_slices=args.split))
     st = px.pexsi_plan_get_stats(plan)
     dev = torch.device("cuda", local)
@@ -290,26 +331,8 @@ def run_ours(args):
     dS = torch.from_numpy(s.S).to(dev)
     out = torch.zeros(3, s.nnz, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    B = args.poles_per_step
-    Q = max(1, round(WORKLOADS[args.workload]["shifts_per_60"] * B / 60))
     all_shifts = mu + np.linspace(-0.5, 0.5, 16) + 1.0e-4
-
-    def step(i, on_device=True, host=None):
-        b0 = ((i * world + rank) * B) % P
-        b1 = min(P, b0 + B)
-        sh = all_shifts[(i * Q) % 16:(i * Q) % 16 + Q]
-        if on_device:
-            info = px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, b0, b1, 1,
-                                      out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), stream,
-                                      want_info=True)
-            px.pexsi_inertia_device(plan, dH.data_ptr(), dS.data_ptr(), sh, stream)
-        else:
-            Hh, Sh, dmh, edmh, fdmh = host
-            info = px.pexsi_dm_poles(plan, Hh, Sh, mu, s.beta, P, dE, b0, b1, 0, dmh, edmh, fdmh)
-            px.pexsi_inertia(plan, Hh, Sh, sh)
-        if info["breakdown_front"] != -1:
-            raise RuntimeError(f"breakdown in front {info['breakdown_front']}")
-        return b1 - b0
+    step = make_step(px, plan, s, mu, dE, dH, dS, out, stream, B, per60, all_shifts, world, rank)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -325,9 +348,7 @@ def run_ours(args):
 
     for i in range(args.warmup):
         step(i)
-    # ---- timed region (device-resident inputs)
-    px.pexsi_profile_reset(plan)
-    px.pexsi_profile_enable(plan, True)
+    # ---- timed region (device-resident inputs, no per-launch instrumentation)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
@@ -341,25 +362,43 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    prof = px.pexsi_profile_read(plan)
-    px.pexsi_profile_enable(plan, False)
     total_solves = solves * world
     value = total_solves / (ms / 1000.0)
+    # ---- per-kernel classes from separate instrumented steps
+    prof = instrumented(px, plan, step, args.warmup + args.steps, args.profile_steps, dev)
 
-    # ---- end to end through the host-buffer call, pinned host memory
+    # ---- end to end through the host-buffer calls, pinned host memory
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-    host = (pin(s.H), pin(s.S), pin(np.zeros(s.nnz)), pin(np.zeros(s.nnz)), pin(np.zeros(s.nnz)))
-    step(0, on_device=False, host=host)
+    Hh, Sh = pin(s.H), pin(s.S)
+    dmh, edmh, fdmh = (pin(np.zeros(s.nnz)) for _ in range(3))
+
+    def host_step(i):
+        b0 = ((i * world + rank) * B) % P
+        b1 = min(P, b0 + B)
+        px.pexsi_dm_poles(plan, Hh, Sh, mu, s.beta, P, dE, b0, b1, 0, dmh, edmh, fdmh)
+        a, b = shifts_in_step(i, B, per60)
+        if b > a:
+            px.pexsi_inertia(plan, Hh, Sh, np.array([all_shifts[k % 16] for k in range(a, b)]))
+        return b1 - b0, b - a
+
+    host_step(0)
     barrier()
     t0 = time.perf_counter()
-    e2e_solves = 0
+    e2e_solves = e2e_shifts = with_shifts = 0
     for i in range(args.e2e_steps):
-        e2e_solves += step(args.warmup + args.steps + i, on_device=False, host=host)
+        a, b = host_step(args.warmup + args.steps + i)
+        e2e_solves += a
+        e2e_shifts += b
+        with_shifts += 1 if b else 0
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = e2e_solves * world / e2e_s
-    h2d = 2 * 2 * s.nnz * 8          # H and S into the DM call and into the inertia call
-    d2h = 3 * s.nnz * 8 + 8 * Q      # DM, EDM, FDM and the counts
+    steps_e2e = max(1, args.e2e_steps)
+    # per step (averaged over the e2e steps): H and S into the DM call, and
+    # again into the inertia call of a step that has shifts; DM, EDM, FDM and
+    # the counts out
+    h2d = int(2 * s.nnz * 8 * (steps_e2e + with_shifts) / steps_e2e)
+    d2h = int(3 * s.nnz * 8 + 8 * e2e_shifts / steps_e2e)
 
     if rank != 0:
         px.pexsi_plan_destroy(plan)
@@ -367,68 +406,160 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant launch class (live CUDA-event timings)
+    # ---- roofline of the dominant launch class (CUDA events on the launch stream)
     kernels = {p["name"]: p for p in prof}
     dom = max(prof, key=lambda p: p["ms"])
-    launches = sum(p["launches"] for p in prof) + kernels["trace"]["launches"]  # trace = 2 kernels
+    per_step_launches = (sum(p["launches"] for p in prof) + kernels["trace"]["launches"]) / max(1, args.profile_steps)
     total_kernel_ms = sum(p["ms"] for p in prof)
     peaks, peak_src = load_peaks()
     roofline = roofline_of(dom, total_kernel_ms, peaks, args.split)
-    roofline["traffic"] = None
-    tpath = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        if tj.get("kernel") == dom["name"] and tj.get("split_slices", 0) == args.split:
-            roofline["traffic"] = tj.get("dram_bytes_per_launch")
+    roofline["traffic"] = traffic_of(args.workload, dom, args.split)
 
-    # split-precision result against the FP64 path on one identical pole batch
-    split_dm = None
-    if args.split and args.fp64_steps > 0:
-        o = torch.zeros(3, s.nnz, dtype=torch.float64, device=dev)
-        px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, 0, B, 0,
-                           o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
-        split_dm = o.cpu().numpy()
-        del o
-
+    latency = dm_latency(px, plan, s, mu, dE, args.latency_calls) if args.latency_calls > 0 else None
     line = {
         "metric": "pole-solves/sec", "value": value, "unit": "pole-solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": (f"f64 in/out; supernode GEMMs as bf16x{args.split} slices on tcgen05 (exact fp32 / int64 "
-                  f"accumulation)" if args.split else "f64"),
+        "dtype": ("f64 in/out; supernode GEMMs as bf16x%d slices on tcgen05 (exact fp32 / int64 accumulation)"
+                  % args.split) if args.split else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "poles_per_step": B, "split_slices": args.split,
-                   "inertia_shifts_per_step": Q, "seed": args.seed, "ordering": "own nested dissection",
-                   "nsuper": st["nsuper"], "nnz_L": st["nnz_L"],
+                   "inertia_shifts": f"{per60} per {P} poles, spread over the steps", "seed": args.seed,
+                   "ordering": "own nested dissection", "nsuper": st["nsuper"], "nnz_L": st["nnz_L"],
                    "gemm_flops_per_pole": st["factor_gemm_flops"] + st["selinv_gemm_flops"],
                    "l2": f"no flush: each step streams {st['front_elems'] * 32 * B / 1e9:.1f} GB of fronts "
                          f"(> 129 MB L2)", "parallelism": "replicas" if world == 1 else f"poles sharded x{world}"},
         "roofline": roofline,
         "gemm_rate": gemm_rate(kernels),
-        "kernel_ms": {p["name"]: round(p["ms"], 3) for p in prof},
+        "kernels_per_step": per_step(prof, args.profile_steps),
         "e2e": {"value": e2e_value, "unit": "pole-solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
-        "gpu_launches": launches,
+        "dm_latency": latency,
+        "gpu_launches": int(round(per_step_launches * args.steps)),
         "clocks": clk,
         "peaks_source": peak_src,
     }
+    ref_dm = None
+    heavy = (max(0, P - 20), P)  # the poles that carry the density matrix
+    if args.split_compare > 0 and args.split == 0 and world == 1:
+        o = torch.zeros(3, s.nnz, dtype=torch.float64, device=dev)
+        px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, heavy[0], heavy[1], 0,
+                           o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
+        ref_dm = o.cpu().numpy()
+        del o
     px.pexsi_plan_destroy(plan)
-    if args.split and args.fp64_steps > 0:
-        line["fp64_path"] = fp64_path(px, s, mu, dE, local, dH, dS, stream, args, B, Q, all_shifts, split_dm)
+    eig = None
+    if world == 1 and args.oracle_cols > 0 and ref_dm is not None:
+        from oracle import dense
+        t0 = time.perf_counter()
+        eig = dense.eig_pencil(s.n, s.colptr, s.rowind, s.H, s.S)
+        eig_s = time.perf_counter() - t0
+        line["oracle_error"] = {"batch": f"poles {heavy[0]}..{heavy[1] - 1} (those carrying the DM)",
+                                "columns": args.oracle_cols, "oracle": "eigen closed form, sampled columns",
+                                "eig_seconds": round(eig_s, 1),
+                                "fp64_path": oracle_error(s, mu, dE, ref_dm, range(*heavy), args.oracle_cols, eig)}
+    if args.split_compare > 0 and args.split == 0 and world == 1:
+        line["split_path"] = split_path(px, s, mu, dE, local, dH, dS, stream, args, per60, all_shifts, ref_dm,
+                                        heavy, eig, peaks)
     if world == 1 and args.serve_requests > 0:
         line["serving"] = serve_trace(px, local, args.serve_rate, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(1)
-        est, wall = oracle_pole_sample(s, mu, dE, 0, args.oracle_cols, rng)
+        est, wall = oracle_pole_sample(s, mu, dE, 0, args.cpu_cols, rng)
         line["cpu_baseline"] = {
             "value": 1.0 / est, "unit": "pole-solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"1 pole: dense LU of the {s.n}x{s.n} shifted matrix + {args.oracle_cols} of {s.n} columns "
-                       f"solved ({wall:.1f} s), extrapolated to all columns = one pole-solve")}
+            "sample": (f"1 pole: the oracle's dense O(n^3) route, not the sparse method -- LU of the {s.n}x{s.n} "
+                       f"shifted matrix + {args.cpu_cols} of {s.n} columns solved ({wall:.1f} s), extrapolated "
+                       f"to all columns = one pole-solve")}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def per_step(prof, steps: int) -> dict:
+    """Per launch class and step: milliseconds, launches, algorithmic bytes
+    and flops (from the library's CUDA-event profiler)."""
+    k = max(1, steps)
+    return {p["name"]: {"ms": round(p["ms"] / k, 3), "launches": p["launches"] / k, "bytes": p["bytes"] / k,
+                        "flops": p["flops"] / k} for p in prof if p["launches"]}
+
+
+def traffic_of(workload: str, dom: dict, split: int):
+    """DRAM bytes per launch of the dominant class from the committed ncu
+    summary profiles/traffic_<workload>.json, when it was taken for this
+    kernel class and precision: the measured DRAM / algorithmic byte ratio of
+    the captured launches times this run's algorithmic bytes per launch."""
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    if not os.path.exists(tpath):
+        return None
+    with open(tpath) as f:
+        tj = json.load(f)
+    if tj.get("kernel_class") != dom["name"] or tj.get("split_slices", 0) != split:
+        return None
+    ratio = tj.get("dram_over_algorithmic")
+    if ratio is None or not dom["launches"]:
+        return None
+    return ratio * dom["bytes"] / dom["launches"]
+
+
+def split_path(px, s, mu, dE, device, dH, dS, stream, args, per60, all_shifts, ref_dm, heavy, eig, peaks):
+    """The split-precision path (bf16 Ozaki slices on the tcgen05 tensor
+    cores) on the same workload: its throughput in 20-pole steps, the
+    roofline of its dominant class, the latency of the full P-pole host call,
+    and its error against the FP64 GPU path and the oracle on the poles that
+    carry the DM."""
+    import torch
+    P, B = s.n_poles, 20
+    S = args.split_compare
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind,
+                          opts=px.pexsi_opts_default(device=device, max_batch=B, split_slices=S))
+    o = torch.zeros(3, s.nnz, dtype=torch.float64, device=dH.device)
+    step = make_step(px, plan, s, mu, dE, dH, dS, o, stream, B, per60, all_shifts)
+    for i in range(3):
+        step(i)
+    torch.cuda.synchronize(dH.device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    solves = 0
+    for i in range(args.split_steps):
+        solves += step(3 + i)
+    e1.record()
+    torch.cuda.synchronize(dH.device)
+    ms = e0.elapsed_time(e1)
+    prof = instrumented(px, plan, step, 3 + args.split_steps, 1, dH.device)
+    kern = {p["name"]: p for p in prof}
+    dom = max(prof, key=lambda p: p["ms"])
+    res = {"value": solves / (ms / 1e3), "unit": "pole-solves/s", "steps": args.split_steps, "poles_per_step": B,
+           "ms_per_step": ms / args.split_steps, "split_slices": S,
+           "dtype": f"f64 in/out; supernode GEMMs as bf16x{S} slices on tcgen05 (exact fp32 / int64 accumulation)",
+           "roofline": roofline_of(dom, sum(p["ms"] for p in prof), peaks, S),
+           "gemm_rate": gemm_rate(kern),
+           "kernels_per_step": per_step(prof, 1)}
+    res["roofline"]["traffic"] = traffic_of(args.workload, dom, S)
+    px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, heavy[0], heavy[1], 0,
+                       o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
+    got = o.cpu().numpy()
+    if ref_dm is not None:
+        scale = [float(np.max(np.abs(ref_dm[k]))) for k in range(3)]
+        dev_ = [float(np.max(np.abs(ref_dm[k] - got[k]))) for k in range(3)]
+        res["vs_fp64_path"] = {"batch": f"poles {heavy[0]}..{heavy[1] - 1}",
+                               "max_abs": dict(zip(("dm", "edm", "fdm"), dev_)),
+                               "rel_to_max_entry": {k: d / sc for k, d, sc in zip(("dm", "edm", "fdm"), dev_, scale)}}
+    if eig is not None:
+        res["oracle_error"] = oracle_error(s, mu, dE, got, range(*heavy), args.oracle_cols, eig)
+    full = px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, 0, P, 0,
+                              o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), stream, want_info=True)
+    res["trace_dm_s_all_poles"] = full["trace_dm_s"]
+    if eig is not None:
+        from oracle import dense, poles
+        tr = dense.trace_eig(eig[0], poles.pole_table(s.beta, dE, P, mu), range(P))
+        res["trace_error_all_poles"] = abs(full["trace_dm_s"] - tr[0])
+    if args.split_latency_calls > 0:
+        res["dm_latency"] = dm_latency(px, plan, s, mu, dE, args.split_latency_calls)
+    px.pexsi_plan_destroy(plan)
+    return res
 
 
 # ------------------------------------------------------------------ serving trace
@@ -499,16 +630,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fluid")
-    ap.add_argument("--poles-per-step", type=int, default=20,
-                    help="poles per batch (20 x 7.3 GB of fronts on fluid512 fits 60%% of HBM)")
+    ap.add_argument("--poles-per-step", type=int, default=0,
+                    help="poles per batch (0: 4 for the FP64 path, 20 for a split-precision run)")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--oracle-cols", type=int, default=64)
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="instrumented steps after the timed region (per-kernel CUDA-event timings)")
+    ap.add_argument("--latency-calls", type=int, default=1,
+                    help="full P-pole pexsi_dm host calls timed for the DM latency of the main path (0 = skip)")
+    ap.add_argument("--oracle-cols", type=int, default=8,
+                    help="sampled columns of the oracle check of the DM-carrying poles (0 = skip)")
+    ap.add_argument("--cpu-cols", type=int, default=64, help="columns solved by the timed CPU oracle sample")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--split", type=int, default=6,
-                    help="bf16 slices of the split-precision supernode GEMMs (0 = FP64 everywhere)")
-    ap.add_argument("--fp64-steps", type=int, default=2,
-                    help="timed steps of the plain FP64 path reported beside a split-precision run (0 = skip)")
+    ap.add_argument("--split", type=int, default=0,
+                    help="bf16 slices of the split-precision supernode GEMMs of the main path (0 = FP64)")
+    ap.add_argument("--split-compare", type=int, default=6,
+                    help="slices of the split-precision path reported beside the FP64 main path (0 = skip)")
+    ap.add_argument("--split-steps", type=int, default=6, help="timed 20-pole steps of the split-precision path")
+    ap.add_argument("--split-latency-calls", type=int, default=5,
+                    help="full P-pole host calls timed for the split path's DM latency")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving trace (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=3.0, help="Poisson arrival rate of the serving trace")
     args = ap.parse_args()

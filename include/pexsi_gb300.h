@@ -51,6 +51,8 @@ enum {
   PEXSI_ERR_BREAKDOWN = -5,     /* zero / non-finite pivot in a diagonal block */
   PEXSI_ERR_INTERNAL = -6,      /* violated internal invariant (a bug)         */
   PEXSI_ERR_CANCELLED = -7,     /* server request cancelled before completion  */
+  PEXSI_ERR_TIMEOUT = -8,       /* a bounded device-side wait ran out (split-
+                                   precision kernels; pexsi_opts.wait_ns)      */
   PEXSI_PENDING = 1             /* server request not finished yet (poll)      */
 };
 
@@ -77,6 +79,22 @@ typedef struct pexsi_opts {
                               diagonal-block inverses and the pole sum stay FP64.
                               Requires panel = 64; other values are INVALID_ARG. */
   int64_t hbm_budget;      /* bytes of device workspace the batch may use, 0 = auto  */
+  int64_t wait_ns;         /* bound, in ns of wall time, of every wait of one role of
+                              a split-precision kernel on another (an mbarrier phase
+                              of a copy, of the MMAs, of a TMEM drain); 0 = 1 s. A
+                              wait that runs out stops the launch cleanly (every
+                              role returns, TMEM is freed, later launches of the
+                              call return at once) and the call returns
+                              PEXSI_ERR_TIMEOUT. No other kernel waits.           */
+  int32_t inject;          /* fault injection for tests of the error paths, 0 = off
+                              (default). 1: CTA 0 of every short-K split GEMM launch
+                              issues no operand copy, so that its MMA issuer's wait
+                              runs out after wait_ns (PEXSI_ERR_TIMEOUT; split_slices
+                              > 0 only). 2: a breakdown of front 0 is recorded from
+                              the host after the first pole batch of every call with
+                              accumulate = 0 (PEXSI_ERR_BREAKDOWN at the end of the
+                              chain).                                             */
+  int32_t reserved1;
 } pexsi_opts;
 
 /* Symbolic statistics of a plan. Flop counts are algorithmic real flops of
@@ -155,7 +173,8 @@ int pexsi_pole_table(double beta, double delta_e, int32_t n_poles, double mu,
  * delta_e) -- Eq. gammapole and Eq. gammaF. Host buffers of nnz doubles; any
  * output may be NULL. S == NULL means S = I (H's diagonal positions). The
  * call is synchronous. On error the outputs are undefined.
- * Errors: INVALID_ARG, NOMEM, CUDA, BREAKDOWN (info->breakdown_front). */
+ * Errors: INVALID_ARG, NOMEM, CUDA, BREAKDOWN (info->breakdown_front),
+ * TIMEOUT (split-precision path only: a bounded device-side wait ran out). */
 int pexsi_dm(pexsi_plan* plan, const double* H, const double* S, double mu, double beta,
              int32_t n_poles, double delta_e, double* dm, double* edm, double* fdm,
              pexsi_dm_info* info);
@@ -173,7 +192,13 @@ int pexsi_dm_poles(pexsi_plan* plan, const double* H, const double* S, double mu
  * doubles (dS may be NULL for S = I; outputs may be NULL). accumulate = 0
  * overwrites the outputs, 1 adds this subrange's contribution to them. The
  * work is enqueued on `stream`; the call returns after enqueueing unless
- * info != NULL, in which case it synchronises `stream` to fill info. */
+ * info != NULL, in which case it synchronises `stream` to fill info.
+ * Status of a chain of calls: a call with accumulate = 0 clears the plan's
+ * breakdown / timeout status, calls with accumulate = 1 keep it, and the
+ * first call with info != NULL returns the status of every batch since the
+ * chain began (BREAKDOWN, TIMEOUT). A chain that is never read with info
+ * reports nothing; pass info on its last call. Inertia calls keep status
+ * words of their own and do not disturb a chain. */
 int pexsi_dm_device(pexsi_plan* plan, const double* dH, const double* dS, double mu,
                     double beta, int32_t n_poles, double delta_e, int32_t pole_begin,
                     int32_t pole_end, int32_t accumulate, double* d_dm, double* d_edm,

@@ -24,9 +24,11 @@ c_double_p = ctypes.POINTER(ctypes.c_double)
 
 ERR_NAMES = {0: "PEXSI_OK", -1: "PEXSI_ERR_INVALID_ARG", -2: "PEXSI_ERR_NOT_SYMMETRIC", -3: "PEXSI_ERR_NOMEM",
              -4: "PEXSI_ERR_CUDA", -5: "PEXSI_ERR_BREAKDOWN", -6: "PEXSI_ERR_INTERNAL", -7: "PEXSI_ERR_CANCELLED",
-             1: "PEXSI_PENDING"}
+             -8: "PEXSI_ERR_TIMEOUT", 1: "PEXSI_PENDING"}
 PEXSI_PENDING = 1
 PEXSI_ERR_CANCELLED = -7
+PEXSI_ERR_TIMEOUT = -8
+PEXSI_ERR_BREAKDOWN = -5
 
 
 class PexsiError(RuntimeError):
@@ -38,7 +40,8 @@ class PexsiError(RuntimeError):
 class pexsi_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("panel", ctypes.c_int32), ("leaf_cols", ctypes.c_int32),
                 ("amalgamate", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("split_slices", ctypes.c_int32),
-                ("hbm_budget", ctypes.c_int64)]
+                ("hbm_budget", ctypes.c_int64), ("wait_ns", ctypes.c_int64), ("inject", ctypes.c_int32),
+                ("reserved1", ctypes.c_int32)]
 
 
 class pexsi_plan_stats(ctypes.Structure):

@@ -80,6 +80,20 @@ int64_t bytes_fixed(const pexsi_plan* p) {
 }
 
 namespace {
+const int kBig = INT_MAX;
+const unsigned long long kInfBits = 0x7FF0000000000000ull;
+}  // namespace
+
+// Clears the status words of one chain (0 = poles, 1 = inertia shifts): the
+// first breakdown front, the smallest pivot ratio and the failure flag of
+// the split-precision waits.
+void reset_status(Workspace& ws, int which) {
+  ck(cudaMemcpyAsync(ws.brk + which, &kBig, sizeof(int), cudaMemcpyHostToDevice, ws.stream), "status");
+  ck(cudaMemcpyAsync(ws.minpiv + which, &kInfBits, sizeof(kInfBits), cudaMemcpyHostToDevice, ws.stream), "status");
+  if (ws.ozfail) ck(cudaMemsetAsync(ws.ozfail + which, 0, sizeof(int), ws.stream), "status");
+}
+
+namespace {
 template <typename T>
 void wsalloc(T** ptr, size_t bytes, Workspace& ws, const char* what) {
   if (ws.async) ck(cudaMallocAsync(reinterpret_cast<void**>(ptr), bytes, ws.stream), what);
@@ -100,8 +114,9 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
   wsalloc(&ws.H, sizeof(double) * nnz, ws, "alloc(H)");
   wsalloc(&ws.S, sizeof(double) * nnz, ws, "alloc(S)");
   wsalloc(&ws.out, sizeof(double) * nnz * 4, ws, "alloc(outputs)");
-  wsalloc(&ws.brk, sizeof(int), ws, "alloc(status)");
-  wsalloc(&ws.minpiv, sizeof(unsigned long long), ws, "alloc(status)");
+  // status words: [0] the pole chain (DM calls), [1] the inertia shifts
+  wsalloc(&ws.brk, 2 * sizeof(int), ws, "alloc(status)");
+  wsalloc(&ws.minpiv, 2 * sizeof(unsigned long long), ws, "alloc(status)");
   wsalloc(&ws.neg, sizeof(int) * kMaxBatch, ws, "alloc(status)");
   wsalloc(&ws.partials, sizeof(double) * 4 * p->trace_blocks, ws, "alloc(trace)");
   wsalloc(&ws.trace3, sizeof(double) * 4, ws, "alloc(trace)");
@@ -111,11 +126,13 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
     wsalloc(&ws.ozB, size_t(std::max(p->ozB_stride, 2 * p->ozB_stride_r)) * batch, ws, "alloc(split B)");
     wsalloc(&ws.exA, sizeof(int) * size_t(p->exA_stride) * 2 * batch, ws, "alloc(split exponents)");
     wsalloc(&ws.exB, sizeof(int) * size_t(p->exB_stride) * 2 * batch, ws, "alloc(split exponents)");
-    wsalloc(&ws.ozfail, sizeof(int), ws, "alloc(status)");
+    wsalloc(&ws.ozfail, 2 * sizeof(int), ws, "alloc(status)");
     wsalloc(&ws.ymax, sizeof(uint32_t) * size_t(p->ymax_stride) * batch, ws, "alloc(split row maxima)");
   }
   if (!ws.ev0) ck(cudaEventCreate(&ws.ev0), "cudaEventCreate");
   if (!ws.ev1) ck(cudaEventCreate(&ws.ev1), "cudaEventCreate");
+  reset_status(ws, 0);
+  reset_status(ws, 1);
 }
 
 void workspace_free(Workspace& ws) {
@@ -218,8 +235,9 @@ Profiler g_off;  // a profiler that is never switched on
 OzScratch split_scratch(const pexsi_plan* p, Workspace& ws, bool real) {
   return OzScratch{ws.ozA, real ? p->d_ozA_off_r : p->d_ozA_off, real ? p->ozA_stride_r : p->ozA_stride,
                    ws.ozB, real ? p->d_ozB_off_r : p->d_ozB_off, real ? p->ozB_stride_r : p->ozB_stride,
-                   ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride, ws.ozfail,
-                   ws.ymax, p->d_ymax_off, p->ymax_stride};
+                   ws.exA, p->d_exA_off, p->exA_stride, ws.exB, p->d_exB_off, p->exB_stride,
+                   ws.ozfail + (real ? 1 : 0), ws.ymax, p->d_ymax_off, p->ymax_stride, p->wait_ns,
+                   p->opts.inject == 1 ? 1 : 0};
 }
 
 // Factor the batch in F (assembled), leaves to root.
@@ -227,7 +245,8 @@ template <typename T>
 void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& sh, bool count, Profiler& pf) {
   cudaStream_t st = ws.stream;
   DevFronts fr = p->fronts();
-  DevStatus status{ws.brk, ws.minpiv, ws.neg};
+  // the inertia shifts (count) keep their own status words
+  DevStatus status{ws.brk + (count ? 1 : 0), ws.minpiv + (count ? 1 : 0), ws.neg};
   const int b = p->b;
   const double es = double(sizeof(T)), fl = sizeof(T) == 16 ? 8.0 : 2.0, nb = sh.nb;
   for (size_t L = 0; L < p->levels.size(); ++L) {
@@ -409,21 +428,17 @@ BatchShifts make_shifts(const std::vector<std::complex<double>>& z, const std::v
   return sh;
 }
 
-const int kBig = INT_MAX;
-const unsigned long long kInfBits = 0x7FF0000000000000ull;
-
-void reset_status(Workspace& ws) {
-  ck(cudaMemcpyAsync(ws.brk, &kBig, sizeof(int), cudaMemcpyHostToDevice, ws.stream), "status");
-  ck(cudaMemcpyAsync(ws.minpiv, &kInfBits, sizeof(kInfBits), cudaMemcpyHostToDevice, ws.stream), "status");
-  if (ws.ozfail) ck(cudaMemsetAsync(ws.ozfail, 0, sizeof(int), ws.stream), "status");
-}
-
-// A bounded wait inside the split-precision GEMM ran out (never expected).
-int split_failed(Workspace& ws) {
+// A bounded wait inside the split-precision kernels ran out: the site it
+// gave up at, read from the status word of the chain (0 = poles, 1 = inertia).
+int split_failed(Workspace& ws, int which, std::string* err, const char* what) {
   if (!ws.ozfail) return 0;
   int f = 0;
-  ck(cudaMemcpyAsync(&f, ws.ozfail, sizeof(int), cudaMemcpyDeviceToHost, ws.stream), "status");
+  ck(cudaMemcpyAsync(&f, ws.ozfail + which, sizeof(int), cudaMemcpyDeviceToHost, ws.stream), "status");
   ck(cudaStreamSynchronize(ws.stream), "sync");
+  if (f && err)
+    *err = std::string(what) + ": a bounded device-side wait ran out (mode " + std::to_string((f >> 28) & 3) +
+           ", wait " + std::to_string(((f >> 20) & 255) & 15) + ", K tile " + std::to_string(((f >> 20) & 255) >> 4) +
+           ", CTA " + std::to_string((f - 1) & ((1 << 20) - 1)) + ")";
   return f;
 }
 
@@ -453,12 +468,22 @@ int dm_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* d
   cudaStream_t st = ws.stream;
   double* d_ddm = ws.out + 3 * p->sym.nnz;
   if (info) ck(cudaEventRecord(ws.ev0, st), "event");
-  reset_status(ws);
+  // A call with accumulate = 0 starts a chain: its status words are cleared.
+  // Calls that accumulate keep them, so that the call which finally reads
+  // them (info != NULL) reports a breakdown or a timed-out wait of any batch
+  // of the chain.
+  if (!accumulate) reset_status(ws, 0);
   bool first = true;
   for (int b0 = begin; b0 < end; b0 += ws.batch) {
     int nb = std::min(ws.batch, end - b0);
     BatchShifts sh = make_shifts(z, &wr, &we, &wf, b0, nb, &wd);
     run_complex_batch(p, ws, dH, S, sh, pf);
+    if (first && !accumulate && p->opts.inject == 2) {
+      // fault injection (testing the status path): a breakdown of front 0 in
+      // the chain's first batch, recorded from the host
+      static const int kFront0 = 0;
+      ck(cudaMemcpyAsync(ws.brk, &kFront0, sizeof(int), cudaMemcpyHostToDevice, st), "inject");
+    }
     int overwrite = (first && !accumulate) ? 1 : 0;
     cudaEvent_t a = pf.begin(st);
     launch_pole_sum(ws.Y, p->sym.front_elems, p->d_entry_pos, p->sym.nnz, sh, overwrite, d_dm, d_edm, d_fdm, d_ddm,
@@ -493,15 +518,10 @@ int dm_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* d
   info->gemm_flops = (p->flops.factor_gemm + p->flops.selinv_gemm) * (end - begin);
   info->n_poles = end - begin;
   info->breakdown_front = brk == INT_MAX ? -1 : brk;
+  if (split_failed(ws, 0, err, "split-precision GEMM")) return PEXSI_ERR_TIMEOUT;
   if (brk != INT_MAX) {
     *err = "zero or tiny pivot in front " + std::to_string(brk);
     return PEXSI_ERR_BREAKDOWN;
-  }
-  if (int f = split_failed(ws)) {
-    *err = "split-precision GEMM: a bounded wait ran out (mode " + std::to_string((f >> 30) & 1) + ", wait " +
-           std::to_string(((f >> 20) & 1023) & 15) + ", K tile " + std::to_string(((f >> 20) & 1023) >> 4) +
-           ", tile " + std::to_string((f - 1) & ((1 << 20) - 1)) + ")";
-    return PEXSI_ERR_INTERNAL;
   }
   return PEXSI_OK;
 }
@@ -521,7 +541,7 @@ int inertia_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const doub
   for (int b0 = 0; b0 < n_shifts; b0 += cap) {
     int nb = std::min(cap, n_shifts - b0);
     BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, b0, nb);
-    reset_status(ws);
+    reset_status(ws, 1);
     ck(cudaMemsetAsync(ws.neg, 0, sizeof(int) * kMaxBatch, st), "status");
     ck(cudaMemsetAsync(F, 0, sizeof(double) * size_t(pool) * nb, st), "memset(F)");
     cudaEvent_t a = pf.begin(st);
@@ -531,15 +551,11 @@ int inertia_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const doub
     int neg[kMaxBatch];
     int brk = INT_MAX;
     ck(cudaMemcpyAsync(neg, ws.neg, sizeof(int) * nb, cudaMemcpyDeviceToHost, st), "D2H(counts)");
-    ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    ck(cudaMemcpyAsync(&brk, ws.brk + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
     ck(cudaStreamSynchronize(st), "sync");
     for (int t = 0; t < nb; ++t) counts[b0 + t] = neg[t];
     brk_all = std::min(brk_all, brk);
-    if (int f = split_failed(ws)) {
-      *err = "split-precision GEMM (inertia): a bounded wait ran out (wait " + std::to_string(((f >> 20) & 1023) & 15) +
-             ", tile " + std::to_string((f - 1) & ((1 << 20) - 1)) + ")";
-      return PEXSI_ERR_INTERNAL;
-    }
+    if (split_failed(ws, 1, err, "split-precision GEMM (inertia)")) return PEXSI_ERR_TIMEOUT;
   }
   if (brk_all != INT_MAX) {
     *err = "zero or tiny pivot in front " + std::to_string(brk_all);
@@ -552,22 +568,17 @@ int selinv_one(const pexsi_plan* p, Workspace& ws, const double* dH, const doubl
                double2* d_ainv, std::string* err) {
   std::vector<std::complex<double>> z{{z_re, z_im}};
   BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, 0, 1);
-  reset_status(ws);
+  reset_status(ws, 0);
   run_complex_batch(p, ws, dH, dS ? dS : p->d_ident, sh, g_off);
   launch_extract(ws.Y, p->d_entry_pos, p->sym.nnz, d_ainv, ws.stream);
   ck(cudaGetLastError(), "extract");
   int brk = INT_MAX;
   ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, ws.stream), "status");
   ck(cudaStreamSynchronize(ws.stream), "sync");
+  if (split_failed(ws, 0, err, "split-precision GEMM")) return PEXSI_ERR_TIMEOUT;
   if (brk != INT_MAX) {
     *err = "zero or tiny pivot in front " + std::to_string(brk);
     return PEXSI_ERR_BREAKDOWN;
-  }
-  if (int f = split_failed(ws)) {
-    *err = "split-precision GEMM: a bounded wait ran out (mode " + std::to_string((f >> 30) & 1) + ", wait " +
-           std::to_string(((f >> 20) & 1023) & 15) + ", K tile " + std::to_string(((f >> 20) & 1023) >> 4) +
-           ", tile " + std::to_string((f - 1) & ((1 << 20) - 1)) + ")";
-    return PEXSI_ERR_INTERNAL;
   }
   return PEXSI_OK;
 }
@@ -820,6 +831,7 @@ const char* pexsi_strerror(int code) {
     case PEXSI_ERR_BREAKDOWN: return "factorisation breakdown (zero or tiny pivot)";
     case PEXSI_ERR_INTERNAL: return "internal error";
     case PEXSI_ERR_CANCELLED: return "request cancelled";
+    case PEXSI_ERR_TIMEOUT: return "a bounded device-side wait ran out";
     case PEXSI_PENDING: return "request pending";
     default: return "unknown error";
   }
@@ -863,6 +875,11 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
       delete p;
       return PEXSI_ERR_INVALID_ARG;
     }
+    if (p->opts.wait_ns < 0 || p->opts.inject < 0 || p->opts.inject > 2) {
+      delete p;
+      return PEXSI_ERR_INVALID_ARG;
+    }
+    p->wait_ns = p->opts.wait_ns > 0 ? uint64_t(p->opts.wait_ns) : 1000000000ull;
     p->oz_slices = p->opts.split_slices;
     p->b = p->opts.panel;
     std::string err;

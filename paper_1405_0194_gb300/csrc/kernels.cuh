@@ -63,6 +63,8 @@ struct OzScratch {
   uint32_t* ymax;
   const int64_t* ymax_off;  // first row of each front
   int64_t ymax_stride;      // rows per pole
+  uint64_t wait_ns;         // bound of every wait on another role (wall time)
+  int stall;                // testing: CTA 0 of the short-K GEMM issues no copy
 };
 
 // ---- launchers (T = double for real inertia, double2 for complex poles) ----

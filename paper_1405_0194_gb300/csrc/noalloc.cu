@@ -100,8 +100,17 @@ extern "C" int pexsi_trace_noalloc(const double* d_dm, const double* d_edm, cons
   int64_t chunk = (nnz + nblocks - 1) / nblocks;
   if (chunk < 1) chunk = 1;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  (void)cudaGetLastError();  // drop an earlier call's recorded error; the check below is for these launches
-  k_trace_partial_static<<<int(nblocks), 256, 0, st>>>(d_dm, d_edm, d_fdm, d_S, nnz, chunk, scratch);
-  k_trace_final_static<<<1, 32, 0, st>>>(scratch, int(nblocks), d_out3);
-  return cudaGetLastError() == cudaSuccess ? PEXSI_OK : PEXSI_ERR_CUDA;
+  // The launches' own return codes are checked, so an error that another
+  // component left pending in the runtime is neither cleared nor taken for
+  // one of these launches.
+  int nb = int(nblocks);
+  void* args1[] = {&d_dm, &d_edm, &d_fdm, &d_S, &nnz, &chunk, &scratch};
+  if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_trace_partial_static), dim3(nb), dim3(256), args1, 0, st) !=
+      cudaSuccess)
+    return PEXSI_ERR_CUDA;
+  void* args2[] = {&scratch, &nb, &d_out3};
+  if (cudaLaunchKernel(reinterpret_cast<const void*>(&k_trace_final_static), dim3(1), dim3(32), args2, 0, st) !=
+      cudaSuccess)
+    return PEXSI_ERR_CUDA;
+  return PEXSI_OK;
 }

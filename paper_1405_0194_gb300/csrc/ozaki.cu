@@ -117,20 +117,22 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait (kWaitNs of wall time) for the completion of the barrier
-// phase of the given parity; gives up early once another role has recorded a
-// failure.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, const volatile int* fail) {
+// Bounded wait (budget_ns of wall time, the plan's wait bound) for the
+// completion of the barrier phase of the given parity; gives up early once
+// another role has recorded a failure.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, const volatile int* fail, uint64_t budget_ns) {
   if (bar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (bar_try(bar, parity)) return true;
     if (*fail) return false;
-    if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    if ((it & 255u) == 0 && global_ns() - t0 > budget_ns) return false;
   }
 }
 
-// Bounded wait that ignores failures (draining own copies / MMAs in flight).
+// Bounded wait that ignores failures (draining own copies / MMAs in flight):
+// always the full second, whatever the plan's wait bound, since what it
+// waits for was issued and completes on its own.
 __device__ __forceinline__ bool bar_wait_all(uint32_t bar, uint32_t parity) {
   if (bar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
@@ -664,9 +666,11 @@ __global__ void __launch_bounds__(256) k_oz_slice_real(double* __restrict__ F, D
   }
 }
 
-// Where a wait ran out: site (1..8) + 16 * (K tile mod 64).
+// Where a wait ran out: site (1..8) + 16 * (K tile mod 16), below 256; the
+// launch reports 1 + (mode << 28) + (this << 20) + CTA index, mode 1-3 for the
+// short-K GEMM (its MODE), 0 for the Takahashi / Y[P,P] kernel.
 __device__ __forceinline__ void record_fail(int* s_fail, int site, int kt) {
-  atomicCAS(s_fail, 0, site + 16 * (kt & 63));
+  atomicCAS(s_fail, 0, site + 16 * (kt & 15));
 }
 
 // ---------------------------------------------------------------- GEMM (short K)
@@ -746,7 +750,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   constexpr int SA = CPLX ? kSliceA : 2 * kBlk;     // bytes of one slice of A (one K tile)
   constexpr int SB = CPLX ? kSliceB : kBlk;         // bytes of one slice of B (one K tile: Br, Bi; or Br)
   constexpr bool SCHUR = MODE != 2;                  // read-modify-write of the trailing block
-  if (*static_cast<volatile int*>(oz.fail)) return;  // an earlier CTA gave up: the result is void anyway
+  // An earlier CTA gave up (the result is void anyway): the whole CTA leaves
+  // together, on one read of the flag, before any barrier or TMEM is set up.
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *static_cast<volatile int*>(oz.fail);
+  __syncthreads();
+  if (s_skip) return;
   uint8_t* sA = osm;                                 // kSlotsA x one slice of A (Ar, Ai, -Ar; or Ar)
   uint8_t* sB = osm + kSlotsA * kSliceA;             // kSlotsB x S slices of B (Br, Bi; or Br)
   int* s_pref = reinterpret_cast<int*>(sB + kSlotsB * 6 * kSliceB);  // tiles before front f
@@ -816,7 +825,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
   if (warp == kEpiWarps) {
     if (lane == 0) {  // ---- producer
       int na = 0, nbf = 0;
-      bool ok = true;
+      // fault injection (testing the timeout path): CTA 0 issues no copy, so
+      // the MMA issuer's first wait runs out and the launch reports it
+      bool ok = !(oz.stall && blockIdx.x == 0);
       for (int it = blockIdx.x; it < items && ok && !*fail; it += gridDim.x) {
         int pole, mt, nt;
         PanelDims d;
@@ -826,7 +837,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
         const uint8_t* gB = oz.B + int64_t(pole) * oz.B_stride + oz.B_off[d.f] + int64_t(nt) * nkt * S * SB;
         for (int kt = 0; kt < nkt && ok; ++kt) {
           const int sb = nbf % kSlotsB, ub = nbf / kSlotsB;
-          if (ub > 0 && !bar_wait(smem_u32(&empty_b[sb]), (ub - 1) & 1, fail)) {
+          if (ub > 0 && !bar_wait(smem_u32(&empty_b[sb]), (ub - 1) & 1, fail, oz.wait_ns)) {
             record_fail(&s_fail, 1, kt);
             ok = false;
             break;
@@ -837,7 +848,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
           ++nbf;
           for (int s = 0; s < S; ++s) {
             const int sa = na % kSlotsA, ua = na / kSlotsA;
-            if (ua > 0 && !bar_wait(smem_u32(&empty_a[sa]), (ua - 1) & 1, fail)) {
+            if (ua > 0 && !bar_wait(smem_u32(&empty_a[sa]), (ua - 1) & 1, fail, oz.wait_ns)) {
               record_fail(&s_fail, 2, kt);
               ok = false;
               break;
@@ -868,14 +879,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
           PanelDims d;
           if (!decode(it, pole, d, mt, nt)) continue;
           const int nkt = ceil_div(d.bb, kOzK);
-          if (ti > 0 && !bar_wait(smem_u32(&acc_empty), (ti - 1) & 1, fail)) {  // previous tile drained
+          if (ti > 0 && !bar_wait(smem_u32(&acc_empty), (ti - 1) & 1, fail, oz.wait_ns)) {  // previous tile drained
             record_fail(&s_fail, 4, 0);
             ok = false;
             break;
           }
           for (int kt = 0; kt < nkt && ok; ++kt) {
             const int sb = nbf % kSlotsB;
-            if (!bar_wait(smem_u32(&full_b[sb]), (nbf / kSlotsB) & 1, fail)) {
+            if (!bar_wait(smem_u32(&full_b[sb]), (nbf / kSlotsB) & 1, fail, oz.wait_ns)) {
               record_fail(&s_fail, 5, kt);
               ok = false;
               break;
@@ -885,7 +896,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
 #pragma unroll
             for (int s = 1; s <= SS; ++s) {
               const int sa = na % kSlotsA;
-              if (!bar_wait(smem_u32(&full_a[sa]), (na / kSlotsA) & 1, fail)) {
+              if (!bar_wait(smem_u32(&full_a[sa]), (na / kSlotsA) & 1, fail, oz.wait_ns)) {
                 record_fail(&s_fail, 6, kt);
                 ok = false;
                 break;
@@ -936,7 +947,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
       const int eb_lane = jl < jmax ? oz.exB[int64_t(pole) * oz.exB_stride + oz.exB_off[d.f] + jl] : 0;
       const int ea = row_in ? oz.exA[int64_t(pole) * oz.exA_stride + oz.exA_off[d.f] + i] : 0;
       bool ok = true;
-      if (lane == 0) ok = bar_wait(smem_u32(&acc_full), ti & 1, fail);
+      if (lane == 0) ok = bar_wait(smem_u32(&acc_full), ti & 1, fail, oz.wait_ns);
       ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
       if (!ok) {
         if (lane == 0) record_fail(&s_fail, 8, ti);
@@ -993,7 +1004,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
 
   __syncthreads();
   if (s_fail && threadIdx.x == 0)  // where the wait gave up: mode, site + 16 * K tile, CTA
-    atomicMax(oz.fail, 1 + (MODE << 28) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
+    atomicMax(oz.fail, 1 + (MODE << 28) + (min(s_fail, 255) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -1141,7 +1152,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
   __shared__ int s_ea[kOzRows], s_eb[kOzRows];
   PanelDims d;
   if (!panel_dims(fr, fronts, blockIdx.y, p0, b, d)) return;
-  if (*static_cast<volatile int*>(oz.fail)) return;
+  // an earlier CTA gave up: leave together, on one read of the flag
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *static_cast<volatile int*>(oz.fail);
+  __syncthreads();
+  if (s_skip) return;
   const int mt = DP ? 0 : int(blockIdx.x);
   if (DP ? int(blockIdx.x) * kFChunk >= ceil_div(d.mp, kFK) : mt >= ceil_div(d.mp, kOzRows)) return;
   const int pole = blockIdx.z;
@@ -1203,13 +1218,13 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         constexpr int SS = decltype(SC)::value;
         for (int kt = 0; kt < nkt; ++kt) {
           const int c = kt / kFChunk, in_chunk = kt % kFChunk;
-          if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail)) {
+          if (in_chunk == 0 && c > 0 && !bar_wait(smem_u32(&acc_empty), (c - 1) & 1, fail, oz.wait_ns)) {
             record_fail(&s_fail, 4, kt);
             break;
           }
           const int slot = kt % kFSlots;
           const uint32_t par = (kt / kFSlots) & 1;
-          if (!bar_wait(smem_u32(&full_a[slot]), par, fail) || (!DP && !bar_wait(smem_u32(&full_b[slot]), par, fail))) {
+          if (!bar_wait(smem_u32(&full_a[slot]), par, fail, oz.wait_ns) || (!DP && !bar_wait(smem_u32(&full_b[slot]), par, fail, oz.wait_ns))) {
             record_fail(&s_fail, 6, kt);
             break;
           }
@@ -1248,7 +1263,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
     bool ok = true;
     auto drain = [&](int ch) -> bool {
       bool got = true;
-      if (lane == 0) got = bar_wait(smem_u32(&acc_full), ch & 1, fail);
+      if (lane == 0) got = bar_wait(smem_u32(&acc_full), ch & 1, fail, oz.wait_ns);
       got = __shfl_sync(0xFFFFFFFFu, got, 0);
       if (!got) {
         if (lane == 0) record_fail(&s_fail, 8, ch * kFChunk);
@@ -1333,7 +1348,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
       const int slot = kt % kFSlots, use = kt / kFSlots;
       bool free_slot = true;
       if (use > 0) {
-        if (lane == 0) free_slot = bar_wait(smem_u32(&empty[slot]), (use - 1) & 1, fail);
+        if (lane == 0) free_slot = bar_wait(smem_u32(&empty[slot]), (use - 1) & 1, fail, oz.wait_ns);
         free_slot = __shfl_sync(0xFFFFFFFFu, free_slot, 0);
       }
       if (!free_slot) {
@@ -1388,7 +1403,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
   __syncthreads();
   if (s_fail) {
     if (threadIdx.x == 0)
-      atomicMax(oz.fail, 1 + (3 << 28) + (min(s_fail, 1023) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
+      atomicMax(oz.fail, 1 + (0 << 28) + (min(s_fail, 255) << 20) + min(int(blockIdx.x), (1 << 20) - 1));
   } else if (DP && warp < kFWorkers) {
     // the range's exact sums: lane row (0-63 real, 64-127 imaginary parts of
     // row p of the product), 64 columns q, as int64 in `part`

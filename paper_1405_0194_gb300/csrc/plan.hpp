@@ -102,6 +102,7 @@ struct pexsi_plan {
   pexsi_opts opts{};
   std::string last_error;
   int b = 64;
+  uint64_t wait_ns = 1000000000ull;  // bound of the device-side waits (opts.wait_ns, 0 = 1 s)
   int64_t* d_front_off = nullptr;
   int32_t *d_s = nullptr, *d_m = nullptr, *d_parent = nullptr, *d_rel = nullptr;
   int64_t* d_rptr = nullptr;

@@ -99,7 +99,9 @@ int execute(Request& r, cudaStream_t st, std::string* err) {
       double* d_edm = r.req.edm ? o_edm : nullptr;
       double* d_fdm = r.req.fdm ? o_fdm : nullptr;
       pexsi_dm_info info;
-      // one device batch at a time so a cancellation takes effect between them
+      // one device batch at a time so a cancellation takes effect between
+      // them; the first batch (accumulate = 0) clears the status words and
+      // the last one (info) reports a breakdown or timed-out wait of any batch
       for (int b0 = 0; b0 < r.req.n_poles && rc == PEXSI_OK; b0 += r.batch) {
         if (r.cancel.load()) { rc = PEXSI_ERR_CANCELLED; break; }
         int b1 = std::min(r.req.n_poles, b0 + r.batch);

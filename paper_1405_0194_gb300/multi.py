@@ -32,24 +32,26 @@ def shard(count: int, world: int, rank: int) -> tuple[int, int]:
     return begin, begin + base + (1 if rank < extra else 0)
 
 
-def dm_allreduce(compute_range: Callable[[int, int, int], None], out, n_poles: int, batch: int, group=None):
+def dm_allreduce(compute_range: Callable[..., None], out, n_poles: int, batch: int, group=None):
     """Pole sum over all ranks of `group`.
 
-    compute_range(begin, end, accumulate) evaluates poles [begin, end) into
-    `out` (a 3 x nnz float64 tensor on this rank's device: DM, EDM, FDM),
-    overwriting it when accumulate == 0 and adding otherwise. Each rank runs
-    its share in batches of at most `batch` poles, then one sum-allreduce
-    leaves the full result in `out` on every rank."""
+    compute_range(begin, end, accumulate, last) evaluates poles [begin, end)
+    into `out` (a 3 x nnz float64 tensor on this rank's device: DM, EDM, FDM),
+    overwriting it when accumulate == 0 and adding otherwise; `last` marks
+    the rank's final batch, where the status of all its batches is checked
+    (a failure raises there, before the collective). Each rank runs its share
+    in batches of at most `batch` poles, then one sum-allreduce leaves the
+    full result in `out` on every rank."""
     import torch.distributed as dist
 
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     begin, end = shard(n_poles, world, rank)
-    first = True
-    for p in range(begin, end, max(1, batch)):
-        compute_range(p, min(end, p + batch), 0 if first else 1)
-        first = False
-    if first:  # no poles on this rank: contribute zeros
+    step = max(1, batch)
+    starts = list(range(begin, end, step))
+    for k, p in enumerate(starts):
+        compute_range(p, min(end, p + step), 0 if k == 0 else 1, k == len(starts) - 1)
+    if not starts:  # no poles on this rank: contribute zeros
         out.zero_()
     dist.all_reduce(out, op=dist.ReduceOp.SUM, group=group)
     return out
@@ -91,9 +93,11 @@ def dm_sharded(plan, dH: int, dS: int, mu: float, beta: float, n_poles: int, del
     collective is ordered after them)."""
     from . import capi
 
-    def compute_range(b: int, e: int, acc: int) -> None:
+    def compute_range(b: int, e: int, acc: int, last: bool) -> None:
+        # the last batch reads the chain's status: a breakdown or a timed-out
+        # wait in any batch of this rank raises PexsiError here
         capi.pexsi_dm_device(plan, dH, dS, mu, beta, n_poles, delta_e, b, e, acc, out[0].data_ptr(),
-                             out[1].data_ptr(), out[2].data_ptr(), stream)
+                             out[1].data_ptr(), out[2].data_ptr(), stream, want_info=last)
 
     return dm_allreduce(compute_range, out, n_poles, batch, group)
 

@@ -55,6 +55,9 @@ def _rank_work(rank, n_poles):
 
     import nao_synth as ns
     from oracle import dense, poles
+    import torch.distributed as dist
+
+    from paper_1405_0194_gb300 import multi
     from paper_1405_0194_gb300.multi import dm_allreduce, inertia_allgather
 
     s = ns.make_chain(natoms=16, seed=3)
@@ -66,7 +69,9 @@ def _rank_work(rank, n_poles):
     out = torch.zeros(3, s.nnz, dtype=torch.float64)
     seen = []
 
-    def compute_range(b, e, acc):
+    def compute_range(b, e, acc, last):
+        # the status of a rank's chain is read on its final batch alone
+        assert last == (e == multi.shard(n_poles, dist.get_world_size(), dist.get_rank())[1])
         seen.extend(range(b, e))
         part = np.zeros((3, s.nnz))
         for l in range(b, e):

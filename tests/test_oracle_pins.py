@@ -270,3 +270,35 @@ def test_electron_count_derivative_closed_form(chain):
     N = lambda m: poles.fermi_dirac(lam - m, s.beta).real.sum()
     h = 1e-6
     assert abs(g.sum() - (N(mu + h) - N(mu - h)) / (2 * h)) < 1e-3 * max(1.0, abs(g.sum()))
+
+
+def test_chemical_potential_single_level_closed_form():
+    """One level at eps0 holding n_e electrons (spin included): the Fermi
+    function gives mu = eps0 - ln(2/n_e - 1)/beta in closed form (Eq.
+    fermidirac, Eq. Nmu). The search converges to it as the pole error
+    falls with P, from a bracket placed off-centre on either side (a
+    bisection that moves the wrong end ends at a bracket edge)."""
+    beta, eps0 = 1000.0, 0.2
+    lam = np.array([eps0])
+    errs = []
+    for ne in (0.5, 1.0, 1.7):
+        exact = eps0 - math.log(2.0 / ne - 1.0) / beta
+        for P in (40, 60, 80):
+            mu = dense.chemical_potential(lam, beta, 1.0, P, ne, -0.5, 0.9)
+            errs.append((ne, P, abs(mu - exact)))
+        assert abs(dense.chemical_potential(lam, beta, 1.0, 80, ne, exact - 0.01, exact + 0.6) - exact) < 1e-11
+        assert abs(dense.chemical_potential(lam, beta, 1.0, 80, ne, exact - 0.6, exact + 0.01) - exact) < 1e-11
+    for ne in (0.5, 1.0, 1.7):
+        e = [err for (n_, P, err) in errs if n_ == ne]
+        assert e[2] < 1e-11 and e[0] >= e[2]
+
+
+def test_chemical_potential_lands_in_a_gap():
+    """Four levels, n_e = 4 (two filled levels with spin): N_P(mu) = 4 holds
+    across the whole gap (-0.1, 0.05) to the pole error, so any root found
+    must lie in the gap and give N_P(mu) = 4."""
+    beta = 1000.0
+    lam = np.array([-0.3, -0.1, 0.05, 0.3])
+    mu = dense.chemical_potential(lam, beta, 1.0, 60, 4.0, -0.29, 0.29)
+    assert -0.1 < mu < 0.05
+    assert abs(dense.electron_count_poles(lam, beta, 1.0, 60, mu) - 4.0) < 1e-9

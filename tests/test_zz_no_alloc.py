@@ -1,5 +1,6 @@
 """The allocation-free trace entry point, checked against the trace that
-pexsi_dm_device reports, on two calls in a row.
+pexsi_dm_device reports and against a host dot product of the same arrays,
+on two calls in a row.
 
 pexsi_trace_noalloc exists for callers that cannot allocate device memory when
 they need Tr[DM S], Tr[EDM S] and Tr[FDM S] -- code capturing a stream into a
@@ -43,8 +44,12 @@ def test_trace_noalloc_matches_dm_call_twice():
                                res[k].data_ptr(), st)
     torch.cuda.synchronize()
     got = res.cpu().numpy()
+    # the same sums on the host, from the same device arrays
+    host = out.cpu().numpy()
+    dot = np.array([np.dot(host[q], s.S) for q in range(3)])
     for k in range(2):
         assert np.max(np.abs(got[k] - ref)) <= TOL_TRACE * max(1.0, np.max(np.abs(ref)))
+        assert np.max(np.abs(got[k] - dot)) <= TOL_TRACE * max(1.0, np.max(np.abs(dot)))
     # one output NULL: its trace is written as 0
     px.pexsi_trace_noalloc(out[0].data_ptr(), 0, 0, dS.data_ptr(), s.nnz, res[0].data_ptr(), st)
     torch.cuda.synchronize()
