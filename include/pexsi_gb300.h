@@ -232,6 +232,47 @@ int pexsi_inertia_device(pexsi_plan* plan, const double* dH, const double* dS,
 int pexsi_plan_get_supernodes(const pexsi_plan* plan, int32_t* first, int64_t* rptr, int32_t* rows,
                               int32_t* parent);
 
+/* ------------------------------------------------------------ complex Hermitian H and S
+ * The variant Sec. IV names for k-point sampling and spin-orbit coupling:
+ * H and S complex Hermitian on the same structurally symmetric pattern. For
+ * the folded shifts z_l (Im z_l > 0) of Eq. polerho, (H - conj(z) S)^{-1} =
+ * ((H - z S)^{-1})^H, so the pole sum becomes
+ *   Gamma = sum_l (w_l G_l - conj(w_l) G_l^H) / (2i),  G_l = (H - z_l S)^{-1},
+ * a complex Hermitian matrix on the pattern (for real H and S it reduces to
+ * Im sum_l w_l G_l of pexsi_dm). A = H - z S is only structurally symmetric,
+ * so the fronts hold an unpivoted (across panels) L D U factorisation and
+ * selected inversion runs the two-sided Takahashi recursion Y[S,P] =
+ * -Y[S,S] L[S,P], Y[P,S] = -U[P,S] Y[S,S], Y[P,P] = D^-1 - U[P,S] Y[S,P]
+ * (Sec. II.B steps 3-4 with U in place of L^T). These calls run the FP64
+ * kernels whatever the plan's split_slices.
+ * Layout: H, S, DM, EDM, FDM and ainv hold nnz complex values as interleaved
+ * (re, im) doubles (2 nnz doubles) in the plan's CSC order; H[(r,c)] must be
+ * conj(H[(c,r)]) (likewise S), S positive definite. S == NULL means S = I.
+ * The traces in info are Tr[X S] = sum_e X_e conj(S_e) (real for Hermitian
+ * X and S). Ownership, status chains and errors as pexsi_dm /
+ * pexsi_dm_device; the first Hermitian call on a plan builds its maps and
+ * staging (4 x 8 nnz + 6 x 16 nnz bytes of device memory, kept with the plan). */
+int pexsi_dm_hermitian(pexsi_plan* plan, const double* H, const double* S, double mu, double beta,
+                       int32_t n_poles, double delta_e, double* dm, double* edm, double* fdm,
+                       pexsi_dm_info* info);
+/* Device form over the pole subrange [pole_begin, pole_end) (device buffers of
+ * 2 nnz doubles each, enqueued on `stream`; accumulate and info as
+ * pexsi_dm_device). */
+int pexsi_dm_hermitian_device(pexsi_plan* plan, const double* dH, const double* dS, double mu,
+                              double beta, int32_t n_poles, double delta_e, int32_t pole_begin,
+                              int32_t pole_end, int32_t accumulate, double* d_dm, double* d_edm,
+                              double* d_fdm, void* stream, pexsi_dm_info* info);
+/* Selected elements G[r, c] of (H - z S)^{-1} at every CSC entry (r, c), for
+ * one complex shift z with Im z != 0 (host buffers, ainv: 2 nnz doubles). */
+int pexsi_selinv_hermitian(pexsi_plan* plan, const double* H, const double* S, double z_re, double z_im,
+                           double* ainv);
+/* Inertia counts of the Hermitian pencil (Sec. II.C): counts[m] = number of
+ * eigenvalues of (H, S) below shifts[m], from the Hermitian Bunch-Kaufman
+ * count of each diagonal block D of the L D L^H fronts of H - shifts[m] S
+ * (Sylvester's law with Haynsworth's inertia additivity). */
+int pexsi_inertia_hermitian(pexsi_plan* plan, const double* H, const double* S, const double* shifts,
+                            int32_t n_shifts, int64_t* counts);
+
 /* ------------------------------------------------------------ chemical potential
  * Sec. II.C: find mu with N_beta(mu) = Tr[DM S] = N_e (Eq. Nmu).
  * 1. Inertia counting: N_inf(eps) = 2 x (# eigenvalues of (H,S) below eps) at

@@ -142,6 +142,17 @@ SIGNATURES = [
                                      c_int64_p]),
     ("pexsi_inertia_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, c_double_p,
                                             ctypes.c_int32, c_int64_p, ctypes.c_void_p]),
+    ("pexsi_dm_hermitian", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int32, ctypes.c_double, c_double_p, c_double_p,
+                                          c_double_p, ctypes.POINTER(pexsi_dm_info)]),
+    ("pexsi_dm_hermitian_device", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                                 ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(pexsi_dm_info)]),
+    ("pexsi_selinv_hermitian", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, ctypes.c_double,
+                                              ctypes.c_double, c_double_p]),
+    ("pexsi_inertia_hermitian", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_double_p, ctypes.c_int32,
+                                               c_int64_p]),
     ("pexsi_trace_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("pexsi_mu_opts_default", ctypes.c_int, [ctypes.POINTER(pexsi_mu_opts)]),
@@ -374,6 +385,67 @@ def pexsi_trace_noalloc(d_dm, d_edm, d_fdm, d_S, nnz, d_out3, stream=0):
     rc = lib().pexsi_trace_noalloc(d_dm or None, d_edm or None, d_fdm or None, d_S or None, int(nnz),
                                    d_out3 or None, stream or None)
     _check(rc)
+
+
+# ---------------------------------------------------------------- complex Hermitian H and S
+def _c128(a, n):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.shape[0] != n:
+        raise ValueError(f"expected {n} values, got {a.shape[0]}")
+    return a
+
+
+def _cptr(a):
+    return None if a is None else a.ctypes.data_as(c_double_p)
+
+
+def pexsi_dm_hermitian(plan, H, S, mu, beta, n_poles, delta_e, want=("dm", "edm", "fdm")):
+    """Complex Hermitian H, S (complex128 arrays of nnz, CSC order; S None =
+    identity). Returns complex (dm, edm, fdm, info); unwanted outputs None."""
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _c128(H, nnz)
+    S = None if S is None else _c128(S, nnz)
+    outs = {k: (np.empty(nnz, dtype=np.complex128) if k in want else None) for k in ("dm", "edm", "fdm")}
+    info = pexsi_dm_info()
+    rc = lib().pexsi_dm_hermitian(plan, _cptr(H), _cptr(S), float(mu), float(beta), int(n_poles), float(delta_e),
+                                  _cptr(outs["dm"]), _cptr(outs["edm"]), _cptr(outs["fdm"]), ctypes.byref(info))
+    _check(rc, plan)
+    return outs["dm"], outs["edm"], outs["fdm"], _as_dict(info)
+
+
+def pexsi_dm_hermitian_device(plan, dH, dS, mu, beta, n_poles, delta_e, pole_begin, pole_end, accumulate, d_dm,
+                              d_edm, d_fdm, stream=0, want_info=False):
+    """Device form (addresses of complex128 device arrays of nnz)."""
+    info = pexsi_dm_info() if want_info else None
+    rc = lib().pexsi_dm_hermitian_device(plan, dH or None, dS or None, float(mu), float(beta), int(n_poles),
+                                         float(delta_e), int(pole_begin), int(pole_end), int(accumulate),
+                                         d_dm or None, d_edm or None, d_fdm or None, stream or None,
+                                         None if info is None else ctypes.byref(info))
+    _check(rc, plan)
+    return None if info is None else _as_dict(info)
+
+
+def pexsi_selinv_hermitian(plan, H, S, z) -> np.ndarray:
+    """G[r, c] of (H - z S)^{-1} at every CSC entry (complex128, nnz)."""
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _c128(H, nnz)
+    S = None if S is None else _c128(S, nnz)
+    out = np.empty(nnz, dtype=np.complex128)
+    rc = lib().pexsi_selinv_hermitian(plan, _cptr(H), _cptr(S), float(np.real(z)), float(np.imag(z)), _cptr(out))
+    _check(rc, plan)
+    return out
+
+
+def pexsi_inertia_hermitian(plan, H, S, shifts) -> np.ndarray:
+    nnz = pexsi_plan_get_stats(plan)["nnz"]
+    H = _c128(H, nnz)
+    S = None if S is None else _c128(S, nnz)
+    shifts = _f64(np.atleast_1d(shifts))
+    counts = np.empty(shifts.shape[0], dtype=np.int64)
+    rc = lib().pexsi_inertia_hermitian(plan, _cptr(H), _cptr(S), _ptr(shifts, ctypes.c_double),
+                                       int(shifts.shape[0]), _ptr(counts, ctypes.c_int64))
+    _check(rc, plan)
+    return counts
 
 
 # ---------------------------------------------------------------- mu search

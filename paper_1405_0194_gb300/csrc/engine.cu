@@ -583,6 +583,209 @@ int selinv_one(const pexsi_plan* p, Workspace& ws, const double* dH, const doubl
   return PEXSI_OK;
 }
 
+// ------------------------------------------------------------------ LDU fronts
+// Complex Hermitian H and S (Sec. IV: k-points, spin-orbit coupling). For
+// Im z > 0, A = H - z S is neither Hermitian nor complex symmetric, but
+// Im x^H A x = -Im z x^H S x < 0 for x != 0, so every leading block and
+// Schur complement is nonsingular and A = L D U (L, U unit triangular per
+// panel, D the panels' diagonal blocks) exists without pivoting across
+// panels. A^{-1} = U^{-1} D^{-1} L^{-1} gives, per panel P with trailing rows S,
+//   Y[S,P] = -Y[S,S] L[S,P],  Y[P,S] = -U[P,S] Y[S,S],  Y[P,P] = D^{-1} - U[P,S] Y[S,P],
+// which for U = L^T is the recursion of the complex-symmetric fronts.
+namespace {
+
+void factor_batch_gen(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, bool count, Profiler& pf) {
+  cudaStream_t st = ws.stream;
+  DevFronts fr = p->fronts();
+  DevStatus status{ws.brk + (count ? 1 : 0), ws.minpiv + (count ? 1 : 0), ws.neg};
+  const int b = p->b;
+  const double nb = sh.nb;
+  for (size_t L = 0; L < p->levels.size(); ++L) {
+    const Level& lv = p->levels[L];
+    const int32_t* dfr = p->d_level_fronts + lv.front_off;
+    for (size_t k = 0; k < lv.ea_off.size(); ++k) {
+      cudaEvent_t a = pf.begin(st);
+      launch_extend_add_full(ws.F, fr, p->d_ea + lv.ea_off[k], lv.ea_count[k], p->d_tile_pref + lv.ea_pref_off_full[k],
+                             lv.ea_total_full[k], sh, st);
+      pf.end(a, P_EXTEND, st, 0.0, nb * lv.ea_elems_full[k] * 16.0);
+    }
+    for (int p0 = 0; p0 < lv.max_s; p0 += b) {
+      PanelGeom g = panel_geom(lv, p0, b);
+      PanelWork w = pf.on ? panel_work(lv, p0, b, 16.0, 8.0) : PanelWork();
+      cudaEvent_t a = pf.begin(st);
+      launch_diag_inv_gen(ws.F, fr, dfr, g.nact, p0, b, sh, status, count, st);
+      pf.end(a, P_DIAG, st, nb * w.diag_fl, nb * w.diag_by);
+      a = pf.begin(st);
+      launch_panel_solve_gen(ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st, false);
+      pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
+      a = pf.begin(st);
+      launch_trailing_full(ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
+      pf.end(a, P_SCHUR, st, 2.0 * nb * w.schur_fl, 2.0 * nb * w.schur_by);
+      a = pf.begin(st);
+      launch_panel_solve_gen(ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st, true);
+      pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
+    }
+  }
+  ck(cudaGetLastError(), "LDU factor kernels");
+}
+
+void selinv_batch_gen(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Profiler& pf) {
+  cudaStream_t st = ws.stream;
+  DevFronts fr = p->fronts();
+  const int b = p->b;
+  const double nb = sh.nb;
+  for (int L = int(p->levels.size()) - 1; L >= 0; --L) {
+    const Level& lv = p->levels[L];
+    const int32_t* dfr = p->d_level_fronts + lv.front_off;
+    cudaEvent_t a = pf.begin(st);
+    launch_gather(ws.Y, fr, dfr, int(lv.fronts.size()), p->d_tile_pref + lv.gather_pref_off, lv.gather_total, sh, st);
+    pf.end(a, P_GATHER, st, 0.0, nb * lv.gather_bytes);
+    const int last = ((lv.max_s - 1) / b) * b;
+    for (int p0 = last; p0 >= 0; p0 -= b) {
+      PanelGeom g = panel_geom(lv, p0, b);
+      PanelWork w = pf.on ? panel_work(lv, p0, b, 16.0, 8.0) : PanelWork();
+      a = pf.begin(st);
+      launch_selinv_offdiag_gen(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
+      pf.end(a, P_OFFDIAG, st, 2.0 * nb * w.off_fl, 2.0 * nb * w.off_by);
+      a = pf.begin(st);
+      launch_selinv_diag_partial_gen(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, g.row_tiles,
+                                     p0, b, sh, st);
+      pf.end(a, P_DPART, st, nb * w.dpart_fl, nb * w.dpart_by);
+      a = pf.begin(st);
+      launch_selinv_diag_reduce_gen(ws.Y, ws.F, ws.part, p->d_part_off, p->part_stride, fr, dfr, g.nact, p0, b, sh, st);
+      pf.end(a, P_DRED, st, 0.0, nb * w.dred_by);
+    }
+  }
+  ck(cudaGetLastError(), "LDU selinv kernels");
+}
+
+void run_gen_batch(const pexsi_plan* p, Workspace& ws, const double2* dH, const double2* dS, const BatchShifts& sh,
+                   bool count, bool selinv, Profiler& pf) {
+  const int64_t pool = p->sym.front_elems;
+  ck(cudaMemsetAsync(ws.F, 0, sizeof(double2) * size_t(pool) * sh.nb, ws.stream), "memset(F)");
+  cudaEvent_t a = pf.begin(ws.stream);
+  launch_assemble_gen(ws.F, dH, dS, p->d_pos_full, p->sym.nnz, pool, sh, ws.stream);
+  pf.end(a, P_ASSEMBLE, ws.stream, 0.0, double(p->sym.nnz) * (32.0 + 16.0 * sh.nb));
+  factor_batch_gen(p, ws, sh, count, pf);
+  if (selinv) selinv_batch_gen(p, ws, sh, pf);
+}
+
+}  // namespace
+
+int dm_range_herm(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double2* dH, const double2* dS, double mu,
+                  double beta, int P, double delta_e, int begin, int end, int accumulate, double2* d_dm,
+                  double2* d_edm, double2* d_fdm, pexsi_dm_info* info, std::string* err) {
+  Profiler& pf = prof ? *prof : g_off;
+  std::vector<std::complex<double>> z, wr, we, wf, wd;
+  int rc = pole_table(beta, delta_e, P, mu, z, wr, we, wf, &wd);
+  if (rc) { *err = "bad pole-expansion parameters"; return rc; }
+  const double2* S = dS ? dS : p->d_ident_c;
+  cudaStream_t st = ws.stream;
+  const int64_t nnz = p->sym.nnz;
+  double2* d_ddm = p->d_hout + 3 * nnz;
+  if (info) ck(cudaEventRecord(ws.ev0, st), "event");
+  if (!accumulate) reset_status(ws, 0);
+  bool first = true;
+  for (int b0 = begin; b0 < end; b0 += ws.batch) {
+    const int nb = std::min(ws.batch, end - b0);
+    BatchShifts sh = make_shifts(z, &wr, &we, &wf, b0, nb, &wd);
+    run_gen_batch(p, ws, dH, S, sh, false, true, pf);
+    if (first && !accumulate && p->opts.inject == 2) {
+      static const int kFront0 = 0;
+      ck(cudaMemcpyAsync(ws.brk, &kFront0, sizeof(int), cudaMemcpyHostToDevice, st), "inject");
+    }
+    const int overwrite = (first && !accumulate) ? 1 : 0;
+    cudaEvent_t a = pf.begin(st);
+    launch_pole_sum_herm(ws.Y, p->sym.front_elems, p->d_pos_full, p->d_pos_t, nnz, sh, overwrite, d_dm, d_edm, d_fdm,
+                         d_ddm, st);
+    pf.end(a, P_POLESUM, st, 4.0 * 12.0 * nb * double(nnz), double(nnz) * (16.0 + 32.0 * nb + 64.0 * (overwrite ? 1 : 2)));
+    first = false;
+  }
+  ck(cudaGetLastError(), "pole sum");
+  if (!info) return PEXSI_OK;
+  std::memset(info, 0, sizeof(*info));
+  // Tr[X S] = sum_e X_e conj(S_e) for Hermitian S: its real part is the
+  // dot product of the interleaved arrays (the imaginary part vanishes)
+  cudaEvent_t a = pf.begin(st);
+  launch_traces(reinterpret_cast<const double*>(d_dm), reinterpret_cast<const double*>(d_edm),
+                reinterpret_cast<const double*>(d_fdm), reinterpret_cast<const double*>(d_ddm),
+                reinterpret_cast<const double*>(S), 2 * nnz, ws.partials, p->trace_blocks, ws.trace3, st);
+  pf.end(a, P_TRACE, st, 8.0 * double(nnz), 80.0 * double(nnz), 2);
+  ck(cudaEventRecord(ws.ev1, st), "event");
+  double tr[4] = {0, 0, 0, 0};
+  int brk = INT_MAX;
+  unsigned long long mp = 0;
+  ck(cudaMemcpyAsync(tr, ws.trace3, sizeof(tr), cudaMemcpyDeviceToHost, st), "trace");
+  ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+  ck(cudaMemcpyAsync(&mp, ws.minpiv, sizeof(mp), cudaMemcpyDeviceToHost, st), "status");
+  ck(cudaStreamSynchronize(st), "sync");
+  float ms = 0;
+  ck(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1), "event");
+  info->trace_dm_s = d_dm ? tr[0] : 0.0;
+  info->trace_edm_s = d_edm ? tr[1] : 0.0;
+  info->trace_fdm_s = d_fdm ? tr[2] : 0.0;
+  info->trace_ddm_s = tr[3];
+  std::memcpy(&info->min_pivot_ratio, &mp, sizeof(double));
+  info->ms_total = ms;
+  info->gemm_flops = (2.0 * p->flops.factor_gemm + 2.0 * p->flops.selinv_gemm) * (end - begin);
+  info->n_poles = end - begin;
+  info->breakdown_front = brk == INT_MAX ? -1 : brk;
+  if (brk != INT_MAX) {
+    *err = "zero or tiny pivot in front " + std::to_string(brk);
+    return PEXSI_ERR_BREAKDOWN;
+  }
+  return PEXSI_OK;
+}
+
+// Inertia counts of the Hermitian pencil: LDU (= L D L^H) fronts of H -
+// sigma S with real sigma and the Hermitian Bunch-Kaufman count of each D
+// block (Sylvester's law, Haynsworth's inertia additivity, Sec. II.C).
+int inertia_range_herm(const pexsi_plan* p, Workspace& ws, const double2* dH, const double2* dS, const double* shifts,
+                       int n_shifts, int64_t* counts, std::string* err) {
+  const double2* S = dS ? dS : p->d_ident_c;
+  cudaStream_t st = ws.stream;
+  std::vector<std::complex<double>> z(n_shifts);
+  for (int t = 0; t < n_shifts; ++t) z[t] = {shifts[t], 0.0};
+  int brk_all = INT_MAX;
+  for (int b0 = 0; b0 < n_shifts; b0 += ws.batch) {
+    const int nb = std::min(ws.batch, n_shifts - b0);
+    BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, b0, nb);
+    reset_status(ws, 1);
+    ck(cudaMemsetAsync(ws.neg, 0, sizeof(int) * kMaxBatch, st), "status");
+    run_gen_batch(p, ws, dH, S, sh, true, false, g_off);
+    int neg[kMaxBatch];
+    int brk = INT_MAX;
+    ck(cudaMemcpyAsync(neg, ws.neg, sizeof(int) * nb, cudaMemcpyDeviceToHost, st), "D2H(counts)");
+    ck(cudaMemcpyAsync(&brk, ws.brk + 1, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    ck(cudaStreamSynchronize(st), "sync");
+    for (int t = 0; t < nb; ++t) counts[b0 + t] = neg[t];
+    brk_all = std::min(brk_all, brk);
+  }
+  if (brk_all != INT_MAX) {
+    *err = "zero or tiny pivot in front " + std::to_string(brk_all);
+    return PEXSI_ERR_BREAKDOWN;
+  }
+  return PEXSI_OK;
+}
+
+int selinv_one_herm(const pexsi_plan* p, Workspace& ws, const double2* dH, const double2* dS, double z_re, double z_im,
+                    double2* d_ainv, std::string* err) {
+  std::vector<std::complex<double>> z{{z_re, z_im}};
+  BatchShifts sh = make_shifts(z, nullptr, nullptr, nullptr, 0, 1);
+  reset_status(ws, 0);
+  run_gen_batch(p, ws, dH, dS ? dS : p->d_ident_c, sh, false, true, g_off);
+  launch_extract(ws.Y, p->d_pos_full, p->sym.nnz, d_ainv, ws.stream);
+  ck(cudaGetLastError(), "extract");
+  int brk = INT_MAX;
+  ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, ws.stream), "status");
+  ck(cudaStreamSynchronize(ws.stream), "sync");
+  if (brk != INT_MAX) {
+    *err = "zero or tiny pivot in front " + std::to_string(brk);
+    return PEXSI_ERR_BREAKDOWN;
+  }
+  return PEXSI_OK;
+}
+
 }  // namespace pexsi
 
 using namespace pexsi;
@@ -593,7 +796,7 @@ void free_plan_device(pexsi_plan* p) {
   void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
                   p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_tile_pref, p->d_part_off, p->d_ident,
                   p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off, p->d_ozA_off_r, p->d_ozB_off_r,
-                  p->d_ymax_off};
+                  p->d_ymax_off, p->d_pos_full, p->d_pos_t, p->d_ident_c, p->d_hH, p->d_hS, p->d_hout};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   cudaStream_t st = p->ws.stream;
@@ -679,6 +882,20 @@ void build_levels(pexsi_plan* p, std::vector<int32_t>& level_fronts, std::vector
       lv.ea_elems.push_back(elems);
       lv.ea_count.push_back(cnt);
       lv.ea_tiles.push_back(tiles);
+      // whole-square tiles of the same children (LDU fronts)
+      lv.ea_pref_off_full.push_back(int64_t(tile_pref.size()));
+      tile_pref.push_back(0);
+      int64_t total_full = 0;
+      double elems_full = 0;
+      for (int32_t K : fr) {
+        if (k >= kids[K].size()) continue;
+        int32_t r = S.r(kids[K][k]), T = (r + 31) / 32;
+        total_full += int64_t(T) * T;
+        tile_pref.push_back(int32_t(total_full));
+        elems_full += 3.0 * double(r) * r;
+      }
+      lv.ea_total_full.push_back(total_full);
+      lv.ea_elems_full.push_back(elems_full);
     }
   }
   if (p->part_stride == 0) p->part_stride = int64_t(b) * b;
@@ -748,6 +965,29 @@ int ensure_workspace(pexsi_plan* p) {
 }  // namespace
 
 int pexsi::plan_workspace(pexsi_plan* p) { return ensure_workspace(p); }
+
+// Maps and staging of the Hermitian variant, made on its first call: the
+// front position of every CSC entry (its own triangle) and of its transpose,
+// a complex identity for S = I, and complex staging for the host calls.
+int pexsi::hermitian_prepare(pexsi_plan* p) {
+  if (p->d_pos_full) return PEXSI_OK;
+  const Symbolic& S = p->sym;
+  const size_t nnz = size_t(S.nnz);
+  std::vector<int64_t> full(nnz), tr(nnz);
+  for (size_t e = 0; e < nnz; ++e) {
+    full[e] = S.entry_lower[e] ? S.entry_pos[e] : S.entry_pos_up[e];
+    tr[e] = S.entry_lower[e] ? S.entry_pos_up[e] : S.entry_pos[e];
+  }
+  std::vector<double2> ident(nnz, make_double2(0.0, 0.0));
+  for (int64_t e : p->diag_entries) ident[e].x = 1.0;
+  p->d_pos_full = dev_upload(full);
+  p->d_pos_t = dev_upload(tr);
+  p->d_ident_c = dev_upload(ident);
+  ck(cudaMalloc(&p->d_hH, sizeof(double2) * nnz), "cudaMalloc(hermitian staging)");
+  ck(cudaMalloc(&p->d_hS, sizeof(double2) * nnz), "cudaMalloc(hermitian staging)");
+  ck(cudaMalloc(&p->d_hout, sizeof(double2) * nnz * 4), "cudaMalloc(hermitian staging)");
+  return PEXSI_OK;
+}
 
 namespace {
 
@@ -944,7 +1184,10 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
       std::vector<double> ident(S.nnz, 0.0);  // S = I on the pattern
       for (int64_t j = 0; j < n; ++j)
         for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e)
-          if (rowind[e] == j) ident[e] = 1.0;
+          if (rowind[e] == j) {
+            ident[e] = 1.0;
+            p->diag_entries.push_back(e);
+          }
       p->d_ident = dev_upload(ident);
     }
     ck(cudaStreamCreateWithFlags(&p->ws.stream, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -1124,6 +1367,115 @@ int pexsi_inertia(pexsi_plan* p, const double* H, const double* S, const double*
     return pexsi_inertia_device(p, p->ws.H, S ? p->ws.S : nullptr, shifts, n_shifts, counts, p->ws.stream);
   } catch (const CudaError& ce) {
     return map_cuda(p, ce);
+  }
+}
+
+// ---------------------------------------------------------------- complex Hermitian H and S
+namespace {
+int herm_enter(pexsi_plan* p) {
+  ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
+  int rc = ensure_workspace(p);
+  if (rc) return rc;
+  return hermitian_prepare(p);
+}
+}  // namespace
+
+int pexsi_dm_hermitian_device(pexsi_plan* p, const double* dH, const double* dS, double mu, double beta,
+                              int32_t n_poles, double delta_e, int32_t pole_begin, int32_t pole_end, int32_t accumulate,
+                              double* d_dm, double* d_edm, double* d_fdm, void* stream, pexsi_dm_info* info) {
+  if (p && p->opts.device < 0) return fail(p, PEXSI_ERR_INVALID_ARG, "host-only plan has no device");
+  if (!p || !dH) return fail(p, PEXSI_ERR_INVALID_ARG, "NULL plan or H");
+  if (pole_begin < 0 || pole_end > n_poles || pole_begin >= pole_end)
+    return fail(p, PEXSI_ERR_INVALID_ARG, "bad pole range");
+  try {
+    int rc = herm_enter(p);
+    if (rc) return rc;
+    std::string err;
+    rc = on_stream(p, stream, [&] {
+      return dm_range_herm(p, p->ws, &p->prof, reinterpret_cast<const double2*>(dH),
+                           reinterpret_cast<const double2*>(dS), mu, beta, n_poles, delta_e, pole_begin, pole_end,
+                           accumulate, reinterpret_cast<double2*>(d_dm), reinterpret_cast<double2*>(d_edm),
+                           reinterpret_cast<double2*>(d_fdm), info, &err);
+    });
+    return rc ? fail(p, rc, err) : PEXSI_OK;
+  } catch (const CudaError& ce) {
+    return map_cuda(p, ce);
+  } catch (const std::bad_alloc&) {
+    return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int pexsi_dm_hermitian(pexsi_plan* p, const double* H, const double* S, double mu, double beta, int32_t n_poles,
+                       double delta_e, double* dm, double* edm, double* fdm, pexsi_dm_info* info) {
+  if (p && p->opts.device < 0) return fail(p, PEXSI_ERR_INVALID_ARG, "host-only plan has no device");
+  if (!p || !H) return fail(p, PEXSI_ERR_INVALID_ARG, "NULL plan or H");
+  try {
+    int rc = herm_enter(p);
+    if (rc) return rc;
+    Workspace& ws = p->ws;
+    const size_t nnz = size_t(p->sym.nnz);
+    double2 *o_dm = p->d_hout, *o_edm = p->d_hout + nnz, *o_fdm = p->d_hout + 2 * nnz;
+    ck(cudaMemcpyAsync(p->d_hH, H, sizeof(double2) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(H)");
+    if (S) ck(cudaMemcpyAsync(p->d_hS, S, sizeof(double2) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(S)");
+    pexsi_dm_info local;
+    std::string err;
+    rc = dm_range_herm(p, ws, &p->prof, p->d_hH, S ? p->d_hS : nullptr, mu, beta, n_poles, delta_e, 0, n_poles, 0,
+                       dm ? o_dm : nullptr, edm ? o_edm : nullptr, fdm ? o_fdm : nullptr, &local, &err);
+    if (info) *info = local;
+    if (rc) return fail(p, rc, err);
+    if (dm) ck(cudaMemcpyAsync(dm, o_dm, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, ws.stream), "D2H(dm)");
+    if (edm) ck(cudaMemcpyAsync(edm, o_edm, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, ws.stream), "D2H(edm)");
+    if (fdm) ck(cudaMemcpyAsync(fdm, o_fdm, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, ws.stream), "D2H(fdm)");
+    ck(cudaStreamSynchronize(ws.stream), "sync");
+    return PEXSI_OK;
+  } catch (const CudaError& ce) {
+    return map_cuda(p, ce);
+  } catch (const std::bad_alloc&) {
+    return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int pexsi_selinv_hermitian(pexsi_plan* p, const double* H, const double* S, double z_re, double z_im, double* ainv) {
+  if (p && p->opts.device < 0) return fail(p, PEXSI_ERR_INVALID_ARG, "host-only plan has no device");
+  if (!p || !H || !ainv) return fail(p, PEXSI_ERR_INVALID_ARG, "NULL argument");
+  if (z_im == 0.0) return fail(p, PEXSI_ERR_INVALID_ARG, "selected inversion needs Im z != 0");
+  try {
+    int rc = herm_enter(p);
+    if (rc) return rc;
+    Workspace& ws = p->ws;
+    const size_t nnz = size_t(p->sym.nnz);
+    ck(cudaMemcpyAsync(p->d_hH, H, sizeof(double2) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(H)");
+    if (S) ck(cudaMemcpyAsync(p->d_hS, S, sizeof(double2) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(S)");
+    std::string err;
+    rc = selinv_one_herm(p, ws, p->d_hH, S ? p->d_hS : nullptr, z_re, z_im, p->d_hout, &err);
+    if (rc) return fail(p, rc, err);
+    ck(cudaMemcpy(ainv, p->d_hout, sizeof(double2) * nnz, cudaMemcpyDeviceToHost), "D2H(ainv)");
+    return PEXSI_OK;
+  } catch (const CudaError& ce) {
+    return map_cuda(p, ce);
+  } catch (const std::bad_alloc&) {
+    return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int pexsi_inertia_hermitian(pexsi_plan* p, const double* H, const double* S, const double* shifts, int32_t n_shifts,
+                            int64_t* counts) {
+  if (p && p->opts.device < 0) return fail(p, PEXSI_ERR_INVALID_ARG, "host-only plan has no device");
+  if (!p || !H || !shifts || !counts || n_shifts <= 0) return fail(p, PEXSI_ERR_INVALID_ARG, "bad inertia arguments");
+  try {
+    int rc = herm_enter(p);
+    if (rc) return rc;
+    Workspace& ws = p->ws;
+    const size_t nnz = size_t(p->sym.nnz);
+    ck(cudaMemcpyAsync(p->d_hH, H, sizeof(double2) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(H)");
+    if (S) ck(cudaMemcpyAsync(p->d_hS, S, sizeof(double2) * nnz, cudaMemcpyHostToDevice, ws.stream), "H2D(S)");
+    std::string err;
+    rc = inertia_range_herm(p, ws, p->d_hH, S ? p->d_hS : nullptr, shifts, n_shifts, counts, &err);
+    return rc ? fail(p, rc, err) : PEXSI_OK;
+  } catch (const CudaError& ce) {
+    return map_cuda(p, ce);
+  } catch (const std::bad_alloc&) {
+    return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
   }
 }
 

@@ -269,11 +269,12 @@ __global__ void k_assemble(T* __restrict__ F, const double* __restrict__ H, cons
   }
 }
 
-// U_c (trailing r x r lower block of child c) added into the parent front.
-template <typename T>
+// U_c (trailing r x r block of child c: its lower triangle, or with FULL the
+// whole square of an LDU front) added into the parent front.
+template <typename T, bool FULL = false>
 __global__ void k_extend_add(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ children, int nchild,
                              const int32_t* __restrict__ pref) {
-  // one block per lower-triangle 32x32 tile of some child's update block
+  // one block per 32x32 tile (lower-triangle tiles unless FULL) of some child's update block
   const int ci = tile_owner(pref, nchild, int(blockIdx.x));
   const int c = children[ci];
   const int64_t base = int64_t(blockIdx.z) * fr.pool;
@@ -281,7 +282,13 @@ __global__ void k_extend_add(T* __restrict__ F, DevFronts fr, const int32_t* __r
   const int P = fr.parent[c];
   const int mP = fr.m[P];
   int I, J;
-  tri_tile(int(blockIdx.x) - pref[ci], I, J);
+  if (FULL) {
+    const int Tn = (r + 31) / 32, t = int(blockIdx.x) - pref[ci];
+    I = t % Tn;
+    J = t / Tn;
+  } else {
+    tri_tile(int(blockIdx.x) - pref[ci], I, J);
+  }
   const T* Fc = F + base + fr.off[c];
   T* Fp = F + base + fr.off[P];
   const int32_t* rel = fr.rel + fr.rptr[c];
@@ -291,7 +298,7 @@ __global__ void k_extend_add(T* __restrict__ F, DevFronts fr, const int32_t* __r
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     int j = J * 32 + threadIdx.y + 8 * q;
-    if (j < r && j <= i) {
+    if (j < r && (FULL || j <= i)) {
       T u = Fc[(s + i) + int64_t(m) * (s + j)];
       T* d = Fp + ri + int64_t(mP) * rel[j];
       *d = addv(*d, u);
@@ -305,7 +312,116 @@ __global__ void k_extend_add(T* __restrict__ F, DevFronts fr, const int32_t* __r
 // D (inertia) also the number of negative eigenvalues, from a Bunch-Kaufman
 // symmetric-pivoted LDL^T of D (Sylvester's law, Sec. II.C).
 template <typename T>
-__device__ void bk_count(T* Bm, int n, int ld, int* out_neg, bool* singular) {}
+__device__ void bk_count(T* Bm, int n, int ld, int* out_neg, bool* singular);
+
+__device__ __forceinline__ double2 conjv(double2 a) { return make_double2(a.x, -a.y); }
+
+// Complex Hermitian D (a real shift of Hermitian H and S): the same
+// Bunch-Kaufman pivoting on moduli, D = L E L^H with Hermitian 1x1 / 2x2
+// blocks E; a 1x1 pivot d (real) is negative when d < 0, a 2x2 pivot
+// [a conj(b); b c] (a, c real) holds one negative eigenvalue when its
+// determinant a c - |b|^2 < 0 and two when it is positive with a + c < 0.
+template <>
+__device__ void bk_count<double2>(double2* Bm, int n, int ld, int* out_neg, bool* singular) {
+  __shared__ int s_piv[3];
+  __shared__ int s_neg;
+  __shared__ double2 s_u[64], s_w[64];
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  if (threadIdx.x == 0) s_neg = 0;
+  __syncthreads();
+  int k = 0;
+  while (k < n) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      double lam = 0.0;
+      int r = k;
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        const double a = absv(Bm[i * ld + k]);
+        if (a > lam) { lam = a; r = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ol = __shfl_xor_sync(0xffffffffu, lam, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+        if (ol > lam || (ol == lam && orr < r)) { lam = ol; r = orr; }
+      }
+      const double akk = fabs(Bm[k * ld + k].x);
+      int kind = 1, swapr = k;
+      bool sing = false;
+      if (lam == 0.0 && akk == 0.0) { sing = true; kind = 1; }
+      else if (akk >= alpha * lam) { kind = 1; }
+      else {
+        double sig = 0.0;
+        for (int j = k + lane; j < n; j += 32)
+          if (j != r) sig = fmax(sig, absv(Bm[r * ld + j]));
+        for (int o = 16; o > 0; o >>= 1) sig = fmax(sig, __shfl_xor_sync(0xffffffffu, sig, o));
+        if (akk * sig >= alpha * lam * lam) kind = 1;
+        else if (fabs(Bm[r * ld + r].x) >= alpha * sig) { kind = 1; swapr = r; }
+        else { kind = 2; swapr = r; }
+      }
+      if (lane == 0) {
+        s_piv[0] = kind;
+        s_piv[1] = swapr;
+        if (sing) *singular = true;
+      }
+    }
+    __syncthreads();
+    const int kind = s_piv[0], sr = s_piv[1];
+    const int tgt = (kind == 1) ? k : k + 1;
+    if (sr != tgt) {  // symmetric swap of rows/columns tgt and sr (keeps D Hermitian)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double2 t = Bm[tgt * ld + j]; Bm[tgt * ld + j] = Bm[sr * ld + j]; Bm[sr * ld + j] = t;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 t = Bm[i * ld + tgt]; Bm[i * ld + tgt] = Bm[i * ld + sr]; Bm[i * ld + sr] = t;
+      }
+      __syncthreads();
+    }
+    if (kind == 1) {
+      const double d = Bm[k * ld + k].x;
+      if (threadIdx.x == 0) {
+        if (d < 0) ++s_neg;
+        if (d == 0.0) *singular = true;
+      }
+      const double inv = d != 0.0 ? 1.0 / d : 0.0;
+      // u_j = D(k, j) / d = conj(D(j, k)) / d
+      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) s_u[j] = scalev(conjv(Bm[j * ld + k]), inv);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < (n - k - 1) * (n - k - 1); idx += blockDim.x) {
+        int i = k + 1 + idx % (n - k - 1), j = k + 1 + idx / (n - k - 1);
+        Bm[i * ld + j] = fmsv(Bm[i * ld + j], Bm[i * ld + k], s_u[j]);
+      }
+      __syncthreads();
+      k += 1;
+    } else {
+      const double a = Bm[k * ld + k].x, c = Bm[(k + 1) * ld + (k + 1)].x;
+      const double2 bq = Bm[(k + 1) * ld + k];  // E = [a conj(b); b c]
+      const double det = a * c - (bq.x * bq.x + bq.y * bq.y);
+      if (threadIdx.x == 0) {
+        if (det < 0) s_neg += 1;
+        else if (det > 0 && a + c < 0) s_neg += 2;
+        if (det == 0.0) *singular = true;
+      }
+      const double id = det != 0.0 ? 1.0 / det : 0.0;
+      const int nn = n - k - 2;
+      // E^{-1} = [c -conj(b); -b a] / det applied to (x0, x1) = (D(k, j), D(k+1, j))
+      for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) {
+        const double2 x0 = conjv(Bm[j * ld + k]), x1 = conjv(Bm[j * ld + k + 1]);
+        s_u[j] = scalev(subv(scalev(x0, c), mulv(conjv(bq), x1)), id);
+        s_w[j] = scalev(subv(scalev(x1, a), mulv(bq, x0)), id);
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nn * nn; idx += blockDim.x) {
+        int i = k + 2 + idx % nn, j = k + 2 + idx / nn;
+        Bm[i * ld + j] = fmsv(fmsv(Bm[i * ld + j], Bm[i * ld + k], s_u[j]), Bm[i * ld + k + 1], s_w[j]);
+      }
+      __syncthreads();
+      k += 2;
+    }
+  }
+  if (threadIdx.x == 0) *out_neg = s_neg;
+  __syncthreads();
+}
 
 template <>
 __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* singular) {
@@ -412,7 +528,7 @@ __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* 
 // of each SM is the bound, not the latency of its multiply-adds).
 constexpr int kDiagThreads = 256;
 
-template <typename T>
+template <typename T, bool GEN = false>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b,
                            DevStatus st, int count_inertia) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -435,7 +551,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
   double lmax = 0.0;
   for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
     int i = idx % bb, j = idx / bb;
-    T v = (i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
+    // symmetric fronts hold the lower triangle; LDU fronts (GEN) both
+    T v = (GEN || i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
     Aug[i * ld + j] = v;
     lmax = fmax(lmax, absv(v));
   }
@@ -446,8 +563,9 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
 
   if (count_inertia) {
     // Bunch-Kaufman count on a copy placed after the augmented matrix
-    if constexpr (sizeof(T) == sizeof(double)) {
-      double* Bm = reinterpret_cast<double*>(Aug + bb * ld);
+    // (real symmetric blocks, or Hermitian ones of an LDU front with a real shift)
+    if constexpr (sizeof(T) == sizeof(double) || GEN) {
+      T* Bm = Aug + bb * ld;
       for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
         int i = idx % bb, j = idx / bb;
         Bm[i * b + j] = Aug[i * ld + j];
@@ -457,7 +575,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
       __shared__ bool s_sing;
       if (threadIdx.x == 0) s_sing = false;
       __syncthreads();
-      bk_count<double>(Bm, bb, b, &s_neg, &s_sing);
+      bk_count<T>(Bm, bb, b, &s_neg, &s_sing);
       if (threadIdx.x == 0) {
         atomicAdd(&st.neg_count[pb], s_neg);
         if (s_sing) atomicMin(st.breakdown_front, f);
@@ -527,7 +645,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
 }
 
 // ------------------------------------------------------------ panel solve
-template <typename T>
+template <typename T, bool GEN = false>
 __global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts,
                                                      int p0, int b) {
   extern __shared__ __align__(16) double gsm[];
@@ -542,11 +660,13 @@ __global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFront
   T acc[4][4];
   zero_acc(acc);
   gemm_any<T, false>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * p0, m, Mv, bb, bb, gsm);
-  // W^T into the upper triangle (rows p0.., columns q0+I0..)
-  for (int idx = threadIdx.x; idx < Mv * bb; idx += blockDim.x) {
-    int k = idx % bb, r = idx / bb;
-    Fb[(p0 + k) + int64_t(m) * (q0 + I0 + r)] = Fb[(q0 + I0 + r) + int64_t(m) * (p0 + k)];
-  }
+  // W^T into the upper triangle (rows p0.., columns q0+I0..); an LDU front
+  // (GEN) already holds its own row panel A[P,S] there
+  if (!GEN)
+    for (int idx = threadIdx.x; idx < Mv * bb; idx += blockDim.x) {
+      int k = idx % bb, r = idx / bb;
+      Fb[(p0 + k) + int64_t(m) * (q0 + I0 + r)] = Fb[(q0 + I0 + r) + int64_t(m) * (p0 + k)];
+    }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -558,8 +678,37 @@ __global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFront
     }
 }
 
+// Row panel of an LDU front: U[P,S] = D^{-1} A[P,S] over 64-column tiles of
+// S, in place (each CTA reads and writes its own columns only), after the
+// Schur update has used A[P,S].
+__global__ void __launch_bounds__(256) k_panel_upper(double2* __restrict__ F, DevFronts fr,
+                                                     const int32_t* __restrict__ fronts, int p0, int b) {
+  extern __shared__ __align__(16) double gsm[];
+  const int f = fronts[blockIdx.y];
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
+  const int I0 = blockIdx.x * kTile;
+  if (I0 >= mp) return;
+  double2* Fb = F + int64_t(blockIdx.z) * fr.pool + fr.off[f];
+  const int Nv = min(kTile, mp - I0);
+  double2 acc[4][4];
+  zero_acc(acc);
+  gemm_any<double2, false>(acc, Fb + p0 + int64_t(m) * p0, m, Fb + p0 + int64_t(m) * (q0 + I0), m, bb, Nv, bb, gsm);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int r = tx + 16 * i, c = ty + 16 * j;
+      if (r < bb && c < Nv) Fb[(p0 + r) + int64_t(m) * (q0 + I0 + c)] = acc[i][j];
+    }
+}
+
 // ------------------------------------------------------------ Schur update
-template <typename T>
+// F[S,S] -= L[S,P] B[P,S] with B the stored W^T (symmetric fronts: lower
+// triangle tiles) or the row panel A[P,S] of an LDU front (FULL: all tiles).
+template <typename T, bool FULL = false>
 __global__ void __launch_bounds__(256) k_trailing(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts,
                                                   int p0, int b) {
   extern __shared__ __align__(16) double gsm[];
@@ -568,9 +717,14 @@ __global__ void __launch_bounds__(256) k_trailing(T* __restrict__ F, DevFronts f
   if (p0 >= s) return;
   const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
   const int Tn = (mp + kTile - 1) / kTile;
-  if (int(blockIdx.x) >= Tn * (Tn + 1) / 2) return;
+  if (int(blockIdx.x) >= (FULL ? Tn * Tn : Tn * (Tn + 1) / 2)) return;
   int I, J;
-  tri_tile(blockIdx.x, I, J);
+  if (FULL) {
+    I = int(blockIdx.x) % Tn;
+    J = int(blockIdx.x) / Tn;
+  } else {
+    tri_tile(blockIdx.x, I, J);
+  }
   T* Fb = F + int64_t(blockIdx.z) * fr.pool + fr.off[f];
   const int r0 = q0 + I * kTile, c0 = q0 + J * kTile;
   const int Mv = min(kTile, m - r0), Nv = min(kTile, m - c0);
@@ -583,7 +737,7 @@ __global__ void __launch_bounds__(256) k_trailing(T* __restrict__ F, DevFronts f
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int r = tx + 16 * i, c = ty + 16 * j;
-      if (r < Mv && c < Nv && (I != J || r >= c)) {
+      if (r < Mv && c < Nv && (FULL || I != J || r >= c)) {
         T* d = Fb + (r0 + r) + int64_t(m) * (c0 + c);
         *d = subv(*d, acc[i][j]);
       }
@@ -615,6 +769,10 @@ __global__ void k_gather(double2* __restrict__ Y, DevFronts fr, const int32_t* _
   }
 }
 
+// Y[S,P] = -Y[S,S] L[S,P] over 64-row tiles of S, and its mirror Y[P,S] =
+// Y[S,P]^T. LDU fronts (GEN) have no mirror: blocks blockIdx.x >= gridDim.x
+// / 2 compute Y[P,S] = -U[P,S] Y[S,S] over 64-column tiles of S instead.
+template <bool GEN = false>
 __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y, const double2* __restrict__ F, DevFronts fr,
                                                         const int32_t* __restrict__ fronts, int p0, int b) {
   extern __shared__ __align__(16) double gsm[];
@@ -622,7 +780,9 @@ __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y,
   const int s = fr.s[f], m = fr.m[f];
   if (p0 >= s) return;
   const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
-  const int I0 = blockIdx.x * kTile;
+  const int half = GEN ? int(gridDim.x) / 2 : int(gridDim.x);
+  const bool upper = GEN && int(blockIdx.x) >= half;
+  const int I0 = (upper ? int(blockIdx.x) - half : int(blockIdx.x)) * kTile;
   if (I0 >= mp) return;
   const int64_t base = int64_t(blockIdx.z) * fr.pool + fr.off[f];
   double2* Yb = Y + base;
@@ -630,21 +790,27 @@ __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y,
   const int Mv = min(kTile, mp - I0);
   double2 acc[4][4];
   zero_acc(acc);
-  gemm_any<double2, false>(acc, Yb + q0 + I0 + int64_t(m) * q0, m, Fb + q0 + int64_t(m) * p0, m, Mv, bb, mp, gsm);
+  if (upper)  // U[P,S] (bb x mp) times the columns I0.. of Y[S,S]
+    gemm_any<double2, false>(acc, Fb + p0 + int64_t(m) * q0, m, Yb + q0 + int64_t(m) * (q0 + I0), m, bb, Mv, mp, gsm);
+  else
+    gemm_any<double2, false>(acc, Yb + q0 + I0 + int64_t(m) * q0, m, Fb + q0 + int64_t(m) * p0, m, Mv, bb, mp, gsm);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int r = tx + 16 * i, c = ty + 16 * j;
-      if (r < Mv && c < bb) {
+      if (upper) {
+        if (r < bb && c < Mv) Yb[(p0 + r) + int64_t(m) * (q0 + I0 + c)] = negv(acc[i][j]);
+      } else if (r < Mv && c < bb) {
         double2 v = negv(acc[i][j]);
         Yb[(q0 + I0 + r) + int64_t(m) * (p0 + c)] = v;
-        Yb[(p0 + c) + int64_t(m) * (q0 + I0 + r)] = v;
+        if (!GEN) Yb[(p0 + c) + int64_t(m) * (q0 + I0 + r)] = v;
       }
     }
 }
 
+template <bool GEN = false>
 __global__ void __launch_bounds__(256) k_selinv_diag_partial(const double2* __restrict__ Y, const double2* __restrict__ F,
                                                              double2* __restrict__ part, const int64_t* __restrict__ part_off,
                                                              int64_t part_stride, DevFronts fr,
@@ -662,8 +828,13 @@ __global__ void __launch_bounds__(256) k_selinv_diag_partial(const double2* __re
   const int Kv = min(kTile, mp - I0);
   double2 acc[4][4];
   zero_acc(acc);
-  // partial(c1, c2) = sum_{i in tile} L[i, p0+c1] Y[i, p0+c2]
-  gemm_any<double2, true>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Yb + q0 + I0 + int64_t(m) * p0, m, bb, bb, Kv, gsm);
+  // partial(c1, c2) = sum_{i in tile} L[i, p0+c1] Y[i, p0+c2], or for an LDU
+  // front sum_{i in tile} U[p0+c1, i] Y[i, p0+c2]
+  if (GEN)
+    gemm_any<double2, false>(acc, Fb + p0 + int64_t(m) * (q0 + I0), m, Yb + q0 + I0 + int64_t(m) * p0, m, bb, bb, Kv,
+                             gsm);
+  else
+    gemm_any<double2, true>(acc, Fb + q0 + I0 + int64_t(m) * p0, m, Yb + q0 + I0 + int64_t(m) * p0, m, bb, bb, Kv, gsm);
   double2* out = part + int64_t(blockIdx.z) * part_stride + part_off[f] + int64_t(blockIdx.x) * b * b;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -675,6 +846,7 @@ __global__ void __launch_bounds__(256) k_selinv_diag_partial(const double2* __re
     }
 }
 
+template <bool GEN = false>
 __global__ void k_selinv_diag_reduce(double2* __restrict__ Y, const double2* __restrict__ F,
                                      const double2* __restrict__ part, const int64_t* __restrict__ part_off,
                                      int64_t part_stride, DevFronts fr, const int32_t* __restrict__ fronts, int p0, int b) {
@@ -699,7 +871,8 @@ __global__ void k_selinv_diag_reduce(double2* __restrict__ Y, const double2* __r
   for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
     int r = idx % bb, c = idx / bb;
     double2 a = tmp[r + bb * c], t = tmp[c + bb * r];
-    Yb[(p0 + r) + int64_t(m) * (p0 + c)] = make_double2(0.5 * (a.x + t.x), 0.5 * (a.y + t.y));
+    // Y[P,P] of a complex-symmetric front is symmetrised; an LDU front's is not symmetric
+    Yb[(p0 + r) + int64_t(m) * (p0 + c)] = GEN ? a : make_double2(0.5 * (a.x + t.x), 0.5 * (a.y + t.y));
   }
 }
 
@@ -722,6 +895,48 @@ __global__ void k_pole_sum(const double2* __restrict__ Y, int64_t pool, const in
     if (edm) edm[e] = overwrite ? ae : edm[e] + ae;
     if (fdm) fdm[e] = overwrite ? af : fdm[e] + af;
     if (ddm) ddm[e] = overwrite ? ad : ddm[e] + ad;
+  }
+}
+
+// Assembly of an LDU front from complex H and S (interleaved, nnz each):
+// every CSC entry at its own position (both triangles), A = H - z S.
+__global__ void k_assemble_gen(double2* __restrict__ F, const double2* __restrict__ H, const double2* __restrict__ S,
+                               const int64_t* __restrict__ pos, int64_t nnz, int64_t pool, BatchShifts sh) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t p = pos[e];
+    const double2 h = H[e], v = S[e];
+    for (int b = 0; b < sh.nb; ++b)  // (hr + i hi) - (zr + i zi)(sr + i si)
+      F[b * pool + p] = make_double2(h.x - fma(sh.re[b], v.x, -sh.im[b] * v.y), h.y - fma(sh.re[b], v.y, sh.im[b] * v.x));
+  }
+}
+
+// Pole sum of the Hermitian variant: with G = (H - z S)^{-1} and (H - conj(z)
+// S)^{-1} = G^H, the folded pole pair contributes (w G - conj(w) G^H) / 2i;
+// at entry (r, c), with a = w G[r,c] and t = w G[c,r], that is
+// ((a.im + t.im) + i (t.re - a.re)) / 2. Complex outputs (interleaved).
+__global__ void k_pole_sum_herm(const double2* __restrict__ Y, int64_t pool, const int64_t* __restrict__ pos,
+                                const int64_t* __restrict__ pos_t, int64_t nnz, BatchShifts sh, int overwrite,
+                                double2* __restrict__ dm, double2* __restrict__ edm, double2* __restrict__ fdm,
+                                double2* __restrict__ ddm) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t p = pos[e], q = pos_t[e];
+    double2 o[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    for (int b = 0; b < sh.nb; ++b) {
+      const double2 g = Y[b * pool + p], gt = Y[b * pool + q];
+      const double wr[4] = {sh.wr_re[b], sh.we_re[b], sh.wf_re[b], sh.wd_re[b]};
+      const double wi[4] = {sh.wr_im[b], sh.we_im[b], sh.wf_im[b], sh.wd_im[b]};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double2 w = make_double2(wr[k], wi[k]);
+        const double2 a = mulv(w, g), t = mulv(w, gt);
+        o[k].x += 0.5 * (a.y + t.y);
+        o[k].y += 0.5 * (t.x - a.x);
+      }
+    }
+    double2* outs[4] = {dm, edm, fdm, ddm};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (outs[k]) outs[k][e] = overwrite ? o[k] : addv(outs[k][e], o[k]);
   }
 }
 
@@ -873,17 +1088,93 @@ cudaError_t configure_kernels(int b) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_r));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_selinv_diag_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // LDU fronts: the Hermitian inertia count keeps a complex copy of the block
+  const size_t need_g = sizeof(double2) * size_t(b) * (b + 1) + sizeof(double2) * b * b;
+  e = cudaFuncSetAttribute(k_diag_inv<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_g));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_selinv_diag_reduce<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(sizeof(double2) * b * b));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_selinv_diag_reduce<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(sizeof(double2) * b * b));
   if (e != cudaSuccess) return e;
   const void* gemms[] = {(const void*)k_panel_solve<double>, (const void*)k_panel_solve<double2>,
+                         (const void*)k_panel_solve<double2, true>, (const void*)k_panel_upper,
                          (const void*)k_trailing<double>, (const void*)k_trailing<double2>,
-                         (const void*)k_selinv_offdiag, (const void*)k_selinv_diag_partial};
+                         (const void*)k_trailing<double2, true>, (const void*)k_selinv_offdiag<false>,
+                         (const void*)k_selinv_offdiag<true>, (const void*)k_selinv_diag_partial<false>,
+                         (const void*)k_selinv_diag_partial<true>};
   for (const void* fn : gemms) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem3m));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// ---- LDU fronts of complex Hermitian H and S (general complex shifted matrices)
+void launch_assemble_gen(double2* F, const double2* H, const double2* S, const int64_t* pos, int64_t nnz,
+                         int64_t pool, const BatchShifts& sh, cudaStream_t st) {
+  k_assemble_gen<<<grid_for(nnz, 256), 256, 0, st>>>(F, H, S, pos, nnz, pool, sh);
+}
+
+void launch_extend_add_full(double2* F, const DevFronts& fr, const int32_t* children, int nchild, const int32_t* pref,
+                            int64_t total_tiles, const BatchShifts& sh, cudaStream_t st) {
+  if (nchild <= 0 || total_tiles <= 0) return;
+  dim3 grid(unsigned(total_tiles), 1, sh.nb), block(32, 8);
+  k_extend_add<double2, true><<<grid, block, 0, st>>>(F, fr, children, nchild, pref);
+}
+
+void launch_diag_inv_gen(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+                         const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
+  if (nfronts <= 0) return;
+  size_t smem = sizeof(double2) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double2) * b * b : 0);
+  dim3 grid(nfronts, sh.nb);
+  k_diag_inv<double2, true><<<grid, kDiagThreads, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
+}
+
+void launch_panel_solve_gen(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_row_tiles,
+                            int p0, int b, const BatchShifts& sh, cudaStream_t st, bool upper) {
+  if (nfronts <= 0 || max_row_tiles <= 0) return;
+  dim3 grid(max_row_tiles, nfronts, sh.nb);
+  if (upper) k_panel_upper<<<grid, 256, kSmem3m, st>>>(F, fr, fronts, p0, b);
+  else k_panel_solve<double2, true><<<grid, 256, kSmem3m, st>>>(F, fr, fronts, p0, b);
+}
+
+void launch_trailing_full(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_row_tiles,
+                          int p0, int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_row_tiles <= 0) return;
+  dim3 grid(max_row_tiles * max_row_tiles, nfronts, sh.nb);
+  k_trailing<double2, true><<<grid, 256, kSmem3m, st>>>(F, fr, fronts, p0, b);
+}
+
+void launch_selinv_offdiag_gen(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                               int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_row_tiles <= 0) return;
+  dim3 grid(2 * max_row_tiles, nfronts, sh.nb);
+  k_selinv_offdiag<true><<<grid, 256, kSmem3m, st>>>(Y, F, fr, fronts, p0, b);
+}
+
+void launch_selinv_diag_partial_gen(const double2* Y, const double2* F, double2* part, const int64_t* part_off,
+                                    int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                                    int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0 || max_row_tiles <= 0) return;
+  dim3 grid(max_row_tiles, nfronts, sh.nb);
+  k_selinv_diag_partial<true><<<grid, 256, kSmem3m, st>>>(Y, F, part, part_off, part_stride, fr, fronts, p0, b);
+}
+
+void launch_selinv_diag_reduce_gen(double2* Y, const double2* F, const double2* part, const int64_t* part_off,
+                                   int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0,
+                                   int b, const BatchShifts& sh, cudaStream_t st) {
+  if (nfronts <= 0) return;
+  dim3 grid(nfronts, sh.nb);
+  k_selinv_diag_reduce<true><<<grid, 256, sizeof(double2) * b * b, st>>>(Y, F, part, part_off, part_stride, fr, fronts,
+                                                                          p0, b);
+}
+
+void launch_pole_sum_herm(const double2* Y, int64_t pool, const int64_t* pos, const int64_t* pos_t, int64_t nnz,
+                          const BatchShifts& sh, int overwrite, double2* dm, double2* edm, double2* fdm, double2* ddm,
+                          cudaStream_t st) {
+  k_pole_sum_herm<<<grid_for(nnz, 256), 256, 0, st>>>(Y, pool, pos, pos_t, nnz, sh, overwrite, dm, edm, fdm, ddm);
 }
 
 #define PEXSI_INSTANTIATE(T)                                                                                        \

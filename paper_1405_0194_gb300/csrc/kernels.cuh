@@ -165,6 +165,36 @@ void launch_oz_gemm_schur_real(double* F, const DevFronts& fr, const int32_t* fr
                                int p0, int b, int S, const OzScratch& oz, int nb, cudaStream_t st, int cb);
 cudaError_t oz_configure(int S);
 
+// ---- LDU fronts (complex Hermitian H and S, Sec. IV's k-point / spin-orbit
+// variant): A = H - z S is only structurally symmetric, so a front holds L
+// below and U above its diagonal blocks, the Schur update covers the whole
+// trailing square, and selected inversion computes Y[S,P] = -Y[S,S] L[S,P]
+// and Y[P,S] = -U[P,S] Y[S,S] separately, with Y[P,P] = D^-1 - U[P,S] Y[S,P].
+void launch_assemble_gen(double2* F, const double2* H, const double2* S, const int64_t* pos, int64_t nnz,
+                         int64_t pool, const BatchShifts& sh, cudaStream_t st);
+void launch_extend_add_full(double2* F, const DevFronts& fr, const int32_t* children, int nchild, const int32_t* pref,
+                            int64_t total_tiles, const BatchShifts& sh, cudaStream_t st);
+// count_inertia (real shifts of Hermitian H, S): Hermitian Bunch-Kaufman count of each D block
+void launch_diag_inv_gen(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+                         const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st);
+// upper = false: L[S,P] = A[S,P] D^-1 (A[P,S] stays); upper = true: U[P,S] = D^-1 A[P,S]
+void launch_panel_solve_gen(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_row_tiles,
+                            int p0, int b, const BatchShifts& sh, cudaStream_t st, bool upper);
+void launch_trailing_full(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int max_row_tiles,
+                          int p0, int b, const BatchShifts& sh, cudaStream_t st);
+void launch_selinv_offdiag_gen(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                               int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st);
+void launch_selinv_diag_partial_gen(const double2* Y, const double2* F, double2* part, const int64_t* part_off,
+                                    int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts,
+                                    int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st);
+void launch_selinv_diag_reduce_gen(double2* Y, const double2* F, const double2* part, const int64_t* part_off,
+                                   int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0,
+                                   int b, const BatchShifts& sh, cudaStream_t st);
+// (w G - conj(w) G^H) / 2i at each CSC entry: pos = its own position, pos_t = that of its transpose
+void launch_pole_sum_herm(const double2* Y, int64_t pool, const int64_t* pos, const int64_t* pos_t, int64_t nnz,
+                          const BatchShifts& sh, int overwrite, double2* dm, double2* edm, double2* fdm, double2* ddm,
+                          cudaStream_t st);
+
 // Raises the dynamic shared-memory limits the kernels need for panel width b.
 cudaError_t configure_kernels(int b);
 

@@ -44,6 +44,9 @@ struct Level {
   // the plan's d_tile_pref, so that a launch has exactly one block per tile
   int64_t gather_pref_off = 0, gather_total = 0;
   std::vector<int64_t> ea_pref_off, ea_total;
+  // the same for the whole r x r update block of each child (LDU fronts)
+  std::vector<int64_t> ea_pref_off_full, ea_total_full;
+  std::vector<double> ea_elems_full;
   int32_t max_s = 0;
 };
 
@@ -131,6 +134,12 @@ struct pexsi_plan {
   int trace_blocks = 256;
   pexsi::Profiler prof;
   pexsi::Workspace ws;  // the plan's own workspace (plan API calls)
+  // complex Hermitian variant (LDU fronts), created on its first call: the
+  // front position of each CSC entry and of its transpose, a complex
+  // identity S, and the plan API's complex staging (H, S: nnz; outputs: 4 nnz)
+  int64_t *d_pos_full = nullptr, *d_pos_t = nullptr;
+  std::vector<int64_t> diag_entries;  // CSC entries on the diagonal
+  double2 *d_ident_c = nullptr, *d_hH = nullptr, *d_hS = nullptr, *d_hout = nullptr;
 
   pexsi::DevFronts fronts() const {
     pexsi::DevFronts f;
@@ -172,6 +181,19 @@ int inertia_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const doub
 
 // The plan's own workspace (created on first use); PEXSI code.
 int plan_workspace(pexsi_plan* p);
+
+// Complex Hermitian H and S (interleaved complex, nnz each; dS NULL = I):
+// poles [begin, end) into complex d_dm / d_edm / d_fdm (any may be NULL)
+// through LDU fronts; Gamma^d into the plan's staging. Same status rules as
+// dm_range. Needs the plan's Hermitian maps (hermitian_prepare).
+int hermitian_prepare(pexsi_plan* p);
+int inertia_range_herm(const pexsi_plan* p, Workspace& ws, const double2* dH, const double2* dS, const double* shifts,
+                       int n_shifts, int64_t* counts, std::string* err);
+int selinv_one_herm(const pexsi_plan* p, Workspace& ws, const double2* dH, const double2* dS, double z_re, double z_im,
+                    double2* d_ainv, std::string* err);
+int dm_range_herm(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double2* dH, const double2* dS, double mu,
+                  double beta, int P, double delta_e, int begin, int end, int accumulate, double2* d_dm,
+                  double2* d_edm, double2* d_fdm, pexsi_dm_info* info, std::string* err);
 
 // Selected inverse of one complex shift into d_ainv (device, nnz complex);
 // synchronises ws.stream.

@@ -750,6 +750,7 @@ int analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
   // map CSC entries to front positions of their lower-triangle copy
   out.entry_pos.resize(out.nnz);
   out.entry_lower.resize(out.nnz);
+  out.entry_pos_up.resize(out.nnz);
   for (int64_t j = 0; j < n; ++j) {
     int32_t b = out.iperm[j];
     for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e) {
@@ -767,6 +768,7 @@ int analyse(int64_t n, const int64_t* colptr, const int32_t* rowind, const int32
         lr = out.s(K) + int32_t(f - pr);
       }
       out.entry_pos[e] = out.front_off[K] + int64_t(lc) * out.m(K) + lr;
+      out.entry_pos_up[e] = out.front_off[K] + int64_t(lr) * out.m(K) + lc;
       out.entry_lower[e] = a >= b ? 1 : 0;
     }
   }

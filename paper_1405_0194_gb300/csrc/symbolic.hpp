@@ -31,6 +31,9 @@ struct Symbolic {
   // in the new numbering) inside its front, and whether e is that lower copy.
   std::vector<int64_t> entry_pos;
   std::vector<uint8_t> entry_lower;
+  // The mirror of entry_pos across the front's diagonal: the upper-triangle
+  // position of the same pair of rows (LDU fronts store both triangles).
+  std::vector<int64_t> entry_pos_up;
 
   int32_t nlevels = 0;
   std::vector<std::vector<int32_t>> level_fronts;  // fronts per height, big first
