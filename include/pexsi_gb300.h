@@ -273,6 +273,74 @@ int pexsi_selinv_hermitian(pexsi_plan* plan, const double* H, const double* S, d
 int pexsi_inertia_hermitian(pexsi_plan* plan, const double* H, const double* S, const double* shifts,
                             int32_t n_shifts, int64_t* counts);
 
+/* ------------------------------------------------------------ groups of systems
+ * Batching across systems (poles and systems are independent, Sec. II.B; the
+ * elimination-tree concurrency of Eq. parent): the fronts of several
+ * systems of different sizes are concatenated into one pool and their
+ * elimination trees into one forest, so that each launch of the level
+ * schedule -- block inverses, panel solves, Schur updates, Takahashi steps,
+ * persistent split-precision GEMMs -- covers the fronts of every system at
+ * that height of its tree, for all poles of a wave. Assembly and the pole
+ * sum run per system (its own H, S, mu, beta, Delta E). A system's result is
+ * the one its own plan gives with the same wave size and options.
+ *
+ * pexsi_group_create: plans[q] (n_plans of them) supply the symbolic
+ * structure of system q (host-only plans, device = -1, suffice; the group
+ * copies what it needs and the plans may be destroyed afterwards); all must
+ * share opts->panel. opts: device, split_slices, max_batch (the most poles
+ * per wave), hbm_budget, wait_ns of the group. Errors: INVALID_ARG (no
+ * plans, NULL plan, panel mismatch, host-only device), NOMEM (one pole of
+ * all systems does not fit the budget), CUDA. */
+typedef struct pexsi_group pexsi_group;
+
+/* Schedule of a group: poles per wave, and the panels per block of the
+ * split-precision Schur update (one K = 64 * oz_block update per block). */
+typedef struct pexsi_schedule {
+  int32_t wave;        /* poles of every system per wave, 1..batch capacity   */
+  int32_t oz_block;    /* 1, 2, 3 or 4 (split_slices > 0; ignored otherwise)  */
+  double ms_per_pole;  /* the tuner's measurement (0 when set by hand)         */
+  int32_t from_cache;  /* 1: the tuner took it from the cache file             */
+  int32_t candidates;  /* schedules the tuner timed                           */
+} pexsi_schedule;
+
+int pexsi_group_create(const pexsi_plan* const* plans, int32_t n_plans, const pexsi_opts* opts,
+                       pexsi_group** out);
+int pexsi_group_destroy(pexsi_group* group);
+/* Statistics of the merged plan (sums over the systems; batch = capacity). */
+int pexsi_group_get_stats(const pexsi_group* group, pexsi_plan_stats* stats);
+int pexsi_group_get_schedule(const pexsi_group* group, pexsi_schedule* out);
+/* wave = 0 means the batch capacity. Errors: INVALID_ARG (out of range). */
+int pexsi_group_set_schedule(pexsi_group* group, const pexsi_schedule* schedule);
+/* DM / EDM / FDM of every system over the pole subrange [pole_begin,
+ * pole_end) of its n_poles-pole table (the same P for all systems). dH[q],
+ * dS[q] (NULL or dS == NULL: S = I), d_dm[q], d_edm[q], d_fdm[q] (any may be
+ * NULL): device arrays of system q's nnz; mu, beta, delta_e: arrays of
+ * n_plans. info: NULL (return after enqueueing on `stream`) or n_plans
+ * reports (synchronises; traces per system; breakdown_front is the front
+ * index within its system). Status chains and errors as pexsi_dm_device. */
+int pexsi_group_dm_device(pexsi_group* group, const double* const* dH, const double* const* dS,
+                          const double* mu, const double* beta, int32_t n_poles, const double* delta_e,
+                          int32_t pole_begin, int32_t pole_end, int32_t accumulate, double* const* d_dm,
+                          double* const* d_edm, double* const* d_fdm, void* stream, pexsi_dm_info* info);
+/* Host-buffer form over all n_poles poles (synchronous; S may be NULL). */
+int pexsi_group_dm(pexsi_group* group, const double* const* H, const double* const* S, const double* mu,
+                   const double* beta, int32_t n_poles, const double* delta_e, double* const* dm,
+                   double* const* edm, double* const* fdm, pexsi_dm_info* info);
+/* The group's own schedule tuner: times each candidate schedule (wave = the
+ * batch capacity, half, a quarter; oz_block = 4, 2, 1 on the split path) on
+ * the device with CUDA events, on poles [0, wave) of the given device inputs
+ * (as pexsi_group_dm_device), keeps the fastest per pole, and appends it to
+ * the text file cache_path (NULL = no cache) under a fingerprint of the
+ * device, the precision, the batch capacity and the systems' structure. When
+ * the file already holds the fingerprint, that schedule is applied and
+ * nothing is timed, unless force != 0. out (may be NULL) gets the schedule.
+ * The group's output buffers are overwritten. Errors as
+ * pexsi_group_dm_device. */
+int pexsi_group_tune(pexsi_group* group, const double* const* dH, const double* const* dS, const double* mu,
+                     const double* beta, int32_t n_poles, const double* delta_e, const char* cache_path,
+                     int32_t force, pexsi_schedule* out);
+const char* pexsi_group_last_error_detail(const pexsi_group* group);
+
 /* ------------------------------------------------------------ chemical potential
  * Sec. II.C: find mu with N_beta(mu) = Tr[DM S] = N_e (Eq. Nmu).
  * 1. Inertia counting: N_inf(eps) = 2 x (# eigenvalues of (H,S) below eps) at

@@ -61,6 +61,11 @@ class pexsi_dm_info(ctypes.Structure):
                 ("trace_ddm_s", ctypes.c_double)]
 
 
+class pexsi_schedule(ctypes.Structure):
+    _fields_ = [("wave", ctypes.c_int32), ("oz_block", ctypes.c_int32), ("ms_per_pole", ctypes.c_double),
+                ("from_cache", ctypes.c_int32), ("candidates", ctypes.c_int32)]
+
+
 class pexsi_kernel_profile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double), ("tensor_flops", ctypes.c_double)]
@@ -153,6 +158,26 @@ SIGNATURES = [
                                               ctypes.c_double, c_double_p]),
     ("pexsi_inertia_hermitian", ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_double_p, ctypes.c_int32,
                                                c_int64_p]),
+    ("pexsi_group_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                          ctypes.POINTER(pexsi_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    ("pexsi_group_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("pexsi_group_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pexsi_plan_stats)]),
+    ("pexsi_group_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pexsi_schedule)]),
+    ("pexsi_group_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pexsi_schedule)]),
+    ("pexsi_group_dm_device", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(ctypes.c_void_p), c_double_p, c_double_p, ctypes.c_int32,
+                                             c_double_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                             ctypes.POINTER(pexsi_dm_info)]),
+    ("pexsi_group_dm", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p), c_double_p, c_double_p, ctypes.c_int32,
+                                      c_double_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(pexsi_dm_info)]),
+    ("pexsi_group_tune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), c_double_p, c_double_p, ctypes.c_int32,
+                                        c_double_p, ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(pexsi_schedule)]),
+    ("pexsi_group_last_error_detail", ctypes.c_char_p, [ctypes.c_void_p]),
     ("pexsi_trace_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     ("pexsi_mu_opts_default", ctypes.c_int, [ctypes.POINTER(pexsi_mu_opts)]),
@@ -446,6 +471,99 @@ def pexsi_inertia_hermitian(plan, H, S, shifts) -> np.ndarray:
                                        int(shifts.shape[0]), _ptr(counts, ctypes.c_int64))
     _check(rc, plan)
     return counts
+
+
+# ---------------------------------------------------------------- groups of systems
+def _ptrs(vals):
+    """ctypes array of void* from integers / numpy arrays / None."""
+    arr = (ctypes.c_void_p * len(vals))()
+    for i, v in enumerate(vals):
+        if v is None or (isinstance(v, int) and v == 0):
+            arr[i] = None
+        elif isinstance(v, np.ndarray):
+            arr[i] = v.ctypes.data
+        else:
+            arr[i] = int(v)
+    return arr
+
+
+def _gcheck(rc, group):
+    if rc != 0:
+        d = lib().pexsi_group_last_error_detail(group) if group else b""
+        raise PexsiError(rc, (d.decode() if d else "") or lib().pexsi_strerror(rc).decode())
+
+
+def pexsi_group_create(plans, opts: pexsi_opts | None = None):
+    """A group over the systems of `plans` (plan handles). Returns a handle."""
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    h = ctypes.c_void_p()
+    rc = lib().pexsi_group_create(arr, len(plans), None if opts is None else ctypes.byref(opts), ctypes.byref(h))
+    _check(rc)
+    return h.value
+
+
+def pexsi_group_destroy(group):
+    _check(lib().pexsi_group_destroy(group))
+
+
+def pexsi_group_get_stats(group) -> dict:
+    st = pexsi_plan_stats()
+    _gcheck(lib().pexsi_group_get_stats(group, ctypes.byref(st)), group)
+    return _as_dict(st)
+
+
+def pexsi_group_get_schedule(group) -> dict:
+    sc = pexsi_schedule()
+    _gcheck(lib().pexsi_group_get_schedule(group, ctypes.byref(sc)), group)
+    return _as_dict(sc)
+
+
+def pexsi_group_set_schedule(group, wave=0, oz_block=4):
+    sc = pexsi_schedule(int(wave), int(oz_block), 0.0, 0, 0)
+    _gcheck(lib().pexsi_group_set_schedule(group, ctypes.byref(sc)), group)
+
+
+def pexsi_group_dm_device(group, dH, dS, mu, beta, n_poles, delta_e, pole_begin, pole_end, accumulate, d_dm, d_edm,
+                          d_fdm, stream=0, want_info=False):
+    """Device form: dH, dS, d_dm, d_edm, d_fdm are lists of device addresses
+    (one per system; dS may be None); mu, beta, delta_e lists of floats.
+    Returns a list of info dicts when want_info."""
+    n = len(dH)
+    mu_a, beta_a, de_a = (np.ascontiguousarray(x, dtype=np.float64) for x in (mu, beta, delta_e))
+    infos = (pexsi_dm_info * n)() if want_info else None
+    rc = lib().pexsi_group_dm_device(group, _ptrs(dH), None if dS is None else _ptrs(dS), _ptr(mu_a, ctypes.c_double),
+                                     _ptr(beta_a, ctypes.c_double), int(n_poles), _ptr(de_a, ctypes.c_double),
+                                     int(pole_begin), int(pole_end), int(accumulate), _ptrs(d_dm), _ptrs(d_edm),
+                                     _ptrs(d_fdm), stream or None, infos)
+    _gcheck(rc, group)
+    return None if infos is None else [_as_dict(x) for x in infos]
+
+
+def pexsi_group_dm(group, H, S, mu, beta, n_poles, delta_e):
+    """Host form: H, S lists of float64 arrays (S may be None). Returns
+    (dm, edm, fdm, infos): lists per system."""
+    n = len(H)
+    H = [_f64(h) for h in H]
+    S = None if S is None else [None if x is None else _f64(x) for x in S]
+    outs = [[np.empty(h.shape[0]) for h in H] for _ in range(3)]
+    mu_a, beta_a, de_a = (np.ascontiguousarray(x, dtype=np.float64) for x in (mu, beta, delta_e))
+    infos = (pexsi_dm_info * n)()
+    rc = lib().pexsi_group_dm(group, _ptrs(H), None if S is None else _ptrs(S), _ptr(mu_a, ctypes.c_double),
+                              _ptr(beta_a, ctypes.c_double), int(n_poles), _ptr(de_a, ctypes.c_double),
+                              _ptrs(outs[0]), _ptrs(outs[1]), _ptrs(outs[2]), infos)
+    _gcheck(rc, group)
+    return outs[0], outs[1], outs[2], [_as_dict(x) for x in infos]
+
+
+def pexsi_group_tune(group, dH, dS, mu, beta, n_poles, delta_e, cache_path=None, force=False) -> dict:
+    mu_a, beta_a, de_a = (np.ascontiguousarray(x, dtype=np.float64) for x in (mu, beta, delta_e))
+    sc = pexsi_schedule()
+    rc = lib().pexsi_group_tune(group, _ptrs(dH), None if dS is None else _ptrs(dS), _ptr(mu_a, ctypes.c_double),
+                                _ptr(beta_a, ctypes.c_double), int(n_poles), _ptr(de_a, ctypes.c_double),
+                                None if cache_path is None else str(cache_path).encode(), int(bool(force)),
+                                ctypes.byref(sc))
+    _gcheck(rc, group)
+    return _as_dict(sc)
 
 
 # ---------------------------------------------------------------- mu search

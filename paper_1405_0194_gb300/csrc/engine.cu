@@ -3,6 +3,7 @@
 // selected inversion and the pole sum; inertia shift batches).
 #include <algorithm>
 #include <cfloat>
+#include <cstdio>
 #include <climits>
 #include <cmath>
 #include <complex>
@@ -288,13 +289,13 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
         pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
       }
       if (S > 0) {
-        // Blocks of kOzBlockPanels panels: each panel updates the rest of its
+        // Blocks of p->oz_block (<= kOzBlockPanels) panels: each panel updates the rest of its
         // block (columns before min(cb, s)); after the block's last panel one
         // update with K = the block width covers everything to its right, so
         // that part of the front is read and written once per block instead
         // of once per panel.
         const bool cplx = sizeof(T) == sizeof(double2);
-        const int bw = kOzBlockPanels * b, blk0 = p0 / bw * bw, cb = blk0 + bw;
+        const int bw = p->oz_block * b, blk0 = p0 / bw * bw, cb = blk0 + bw;
         const PanelGeom gb = panel_geom(lv, p0, b, cb);
         double band_fl, band_by, band_slice_by;
         block_band_work(lv, p0, b, cb, es, fl, band_fl, band_by, band_slice_by);
@@ -786,6 +787,138 @@ int selinv_one_herm(const pexsi_plan* p, Workspace& ws, const double2* dH, const
   return PEXSI_OK;
 }
 
+// ------------------------------------------------------------------ groups of systems
+// Several systems side by side in one plan: their fronts are concatenated
+// into one pool and their elimination trees into one forest, so that every
+// launch of the level schedule (block inverses, panel solves, Schur
+// updates, Takahashi steps) covers the fronts of all systems at that height
+// of their trees, for all poles of a wave. Only assembly and the pole sum
+// are per system (each system has its own values, shifts and weights). The
+// poles and the systems are independent (Sec. II.B): the merged forest
+// computes exactly what the systems compute alone.
+Symbolic merge_symbolic(const std::vector<const Symbolic*>& parts) {
+  Symbolic m;
+  int64_t off_n = 0, off_rows = 0, off_pool = 0;
+  int32_t off_super = 0;
+  for (const Symbolic* q : parts) {
+    for (int32_t v : q->perm) m.perm.push_back(v + int32_t(off_n));
+    for (int32_t v : q->iperm) m.iperm.push_back(v + int32_t(off_n));
+    for (int32_t K = 0; K < q->nsuper; ++K) {
+      m.first.push_back(q->first[K] + int32_t(off_n));
+      m.rptr.push_back(q->rptr[K] + off_rows);
+      m.parent.push_back(q->parent[K] >= 0 ? q->parent[K] + off_super : -1);
+      m.height.push_back(q->height[K]);
+      m.front_off.push_back(q->front_off[K] + off_pool);
+    }
+    for (int32_t v : q->rows) m.rows.push_back(v + int32_t(off_n));
+    m.rel.insert(m.rel.end(), q->rel.begin(), q->rel.end());
+    for (int64_t v : q->entry_pos) m.entry_pos.push_back(v + off_pool);
+    for (int64_t v : q->entry_pos_up) m.entry_pos_up.push_back(v + off_pool);
+    m.entry_lower.insert(m.entry_lower.end(), q->entry_lower.begin(), q->entry_lower.end());
+    if (int32_t(m.level_fronts.size()) < q->nlevels) m.level_fronts.resize(q->nlevels);
+    for (int32_t L = 0; L < q->nlevels; ++L)
+      for (int32_t K : q->level_fronts[L]) m.level_fronts[L].push_back(K + off_super);
+    m.nnz += q->nnz;
+    m.nnz_L += q->nnz_L;
+    m.max_front = std::max(m.max_front, q->max_front);
+    m.max_width = std::max(m.max_width, q->max_width);
+    off_n += q->n;
+    off_rows += int64_t(q->rows.size());
+    off_pool += q->front_elems;
+    off_super += q->nsuper;
+  }
+  m.n = off_n;
+  m.nsuper = off_super;
+  m.first.push_back(int32_t(off_n));
+  m.rptr.push_back(off_rows);
+  m.front_off.push_back(off_pool);
+  m.front_elems = off_pool;
+  m.nlevels = int32_t(m.level_fronts.size());
+  return m;
+}
+
+// Poles [begin, end) of every system of a merged plan, in waves of `wave`
+// poles: dH[q], dS[q] (NULL = I) the values of system q, mu[q], beta[q],
+// delta_e[q] its expansion (P poles each), d_dm[q] / d_edm[q] / d_fdm[q] its
+// outputs (any may be NULL). info (nsys entries, NULL = do not wait) gets
+// each system's traces; status rules as dm_range.
+int dm_range_group(const pexsi_plan* p, Workspace& ws, Profiler* prof, int wave, const double* const* dH,
+                   const double* const* dS, const double* mu, const double* beta, int P, const double* delta_e,
+                   int begin, int end, int accumulate, double* const* d_dm, double* const* d_edm, double* const* d_fdm,
+                   pexsi_dm_info* info, const std::vector<int32_t>& f_off, std::string* err) {
+  Profiler& pf = prof ? *prof : g_off;
+  const int nsys = int(p->sys_entry_off.size()) - 1;
+  std::vector<std::vector<std::complex<double>>> z(nsys), wr(nsys), we(nsys), wf(nsys), wd(nsys);
+  for (int q = 0; q < nsys; ++q) {
+    int rc = pole_table(beta[q], delta_e[q], P, mu[q], z[q], wr[q], we[q], wf[q], &wd[q]);
+    if (rc) { *err = "bad pole-expansion parameters of system " + std::to_string(q); return rc; }
+  }
+  cudaStream_t st = ws.stream;
+  const int64_t pool = p->sym.front_elems, nnz_all = p->sym.nnz;
+  wave = std::max(1, std::min(wave > 0 ? wave : ws.batch, ws.batch));
+  if (info) ck(cudaEventRecord(ws.ev0, st), "event");
+  if (!accumulate) reset_status(ws, 0);
+  bool first = true;
+  for (int b0 = begin; b0 < end; b0 += wave) {
+    const int nb = std::min(wave, end - b0);
+    ck(cudaMemsetAsync(ws.F, 0, sizeof(double2) * size_t(pool) * nb, st), "memset(F)");
+    std::vector<BatchShifts> sh(nsys);
+    for (int q = 0; q < nsys; ++q) {
+      sh[q] = make_shifts(z[q], &wr[q], &we[q], &wf[q], b0, nb, &wd[q]);
+      const int64_t a0 = p->sys_asm_off[q], na = p->sys_asm_off[q + 1] - a0;
+      const double* S = dS[q] ? dS[q] : p->d_ident + p->sys_entry_off[q];
+      cudaEvent_t a = pf.begin(st);
+      launch_assemble<double2>(ws.F, dH[q], S, p->d_asm_src + a0, p->d_asm_pos + a0, na, pool, sh[q], st);
+      pf.end(a, P_ASSEMBLE, st, 0.0, double(na) * (32.0 + 16.0 * nb));
+    }
+    factor_batch<double2>(p, ws, ws.F, sh[0], false, pf);
+    selinv_batch(p, ws, sh[0], pf);
+    const int overwrite = (first && !accumulate) ? 1 : 0;
+    for (int q = 0; q < nsys; ++q) {
+      const int64_t e0 = p->sys_entry_off[q], ne = p->sys_entry_off[q + 1] - e0;
+      cudaEvent_t a = pf.begin(st);
+      launch_pole_sum(ws.Y, pool, p->d_entry_pos + e0, ne, sh[q], overwrite, d_dm[q], d_edm[q], d_fdm[q],
+                      ws.out + 3 * nnz_all + e0, st);
+      pf.end(a, P_POLESUM, st, 24.0 * nb * double(ne), double(ne) * (8.0 + 16.0 * nb + 32.0 * (overwrite ? 1 : 2)));
+    }
+    first = false;
+  }
+  ck(cudaGetLastError(), "group pole sum");
+  if (!info) return PEXSI_OK;
+  std::vector<double> tr(4 * size_t(nsys), 0.0);
+  for (int q = 0; q < nsys; ++q) {
+    const int64_t e0 = p->sys_entry_off[q], ne = p->sys_entry_off[q + 1] - e0;
+    const double* S = dS[q] ? dS[q] : p->d_ident + e0;
+    launch_traces(d_dm[q], d_edm[q], d_fdm[q], ws.out + 3 * nnz_all + e0, S, ne, ws.partials, p->trace_blocks,
+                  ws.trace3, st);
+    ck(cudaMemcpyAsync(tr.data() + 4 * q, ws.trace3, 4 * sizeof(double), cudaMemcpyDeviceToHost, st), "trace");
+  }
+  ck(cudaEventRecord(ws.ev1, st), "event");
+  int brk = INT_MAX;
+  ck(cudaMemcpyAsync(&brk, ws.brk, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+  ck(cudaStreamSynchronize(st), "sync");
+  float ms = 0;
+  ck(cudaEventElapsedTime(&ms, ws.ev0, ws.ev1), "event");
+  const int bsys = brk == INT_MAX ? -1 : int(std::upper_bound(f_off.begin(), f_off.end(), brk) - f_off.begin()) - 1;
+  for (int q = 0; q < nsys; ++q) {
+    pexsi_dm_info& in = info[q];
+    std::memset(&in, 0, sizeof(in));
+    in.trace_dm_s = d_dm[q] ? tr[4 * q] : 0.0;
+    in.trace_edm_s = d_edm[q] ? tr[4 * q + 1] : 0.0;
+    in.trace_fdm_s = d_fdm[q] ? tr[4 * q + 2] : 0.0;
+    in.trace_ddm_s = tr[4 * q + 3];
+    in.ms_total = ms;
+    in.n_poles = end - begin;
+    in.breakdown_front = bsys == q ? brk - f_off[q] : -1;
+  }
+  if (split_failed(ws, 0, err, "split-precision GEMM")) return PEXSI_ERR_TIMEOUT;
+  if (brk != INT_MAX) {
+    *err = "zero or tiny pivot in front " + std::to_string(brk - f_off[bsys]) + " of system " + std::to_string(bsys);
+    return PEXSI_ERR_BREAKDOWN;
+  }
+  return PEXSI_OK;
+}
+
 }  // namespace pexsi
 
 using namespace pexsi;
@@ -962,6 +1095,99 @@ int ensure_workspace(pexsi_plan* p) {
   return PEXSI_OK;
 }
 
+// Options of a new plan: defaults for zero fields, then validation.
+int init_opts(pexsi_plan* p, const pexsi_opts* opts) {
+  pexsi_opts_default(&p->opts);
+  if (opts) {
+    p->opts = *opts;
+    pexsi_opts def;
+    pexsi_opts_default(&def);
+    if (p->opts.panel <= 0) p->opts.panel = def.panel;
+    if (p->opts.leaf_cols <= 0) p->opts.leaf_cols = def.leaf_cols;
+  }
+  // the split-precision path tiles the panel as one 64-wide block
+  if (p->opts.panel < 16 || p->opts.panel > 64 || p->opts.split_slices < 0 || p->opts.split_slices > 6 ||
+      p->opts.split_slices == 1 || (p->opts.split_slices > 0 && p->opts.panel != 64))
+    return PEXSI_ERR_INVALID_ARG;
+  if (p->opts.wait_ns < 0 || p->opts.inject < 0 || p->opts.inject > 2) return PEXSI_ERR_INVALID_ARG;
+  p->wait_ns = p->opts.wait_ns > 0 ? uint64_t(p->opts.wait_ns) : 1000000000ull;
+  p->oz_slices = p->opts.split_slices;
+  p->b = p->opts.panel;
+  return PEXSI_OK;
+}
+
+// Device part of a plan whose symbolic structure, options and diagonal
+// entries are set: level schedule, front maps, split-precision layout, the
+// identity overlap and the plan's stream.
+int upload_plan(pexsi_plan* p) {
+  ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
+  ck(configure_kernels(p->b), "cudaFuncSetAttribute");
+  if (p->oz_slices > 0) ck(oz_configure(p->oz_slices), "cudaFuncSetAttribute(split)");
+  const Symbolic& S = p->sym;
+  std::vector<int32_t> hs(S.nsuper), hm(S.nsuper);
+  for (int32_t K = 0; K < S.nsuper; ++K) { hs[K] = S.s(K); hm[K] = S.m(K); }
+  std::vector<int32_t> level_fronts, ea, tile_pref;
+  std::vector<int64_t> part_off;
+  build_levels(p, level_fronts, ea, part_off, tile_pref);
+  for (const Level& lv : p->levels)
+    if (lv.fronts.size() > 65535) {  // grid.y limit of the per-level launches
+      return PEXSI_ERR_INTERNAL;
+    }
+  // assembly list: the lower-triangle copy of each entry; a plan that merges
+  // several systems indexes each system's own value arrays, so the source
+  // index is local to its system, and each system's range of the list is kept
+  std::vector<int64_t> asm_src, asm_pos;
+  if (p->sys_entry_off.empty()) p->sys_entry_off = {0, S.nnz};
+  const size_t nsys = p->sys_entry_off.size() - 1;
+  p->sys_asm_off.assign(nsys + 1, 0);
+  for (size_t q = 0; q < nsys; ++q) {
+    p->sys_asm_off[q] = int64_t(asm_src.size());
+    for (int64_t e = p->sys_entry_off[q]; e < p->sys_entry_off[q + 1]; ++e)
+      if (S.entry_lower[e]) {
+        asm_src.push_back(e - p->sys_entry_off[q]);
+        asm_pos.push_back(S.entry_pos[e]);
+      }
+  }
+  p->sys_asm_off[nsys] = int64_t(asm_src.size());
+  p->nlow = int64_t(asm_src.size());
+  p->d_front_off = dev_upload(S.front_off);
+  p->d_s = dev_upload(hs);
+  p->d_m = dev_upload(hm);
+  p->d_parent = dev_upload(S.parent);
+  p->d_rptr = dev_upload(S.rptr);
+  p->d_rel = dev_upload(S.rel);
+  p->d_asm_src = dev_upload(asm_src);
+  p->d_asm_pos = dev_upload(asm_pos);
+  p->d_entry_pos = dev_upload(S.entry_pos);
+  p->d_level_fronts = dev_upload(level_fronts);
+  p->d_ea = dev_upload(ea);
+  p->d_tile_pref = dev_upload(tile_pref);
+  p->d_part_off = dev_upload(part_off);
+  if (p->oz_slices > 0) {
+    std::vector<int64_t> oa, ob, xa, xb, ra, rb;
+    build_split_layout(p, oa, ob, xa, xb, ra, rb);
+    p->d_ozA_off = dev_upload(oa);
+    p->d_ozB_off = dev_upload(ob);
+    p->d_ozA_off_r = dev_upload(ra);
+    p->d_ozB_off_r = dev_upload(rb);
+    p->d_exA_off = dev_upload(xa);
+    p->d_exB_off = dev_upload(xb);
+    std::vector<int64_t> yo(S.nsuper);
+    for (int64_t K = 0; K < S.nsuper; ++K) {
+      yo[K] = p->ymax_stride;
+      p->ymax_stride += S.m(K);
+    }
+    p->d_ymax_off = dev_upload(yo);
+  }
+  {
+    std::vector<double> ident(S.nnz, 0.0);  // S = I on the pattern
+    for (int64_t e : p->diag_entries) ident[e] = 1.0;
+    p->d_ident = dev_upload(ident);
+  }
+  ck(cudaStreamCreateWithFlags(&p->ws.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  return PEXSI_OK;
+}
+
 }  // namespace
 
 int pexsi::plan_workspace(pexsi_plan* p) { return ensure_workspace(p); }
@@ -1101,96 +1327,31 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
   pexsi_plan* p = nullptr;
   try {
     p = new pexsi_plan();
-    pexsi_opts_default(&p->opts);
-    if (opts) {
-      p->opts = *opts;
-      pexsi_opts def;
-      pexsi_opts_default(&def);
-      if (p->opts.panel <= 0) p->opts.panel = def.panel;
-      if (p->opts.leaf_cols <= 0) p->opts.leaf_cols = def.leaf_cols;
-    }
-    // the split-precision path tiles the panel as one 64-wide block
-    if (p->opts.panel < 16 || p->opts.panel > 64 || p->opts.split_slices < 0 || p->opts.split_slices > 6 ||
-        p->opts.split_slices == 1 || (p->opts.split_slices > 0 && p->opts.panel != 64)) {
+    int rc = init_opts(p, opts);
+    if (rc) {
       delete p;
-      return PEXSI_ERR_INVALID_ARG;
+      return rc;
     }
-    if (p->opts.wait_ns < 0 || p->opts.inject < 0 || p->opts.inject > 2) {
-      delete p;
-      return PEXSI_ERR_INVALID_ARG;
-    }
-    p->wait_ns = p->opts.wait_ns > 0 ? uint64_t(p->opts.wait_ns) : 1000000000ull;
-    p->oz_slices = p->opts.split_slices;
-    p->b = p->opts.panel;
     std::string err;
-    int rc = analyse(n, colptr, rowind, perm_or_null, p->opts.leaf_cols, p->opts.amalgamate != 0, p->sym, err);
+    rc = analyse(n, colptr, rowind, perm_or_null, p->opts.leaf_cols, p->opts.amalgamate != 0, p->sym, err);
     if (rc) {
       delete p;
       return rc;
     }
     p->flops = count_flops(p->sym, p->b);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e)
+        if (rowind[e] == j) p->diag_entries.push_back(e);
     if (p->opts.device < 0) {  // host-only plan: symbolic analysis only
       *out = p;
       return PEXSI_OK;
     }
-    ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
-    ck(configure_kernels(p->b), "cudaFuncSetAttribute");
-    if (p->oz_slices > 0) ck(oz_configure(p->oz_slices), "cudaFuncSetAttribute(split)");
-    const Symbolic& S = p->sym;
-    std::vector<int32_t> hs(S.nsuper), hm(S.nsuper);
-    for (int32_t K = 0; K < S.nsuper; ++K) { hs[K] = S.s(K); hm[K] = S.m(K); }
-    std::vector<int32_t> level_fronts, ea, tile_pref;
-    std::vector<int64_t> part_off;
-    build_levels(p, level_fronts, ea, part_off, tile_pref);
-    for (const Level& lv : p->levels)
-      if (lv.fronts.size() > 65535) {  // grid.y limit of the per-level launches
-        delete p;
-        return PEXSI_ERR_INTERNAL;
-      }
-    std::vector<int64_t> asm_src, asm_pos;
-    for (int64_t e = 0; e < S.nnz; ++e)
-      if (S.entry_lower[e]) { asm_src.push_back(e); asm_pos.push_back(S.entry_pos[e]); }
-    p->nlow = int64_t(asm_src.size());
-    p->d_front_off = dev_upload(S.front_off);
-    p->d_s = dev_upload(hs);
-    p->d_m = dev_upload(hm);
-    p->d_parent = dev_upload(S.parent);
-    p->d_rptr = dev_upload(S.rptr);
-    p->d_rel = dev_upload(S.rel);
-    p->d_asm_src = dev_upload(asm_src);
-    p->d_asm_pos = dev_upload(asm_pos);
-    p->d_entry_pos = dev_upload(S.entry_pos);
-    p->d_level_fronts = dev_upload(level_fronts);
-    p->d_ea = dev_upload(ea);
-    p->d_tile_pref = dev_upload(tile_pref);
-    p->d_part_off = dev_upload(part_off);
-    if (p->oz_slices > 0) {
-      std::vector<int64_t> oa, ob, xa, xb, ra, rb;
-      build_split_layout(p, oa, ob, xa, xb, ra, rb);
-      p->d_ozA_off = dev_upload(oa);
-      p->d_ozB_off = dev_upload(ob);
-      p->d_ozA_off_r = dev_upload(ra);
-      p->d_ozB_off_r = dev_upload(rb);
-      p->d_exA_off = dev_upload(xa);
-      p->d_exB_off = dev_upload(xb);
-      std::vector<int64_t> yo(S.nsuper);
-      for (int64_t K = 0; K < S.nsuper; ++K) {
-        yo[K] = p->ymax_stride;
-        p->ymax_stride += S.m(K);
-      }
-      p->d_ymax_off = dev_upload(yo);
+    rc = upload_plan(p);
+    if (rc) {
+      free_plan_device(p);
+      delete p;
+      return rc;
     }
-    {
-      std::vector<double> ident(S.nnz, 0.0);  // S = I on the pattern
-      for (int64_t j = 0; j < n; ++j)
-        for (int64_t e = colptr[j]; e < colptr[j + 1]; ++e)
-          if (rowind[e] == j) {
-            ident[e] = 1.0;
-            p->diag_entries.push_back(e);
-          }
-      p->d_ident = dev_upload(ident);
-    }
-    ck(cudaStreamCreateWithFlags(&p->ws.stream, cudaStreamNonBlocking), "cudaStreamCreate");
     *out = p;
     return PEXSI_OK;
   } catch (const CudaError&) {
@@ -1478,5 +1639,312 @@ int pexsi_inertia_hermitian(pexsi_plan* p, const double* H, const double* S, con
     return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
   }
 }
+
+// ---------------------------------------------------------------- groups of systems
+}  // extern "C"
+
+struct pexsi_group {
+  pexsi_plan* p = nullptr;      // merged plan over all systems (owns the device memory)
+  int nsys = 0;
+  std::vector<int32_t> f_off;   // first merged front of each system (nsys + 1)
+  int wave = 0;                 // poles per wave (0 = the workspace's batch)
+  std::string fingerprint;      // key of the tuned schedule in a cache file
+};
+
+namespace {
+
+std::string group_fingerprint(const pexsi_group* g) {
+  int dev = g->p->opts.device, sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string f = "sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "x" + std::to_string(sms) +
+                  "/split" + std::to_string(g->p->oz_slices) + "/b" + std::to_string(g->p->b) + "/batch" +
+                  std::to_string(g->p->ws.batch);
+  const Symbolic& S = g->p->sym;
+  for (int q = 0; q < g->nsys; ++q) {
+    int64_t fe = 0, nl = 0;
+    for (int32_t K = g->f_off[q]; K < g->f_off[q + 1]; ++K) {
+      fe += int64_t(S.m(K)) * S.m(K);
+      nl += S.s(K);
+    }
+    f += "/" + std::to_string(nl) + ":" + std::to_string(g->p->sys_entry_off[q + 1] - g->p->sys_entry_off[q]) + ":" +
+         std::to_string(g->f_off[q + 1] - g->f_off[q]) + ":" + std::to_string(fe);
+  }
+  return f;
+}
+
+bool cache_lookup(const char* path, const std::string& key, int& wave, int& block, double& ms) {
+  if (!path) return false;
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return false;
+  char line[4096];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), fh)) {
+    char k[3000];
+    int w = 0, b = 0;
+    double t = 0;
+    if (std::sscanf(line, "%2999s wave=%d block=%d ms_per_pole=%lf", k, &w, &b, &t) == 4 && key == k && w > 0 &&
+        b >= 1 && b <= kOzBlockPanels) {
+      wave = w;
+      block = b;
+      ms = t;
+      found = true;  // the last entry for the key wins
+    }
+  }
+  std::fclose(fh);
+  return found;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pexsi_group_create(const pexsi_plan* const* plans, int32_t n_plans, const pexsi_opts* opts, pexsi_group** out) {
+  if (!out || !plans || n_plans <= 0) return PEXSI_ERR_INVALID_ARG;
+  *out = nullptr;
+  pexsi_group* g = nullptr;
+  try {
+    g = new pexsi_group();
+    g->p = new pexsi_plan();
+    pexsi_plan* p = g->p;
+    int rc = init_opts(p, opts);
+    if (rc == PEXSI_OK && p->opts.device < 0) rc = PEXSI_ERR_INVALID_ARG;
+    std::vector<const Symbolic*> parts;
+    for (int q = 0; q < n_plans && rc == PEXSI_OK; ++q) {
+      if (!plans[q] || plans[q]->b != p->b) rc = PEXSI_ERR_INVALID_ARG;
+      else parts.push_back(&plans[q]->sym);
+    }
+    if (rc) {
+      delete g->p;
+      delete g;
+      return rc;
+    }
+    g->nsys = n_plans;
+    p->sym = merge_symbolic(parts);
+    p->flops = count_flops(p->sym, p->b);
+    p->sys_entry_off.assign(1, 0);
+    g->f_off.assign(1, 0);
+    for (int q = 0; q < n_plans; ++q) {
+      for (int64_t e : plans[q]->diag_entries) p->diag_entries.push_back(e + p->sys_entry_off.back());
+      p->sys_entry_off.push_back(p->sys_entry_off.back() + plans[q]->sym.nnz);
+      g->f_off.push_back(g->f_off.back() + plans[q]->sym.nsuper);
+    }
+    rc = upload_plan(p);
+    if (rc == PEXSI_OK) rc = ensure_workspace(p);
+    if (rc) {
+      free_plan_device(p);
+      delete p;
+      delete g;
+      return rc;
+    }
+    g->fingerprint = group_fingerprint(g);
+    *out = g;
+    return PEXSI_OK;
+  } catch (const CudaError&) {
+    if (g) { if (g->p) { free_plan_device(g->p); delete g->p; } delete g; }
+    return PEXSI_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    if (g) { if (g->p) { free_plan_device(g->p); delete g->p; } delete g; }
+    return PEXSI_ERR_NOMEM;
+  }
+}
+
+int pexsi_group_destroy(pexsi_group* g) {
+  if (!g) return PEXSI_OK;
+  pexsi_plan_destroy(g->p);
+  delete g;
+  return PEXSI_OK;
+}
+
+int pexsi_group_get_stats(const pexsi_group* g, pexsi_plan_stats* st) {
+  if (!g) return PEXSI_ERR_INVALID_ARG;
+  return pexsi_plan_get_stats(g->p, st);
+}
+
+int pexsi_group_get_schedule(const pexsi_group* g, pexsi_schedule* out) {
+  if (!g || !out) return PEXSI_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->wave = g->wave > 0 ? g->wave : g->p->ws.batch;
+  out->oz_block = g->p->oz_block;
+  return PEXSI_OK;
+}
+
+int pexsi_group_set_schedule(pexsi_group* g, const pexsi_schedule* sc) {
+  if (!g || !sc || sc->wave < 0 || sc->wave > g->p->ws.batch || sc->oz_block < 1 || sc->oz_block > kOzBlockPanels)
+    return PEXSI_ERR_INVALID_ARG;
+  g->wave = sc->wave;
+  g->p->oz_block = sc->oz_block;
+  return PEXSI_OK;
+}
+
+int pexsi_group_dm_device(pexsi_group* g, const double* const* dH, const double* const* dS, const double* mu,
+                          const double* beta, int32_t n_poles, const double* delta_e, int32_t pole_begin,
+                          int32_t pole_end, int32_t accumulate, double* const* d_dm, double* const* d_edm,
+                          double* const* d_fdm, void* stream, pexsi_dm_info* info) {
+  if (!g || !dH || !mu || !beta || !delta_e || !d_dm || !d_edm || !d_fdm) return PEXSI_ERR_INVALID_ARG;
+  pexsi_plan* p = g->p;
+  for (int q = 0; q < g->nsys; ++q)
+    if (!dH[q]) return fail(p, PEXSI_ERR_INVALID_ARG, "NULL H of system " + std::to_string(q));
+  if (pole_begin < 0 || pole_end > n_poles || pole_begin >= pole_end)
+    return fail(p, PEXSI_ERR_INVALID_ARG, "bad pole range");
+  std::vector<const double*> S(g->nsys, nullptr);
+  if (dS)
+    for (int q = 0; q < g->nsys; ++q) S[q] = dS[q];
+  try {
+    ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
+    std::string err;
+    int rc = on_stream(p, stream, [&] {
+      return dm_range_group(p, p->ws, &p->prof, g->wave, dH, S.data(), mu, beta, n_poles, delta_e, pole_begin,
+                            pole_end, accumulate, d_dm, d_edm, d_fdm, info, g->f_off, &err);
+    });
+    return rc ? fail(p, rc, err) : PEXSI_OK;
+  } catch (const CudaError& ce) {
+    return map_cuda(p, ce);
+  } catch (const std::bad_alloc&) {
+    return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int pexsi_group_dm(pexsi_group* g, const double* const* H, const double* const* S, const double* mu,
+                   const double* beta, int32_t n_poles, const double* delta_e, double* const* dm, double* const* edm,
+                   double* const* fdm, pexsi_dm_info* info) {
+  if (!g || !H || !mu || !beta || !delta_e || !dm || !edm || !fdm) return PEXSI_ERR_INVALID_ARG;
+  pexsi_plan* p = g->p;
+  try {
+    ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
+    Workspace& ws = p->ws;
+    const int64_t all = p->sym.nnz;
+    const int n = g->nsys;
+    std::vector<const double*> dH(n), dS(n, nullptr);
+    std::vector<double*> o[3];
+    for (int k = 0; k < 3; ++k) o[k].assign(n, nullptr);
+    double* const* want[3] = {dm, edm, fdm};
+    for (int q = 0; q < n; ++q) {
+      if (!H[q]) return fail(p, PEXSI_ERR_INVALID_ARG, "NULL H of system " + std::to_string(q));
+      const int64_t e0 = p->sys_entry_off[q], ne = p->sys_entry_off[q + 1] - e0;
+      ck(cudaMemcpyAsync(ws.H + e0, H[q], sizeof(double) * ne, cudaMemcpyHostToDevice, ws.stream), "H2D(H)");
+      dH[q] = ws.H + e0;
+      if (S && S[q]) {
+        ck(cudaMemcpyAsync(ws.S + e0, S[q], sizeof(double) * ne, cudaMemcpyHostToDevice, ws.stream), "H2D(S)");
+        dS[q] = ws.S + e0;
+      }
+      for (int k = 0; k < 3; ++k) o[k][q] = want[k][q] ? ws.out + k * all + e0 : nullptr;
+    }
+    std::vector<pexsi_dm_info> local(n);
+    std::string err;
+    int rc = dm_range_group(p, ws, &p->prof, g->wave, dH.data(), dS.data(), mu, beta, n_poles, delta_e, 0, n_poles, 0,
+                            o[0].data(), o[1].data(), o[2].data(), local.data(), g->f_off, &err);
+    if (info)
+      for (int q = 0; q < n; ++q) info[q] = local[q];
+    if (rc) return fail(p, rc, err);
+    for (int q = 0; q < n; ++q) {
+      const int64_t e0 = p->sys_entry_off[q], ne = p->sys_entry_off[q + 1] - e0;
+      for (int k = 0; k < 3; ++k)
+        if (want[k][q])
+          ck(cudaMemcpyAsync(want[k][q], ws.out + k * all + e0, sizeof(double) * ne, cudaMemcpyDeviceToHost,
+                             ws.stream), "D2H");
+    }
+    ck(cudaStreamSynchronize(ws.stream), "sync");
+    return PEXSI_OK;
+  } catch (const CudaError& ce) {
+    return map_cuda(p, ce);
+  } catch (const std::bad_alloc&) {
+    return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+// The schedule tuner: times every candidate (wave, oz_block) on the device on
+// the group's own inputs (poles [0, wave) of each system, after one untimed
+// run of the first candidate), keeps the one with the least time per pole,
+// and appends it to the cache file under the group's fingerprint (device,
+// precision, batch capacity, the systems' sizes and front structure). A
+// later call finds it there and times nothing (force = 1 re-times).
+int pexsi_group_tune(pexsi_group* g, const double* const* dH, const double* const* dS, const double* mu,
+                     const double* beta, int32_t n_poles, const double* delta_e, const char* cache_path,
+                     int32_t force, pexsi_schedule* out) {
+  if (!g || !dH || !mu || !beta || !delta_e) return PEXSI_ERR_INVALID_ARG;
+  pexsi_plan* p = g->p;
+  int wave = 0, block = 0;
+  double ms = 0;
+  if (!force && cache_lookup(cache_path, g->fingerprint, wave, block, ms) && wave <= p->ws.batch) {
+    g->wave = wave;
+    p->oz_block = block;
+    if (out) {
+      std::memset(out, 0, sizeof(*out));
+      out->wave = wave;
+      out->oz_block = block;
+      out->ms_per_pole = ms;
+      out->from_cache = 1;
+    }
+    return PEXSI_OK;
+  }
+  try {
+    ck(cudaSetDevice(p->opts.device), "cudaSetDevice");
+    Workspace& ws = p->ws;
+    const int n = g->nsys;
+    const int64_t all = p->sym.nnz;
+    std::vector<const double*> S(n, nullptr);
+    std::vector<double*> o[3];
+    for (int k = 0; k < 3; ++k) {
+      o[k].assign(n, nullptr);
+      for (int q = 0; q < n; ++q) o[k][q] = ws.out + k * all + p->sys_entry_off[q];
+    }
+    if (dS)
+      for (int q = 0; q < n; ++q) S[q] = dS[q];
+    std::vector<int> waves;
+    for (int w = p->ws.batch; w >= 1 && waves.size() < 3; w /= 2) {
+      if (w > n_poles) continue;
+      waves.push_back(w);
+    }
+    if (waves.empty()) waves.push_back(std::min(p->ws.batch, int(n_poles)));
+    std::vector<int> blocks = p->oz_slices > 0 ? std::vector<int>{4, 2, 1} : std::vector<int>{p->oz_block};
+    std::vector<pexsi_dm_info> info(n);
+    std::string err;
+    double best = 1e300;
+    int bw = waves[0], bb = blocks[0], cands = 0;
+    bool warmed = false;
+    for (int w : waves)
+      for (int blk : blocks) {
+        p->oz_block = blk;
+        for (int rep = warmed ? 0 : 1; rep >= 0; --rep) {  // one untimed run before the first timing
+          int rc = dm_range_group(p, ws, nullptr, w, dH, S.data(), mu, beta, n_poles, delta_e, 0, w, 0, o[0].data(),
+                                  o[1].data(), o[2].data(), info.data(), g->f_off, &err);
+          if (rc) return fail(p, rc, err);
+        }
+        warmed = true;
+        ++cands;
+        const double per = info[0].ms_total / w;
+        if (per < best) {
+          best = per;
+          bw = w;
+          bb = blk;
+        }
+      }
+    g->wave = bw;
+    p->oz_block = bb;
+    if (cache_path) {
+      FILE* fh = std::fopen(cache_path, "a");
+      if (fh) {
+        std::fprintf(fh, "%s wave=%d block=%d ms_per_pole=%.6f\n", g->fingerprint.c_str(), bw, bb, best);
+        std::fclose(fh);
+      }
+    }
+    if (out) {
+      std::memset(out, 0, sizeof(*out));
+      out->wave = bw;
+      out->oz_block = bb;
+      out->ms_per_pole = best;
+      out->candidates = cands;
+    }
+    return PEXSI_OK;
+  } catch (const CudaError& ce) {
+    return map_cuda(p, ce);
+  } catch (const std::bad_alloc&) {
+    return fail(p, PEXSI_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+const char* pexsi_group_last_error_detail(const pexsi_group* g) { return g ? g->p->last_error.c_str() : ""; }
 
 }  // extern "C"

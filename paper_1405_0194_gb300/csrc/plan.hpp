@@ -121,6 +121,7 @@ struct pexsi_plan {
   // split-precision scratch layout (per front offsets within a level; strides
   // per batch member): slice tiles of A and B, exponents of A rows, B columns
   int oz_slices = 0;
+  int oz_block = pexsi::kOzBlockPanels;  // panels per block of the split Schur update (1..kOzBlockPanels; tunable)
   int64_t *d_ozA_off = nullptr, *d_ozB_off = nullptr, *d_exA_off = nullptr, *d_exB_off = nullptr;
   int64_t* d_ymax_off = nullptr;  // first row of each front among all fronts' rows
   int64_t ymax_stride = 0;        // sum of m_K
@@ -139,6 +140,10 @@ struct pexsi_plan {
   // identity S, and the plan API's complex staging (H, S: nnz; outputs: 4 nnz)
   int64_t *d_pos_full = nullptr, *d_pos_t = nullptr;
   std::vector<int64_t> diag_entries;  // CSC entries on the diagonal
+  // A plan that merges several systems (pexsi_group): the first CSC entry of
+  // each system among the concatenated entries (nsys + 1), and each system's
+  // range of the assembly list; {0, nnz} and {0, nlow} for a single system.
+  std::vector<int64_t> sys_entry_off, sys_asm_off;
   double2 *d_ident_c = nullptr, *d_hH = nullptr, *d_hS = nullptr, *d_hout = nullptr;
 
   pexsi::DevFronts fronts() const {
@@ -194,6 +199,14 @@ int selinv_one_herm(const pexsi_plan* p, Workspace& ws, const double2* dH, const
 int dm_range_herm(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double2* dH, const double2* dS, double mu,
                   double beta, int P, double delta_e, int begin, int end, int accumulate, double2* d_dm,
                   double2* d_edm, double2* d_fdm, pexsi_dm_info* info, std::string* err);
+
+// Groups of systems (one merged plan): the symbolic structures side by side,
+// and the batched driver over all systems' poles.
+Symbolic merge_symbolic(const std::vector<const Symbolic*>& parts);
+int dm_range_group(const pexsi_plan* p, Workspace& ws, Profiler* prof, int wave, const double* const* dH,
+                   const double* const* dS, const double* mu, const double* beta, int P, const double* delta_e,
+                   int begin, int end, int accumulate, double* const* d_dm, double* const* d_edm, double* const* d_fdm,
+                   pexsi_dm_info* info, const std::vector<int32_t>& f_off, std::string* err);
 
 // Selected inverse of one complex shift into d_ainv (device, nnz complex);
 // synchronises ws.stream.
