@@ -461,8 +461,11 @@ def run_ours(args):
     if args.split_compare > 0 and args.split == 0 and world == 1:
         line["split_path"] = split_path(px, s, mu, dE, local, dH, dS, stream, args, per60, all_shifts, ref_dm,
                                         heavy, eig, peaks)
+    if world == 1 and args.batched_passes > 0:
+        line["batched_split"] = batched_systems(px, local, args.split_compare or 6, args.batched_passes)
     if world == 1 and args.serve_requests > 0:
-        line["serving"] = serve_trace(px, local, args.serve_rate, args.serve_requests)
+        line["serving"] = serve_trace(px, local, args.serve_rate, args.serve_requests, args.serve_set,
+                                      args.serve_fp64_budget, capacity_frac=args.serve_capacity_frac)
     if world == 1 and not args.no_cpu_baseline:
         rng = np.random.default_rng(1)
         est, wall = oracle_pole_sample(s, mu, dE, 0, args.cpu_cols, rng)
@@ -562,65 +565,225 @@ def split_path(px, s, mu, dE, device, dH, dS, stream, args, per60, all_shifts, r
     return res
 
 
-# ------------------------------------------------------------------ serving trace
-SERVE_SYSTEMS = [
-    ("sheet8x8", lambda: ns.make_sheet(ncell=8, seed=11)),
-    ("fluid64", lambda: ns.make_fluid(nmol=64, seed=12)),
-    ("chain256", lambda: ns.make_chain(natoms=256, seed=13, norb=4)),
-]
+# ------------------------------------------------------------------ batched systems
+BATCHED = [("chain500", lambda: ns.make_chain(natoms=500, seed=21)),
+           ("fluid96", lambda: ns.make_fluid(nmol=96, seed=22)),
+           ("sheet14", lambda: ns.make_sheet(ncell=14, seed=23)),
+           ("fluid384", lambda: ns.make_fluid(nmol=384, seed=24)),
+           ("sheet23", lambda: ns.make_sheet(ncell=23, seed=25)),
+           ("chain7500", lambda: ns.make_chain(natoms=7500, seed=26))]
 
 
-def serve_trace(px, device, rate, n_req, seed=0):
-    """Seeded Poisson trace of mu-search-shaped requests (8 inertia shifts then
-    one 60-pole DM) over three system sizes with per-request mu and beta
-    jitter, through the request server twice: continuous batching (4 slots,
-    8-pole device batches) and the plain per-pole path (1 slot, 1 pole per
-    batch). Returns p50 / p99 latency and throughput of both."""
-    rng = np.random.default_rng(seed)
+def batched_systems(px, device, split, passes, P=64):
+    """Six systems of uneven size (chain, sheet and bulk recipes, n = 2,000
+    to 30,000), P = 64 poles each, split precision, in one group: every
+    level launch covers the fronts of all six systems for a wave of poles,
+    the schedule (wave, Schur block width) chosen by the group's tuner.
+    Reported against the same systems run one after another on their own
+    plans, with each system's deviation from the FP64 path on the poles next
+    to the real axis, and from the oracle's closed form for the two smallest."""
+    import torch
+    from oracle import dense, poles as opoles
     systems = []
-    for name, make in SERVE_SYSTEMS:
+    for name, make in BATCHED:
         s = make()
         mu, dE = ns.mu_and_delta_e(s)
-        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=device))
-        systems.append((name, s, mu, dE, plan))
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        systems.append((name, s, mu, dE))
+    dev = torch.device("cuda", device)
+    dH = [torch.from_numpy(s.H).to(dev) for _, s, _, _ in systems]
+    dS = [torch.from_numpy(s.S).to(dev) for _, s, _, _ in systems]
+    outs = [torch.zeros(3, s.nnz, dtype=torch.float64, device=dev) for _, s, _, _ in systems]
+    st = torch.cuda.current_stream(dev).cuda_stream
+    common = ([h.data_ptr() for h in dH], [x.data_ptr() for x in dS], [m for _, _, m, _ in systems],
+              [s.beta for _, s, _, _ in systems], P, [d for _, _, _, d in systems])
+    ptrs = ([o[0].data_ptr() for o in outs], [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs])
+
+    def group_of(split_):
+        plans = [px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=-1))
+                 for _, s, _, _ in systems]
+        g = px.pexsi_group_create(plans, opts=px.pexsi_opts_default(device=device, split_slices=split_))
+        for p in plans:
+            px.pexsi_plan_destroy(p)
+        return g
+
+    g = group_of(split)
+    cache = os.path.join(tempfile.gettempdir(), "pexsi_gb300_schedules.txt")
+    t0 = time.perf_counter()
+    sched = px.pexsi_group_tune(g, *common, cache_path=cache)
+    tune_s = time.perf_counter() - t0
+    px.pexsi_group_dm_device(g, *common, 0, P, 0, *ptrs, st, want_info=True)  # warm-up pass
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(passes):
+        px.pexsi_group_dm_device(g, *common, 0, P, 0, *ptrs, st)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_group = e0.elapsed_time(e1) / passes
+    stats = px.pexsi_group_get_stats(g)
+    # poles next to the real axis on the occupied side, for the error checks
+    lo, hi = P - 4, P
+    px.pexsi_group_dm_device(g, *common, lo, hi, 0, *ptrs, st, want_info=True)
+    split_near = [o.cpu().numpy() for o in outs]
+    px.pexsi_group_destroy(g)
+    # the same systems one after another, each on its own plan
+    seq_ms = []
+    for q, (name, s, mu, dE) in enumerate(systems):
+        plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=device, split_slices=split))
+        o = outs[q]
+        args = (plan, dH[q].data_ptr(), dS[q].data_ptr(), mu, s.beta, P, dE)
+        px.pexsi_dm_device(*args, 0, min(P, 8), 0, o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), st,
+                           want_info=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        px.pexsi_dm_device(*args, 0, P, 0, o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), st)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        seq_ms.append(e0.elapsed_time(e1))
+        px.pexsi_plan_destroy(plan)
+    # FP64 path on the same poles
+    g = group_of(0)
+    px.pexsi_group_dm_device(g, *common, lo, hi, 0, *ptrs, st, want_info=True)
+    fp64_near = [o.cpu().numpy() for o in outs]
+    px.pexsi_group_destroy(g)
+    errs = {}
+    for q, (name, s, mu, dE) in enumerate(systems):
+        d = float(np.max(np.abs(split_near[q] - fp64_near[q])))
+        errs[name] = {"n": s.n, "vs_fp64_path_max_abs": d,
+                      "rel_to_max_entry": d / float(np.max(np.abs(fp64_near[q][0])))}
+        if s.n <= 2300:
+            lam, C = dense.eig_pencil(s.n, s.colptr, s.rowind, s.H, s.S)
+            tab = opoles.pole_table(s.beta, dE, P, mu)
+            cols = np.sort(np.random.default_rng(0).choice(s.n, 8, replace=False))
+            ref = dense.dm_columns_eig(lam, C, s.colptr, s.rowind, tab, cols, range(lo, hi))
+            errs[name]["vs_oracle_sampled_max_abs"] = max(
+                float(np.max(np.abs(split_near[q][k, s.colptr[j]:s.colptr[j + 1]] - ref[j][k])))
+                for j in cols for k in range(3))
+    solves = P * len(systems)
+    return {"workload": "6 systems, 64 poles each: " + ", ".join(f"{nm} (n={s.n})" for nm, s, _, _ in systems),
+            "split_slices": split, "pole_solves_per_pass": solves,
+            "group": {"value": solves / (ms_group / 1e3), "unit": "pole-solves/s", "ms_per_pass": ms_group,
+                      "passes": passes},
+            "one_after_another": {"value": solves / (sum(seq_ms) / 1e3), "unit": "pole-solves/s",
+                                  "ms_per_system": dict(zip([nm for nm, *_ in systems], [round(x, 1) for x in seq_ms]))},
+            "speedup": sum(seq_ms) / ms_group,
+            "schedule": sched, "tune_seconds": round(tune_s, 2), "front_elems": stats["front_elems"],
+            "batch_capacity": stats["batch"],
+            "error_poles": f"{lo}..{hi - 1} of each 64-pole table (occupied side, next to the real axis)",
+            "error": errs}
+
+
+# ------------------------------------------------------------------ serving trace
+SERVE_SETS = {
+    # the serving sizes: 2D and 3D recipes at n = 3.7k, 12k and 27k
+    "config": [("sheet12x12", lambda: ns.make_sheet(ncell=12, seed=11)),
+               ("fluid512", lambda: ns.make_fluid(nmol=512, seed=12)),
+               ("sheet32x32", lambda: ns.make_sheet(ncell=32, seed=13))],
+    # a small set that keeps the default benchmark short
+    "small": [("sheet12x12", lambda: ns.make_sheet(ncell=12, seed=11)),
+              ("fluid128", lambda: ns.make_fluid(nmol=128, seed=12)),
+              ("chain1000", lambda: ns.make_chain(natoms=1000, seed=13, norb=4))],
+}
+
+
+def serve_trace(px, device, rate, n_req, which="small", fp64_budget_s=60.0, seed=0, capacity_frac=None):
+    """Seeded Poisson trace of mu-search-shaped requests (8 inertia shifts,
+    then one 60-pole DM) over the systems of SERVE_SETS[which], with
+    per-request mu (+-0.05 Ha) and beta (+-10%) jitter, through the request
+    server twice:
+      split  -- continuous batching (4 slots, 8-pole device batches), plans
+                with the split-precision GEMMs (6 bf16 slices);
+      fp64   -- the plain per-pole FP64 path (1 slot, 1 pole per batch).
+    The FP64 arm stops at fp64_budget_s of wall time: requests still queued or
+    running are cancelled and enter its p50 / p99 at the budget, so its
+    latencies are lower bounds. With capacity_frac the rate is that fraction
+    of the split arm's measured capacity (requests/s of a first pass).
+    Three requests of the split arm are replayed alone: results identical to
+    the mix (deterministic kernels)."""
+    rng = np.random.default_rng(seed)
+    systems = []
+    for name, make in SERVE_SETS[which]:
+        s = make()
+        mu, dE = ns.mu_and_delta_e(s)
+        plans = {k: px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(device=device, split_slices=k))
+                 for k in (0, 6)}
+        systems.append((name, s, mu, dE, plans))
+    gaps = rng.exponential(1.0, n_req)
     picks = rng.integers(0, len(systems), n_req)
     jit_mu = rng.uniform(-0.05, 0.05, n_req)
     jit_beta = rng.uniform(0.9, 1.1, n_req)
 
-    def run(slots, batch):
+    def request(k, split):
+        name, s, mu, dE, plans = systems[picks[k]]
+        m = mu + jit_mu[k]
+        return px.ServerRequest(plans[split], s.H, s.S, mu=m, beta=s.beta * jit_beta[k], n_poles=60,
+                                delta_e=dE + 0.05, shifts=m + np.linspace(-0.2, 0.2, 8) + 1.0e-4)
+
+    def run(slots, batch, split, rate_, budget=None, only=None):
+        arrivals = np.cumsum(gaps / rate_)
+        idx = list(range(n_req)) if only is None else only
         server = px.pexsi_server_create(px.pexsi_server_opts_default(device=device, slots=slots, batch=batch))
         reqs = []
         t0 = time.perf_counter()
-        for k in range(n_req):
-            while time.perf_counter() - t0 < arrivals[k]:
-                time.sleep(0.0005)
-            name, s, mu, dE, plan = systems[picks[k]]
-            m = mu + jit_mu[k]
-            r = px.ServerRequest(plan, s.H, s.S, mu=m, beta=s.beta * jit_beta[k], n_poles=60, delta_e=dE + 0.05,
-                                 shifts=m + np.linspace(-0.2, 0.2, 8) + 1.0e-4)
+        for k in idx:
+            if only is None:
+                while time.perf_counter() - t0 < arrivals[k]:
+                    time.sleep(0.0005)
+            r = request(k, split)
             px.pexsi_server_submit(server, r)
             reqs.append(r)
-        res = [px.pexsi_server_wait(server, r.ticket) for r in reqs]
+        res = []
+        cancelled = False
+        for r in reqs:
+            while True:
+                x = px.pexsi_server_poll(server, r.ticket)
+                if x is not None:
+                    break
+                if budget is not None and not cancelled and time.perf_counter() - t0 > budget:
+                    for q in reqs:  # everything unfinished at the budget
+                        try:
+                            px.pexsi_server_cancel(server, q.ticket)
+                        except px.PexsiError:
+                            pass  # finished in the meantime
+                    cancelled = True
+                time.sleep(0.002)
+            res.append(x)
         wall = time.perf_counter() - t0
         st = px.pexsi_server_get_stats(server)
         px.pexsi_server_destroy(server)
-        lat = np.array([x["latency_ms"] for x in res])
-        ok = all(x["status"] == 0 for x in res)
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "throughput_req_s": n_req / wall, "pole_solves_s": 60 * n_req / wall,
-                "peak_concurrent": st["peak_concurrent"], "all_ok": ok}, reqs
+        done = [x for x in res if x["status"] == 0]
+        cut = [x for x in res if x["status"] == -7]
+        lat = np.array([x["latency_ms"] if x["status"] == 0 else 1e3 * budget for x in res if x["status"] in (0, -7)])
+        return {"p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                "completed": len(done), "cancelled_at_budget": len(cut),
+                "failed": len(res) - len(done) - len(cut),
+                "throughput_req_s": len(done) / wall, "pole_solves_s": 60 * len(done) / wall, "wall_s": wall,
+                "peak_concurrent": st["peak_concurrent"]}, reqs, res
 
-    cont, r1 = run(4, 8)
-    plain, r2 = run(1, 1)
-    same = max(float(np.max(np.abs(a.dm - b.dm))) for a, b in zip(r1, r2))
-    for *_, plan in systems:
-        px.pexsi_plan_destroy(plan)
-    return {"workload": "Poisson arrivals, requests = 8 inertia shifts + one 60-pole DM over "
+    rate_used = rate
+    if capacity_frac:
+        probe, _, _ = run(4, 8, 6, 1e6)  # all at once: the split arm's capacity
+        rate_used = capacity_frac * probe["throughput_req_s"]
+    split, r_split, res_split = run(4, 8, 6, rate_used)
+    fp64, r_fp64, res_fp64 = run(1, 1, 0, rate_used, budget=fp64_budget_s)
+    # determinism: three split requests replayed alone
+    replay = [k for k in range(min(n_req, 3))]
+    _, r_alone, _ = run(1, 8, 6, rate_used, only=replay)
+    alone_diff = max(float(np.max(np.abs(a.dm - r_split[k].dm))) for a, k in zip(r_alone, replay))
+    split_vs_fp64 = [float(np.max(np.abs(a.dm - b.dm))) for a, b, x in zip(r_split, r_fp64, res_fp64)
+                     if x["status"] == 0]
+    for *_, plans in systems:
+        for p in plans.values():
+            px.pexsi_plan_destroy(p)
+    return {"workload": "Poisson arrivals; request = 8 inertia shifts + one 60-pole DM over "
                         + ", ".join(f"{n} (n={s.n})" for n, s, *_ in systems)
-                        + "; mu jitter +-0.05 Ha, beta jitter +-10% (sizes scaled down from 4k-50k)",
-            "rate_req_s": rate, "requests": n_req, "continuous": cont, "plain_per_pole": plain,
-            "max_abs_dm_diff_between_modes": same}
+                        + "; mu jitter +-0.05 Ha, beta jitter +-10%",
+            "rate_req_s": rate_used, "requests": n_req,
+            "split_continuous": split, "fp64_plain_per_pole": fp64, "fp64_budget_s": fp64_budget_s,
+            "alone_vs_mix_max_abs_dm": alone_diff,
+            "split_vs_fp64_max_abs_dm": max(split_vs_fp64) if split_vs_fp64 else None}
 
 
 def main():
@@ -649,8 +812,16 @@ def main():
     ap.add_argument("--split-steps", type=int, default=6, help="timed 20-pole steps of the split-precision path")
     ap.add_argument("--split-latency-calls", type=int, default=5,
                     help="full P-pole host calls timed for the split path's DM latency")
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving trace (0 = skip)")
-    ap.add_argument("--serve-rate", type=float, default=3.0, help="Poisson arrival rate of the serving trace")
+    ap.add_argument("--batched-passes", type=int, default=2,
+                    help="timed passes of the six-system batched split-precision group (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=16, help="requests of the serving trace (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate of the serving trace")
+    ap.add_argument("--serve-set", choices=sorted(SERVE_SETS), default="small",
+                    help="systems of the serving trace (config: n = 3.7k, 12k, 27k)")
+    ap.add_argument("--serve-fp64-budget", type=float, default=60.0,
+                    help="wall seconds after which the plain FP64 arm's unfinished requests are cancelled")
+    ap.add_argument("--serve-capacity-frac", type=float, default=0.0,
+                    help="if > 0: arrival rate = this fraction of the split arm's measured capacity")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -94,7 +94,11 @@ typedef struct pexsi_opts {
                               the host after the first pole batch of every call with
                               accumulate = 0 (PEXSI_ERR_BREAKDOWN at the end of the
                               chain).                                             */
-  int32_t reserved1;
+  int32_t split_block;     /* split-precision path: panels per block of the Schur
+                              update, 1..4 (0 = 4). Each panel updates the rest of
+                              its block, then one update of K = 64 x split_block
+                              covers everything to the right; 1 is the unblocked
+                              per-panel update (exponents over 64 columns of L).  */
 } pexsi_opts;
 
 /* Symbolic statistics of a plan. Flop counts are algorithmic real flops of

@@ -41,7 +41,7 @@ class pexsi_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("panel", ctypes.c_int32), ("leaf_cols", ctypes.c_int32),
                 ("amalgamate", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("split_slices", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_int64), ("wait_ns", ctypes.c_int64), ("inject", ctypes.c_int32),
-                ("reserved1", ctypes.c_int32)]
+                ("split_block", ctypes.c_int32)]
 
 
 class pexsi_plan_stats(ctypes.Structure):

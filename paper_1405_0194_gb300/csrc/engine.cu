@@ -1109,7 +1109,10 @@ int init_opts(pexsi_plan* p, const pexsi_opts* opts) {
   if (p->opts.panel < 16 || p->opts.panel > 64 || p->opts.split_slices < 0 || p->opts.split_slices > 6 ||
       p->opts.split_slices == 1 || (p->opts.split_slices > 0 && p->opts.panel != 64))
     return PEXSI_ERR_INVALID_ARG;
-  if (p->opts.wait_ns < 0 || p->opts.inject < 0 || p->opts.inject > 2) return PEXSI_ERR_INVALID_ARG;
+  if (p->opts.wait_ns < 0 || p->opts.inject < 0 || p->opts.inject > 2 || p->opts.split_block < 0 ||
+      p->opts.split_block > kOzBlockPanels)
+    return PEXSI_ERR_INVALID_ARG;
+  p->oz_block = p->opts.split_block > 0 ? p->opts.split_block : kOzBlockPanels;
   p->wait_ns = p->opts.wait_ns > 0 ? uint64_t(p->opts.wait_ns) : 1000000000ull;
   p->oz_slices = p->opts.split_slices;
   p->b = p->opts.panel;
