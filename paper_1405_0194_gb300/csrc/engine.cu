@@ -70,8 +70,14 @@ void Profiler::destroy() {
 }
 
 // ------------------------------------------------------------------ workspaces
+// Split-K partials of the FP64 Takahashi step, per batch member: kMaxKsplit
+// tiles of kTile x b for each 64-row tile slot of the partial layout.
+int64_t kpart_stride(const pexsi_plan* p) {
+  return p->oz_slices > 0 ? 0 : p->part_stride / (int64_t(p->b) * p->b) * kMaxKsplit * kTile * p->b;
+}
+
 int64_t bytes_per_pole(const pexsi_plan* p) {
-  return (2 * p->sym.front_elems + p->part_stride) * int64_t(sizeof(double2)) +
+  return (2 * p->sym.front_elems + p->part_stride + kpart_stride(p)) * int64_t(sizeof(double2)) +
          std::max(p->ozA_stride, 2 * p->ozA_stride_r) + std::max(p->ozB_stride, 2 * p->ozB_stride_r) +
          8 * (p->exA_stride + p->exB_stride) + 4 * p->ymax_stride;
 }
@@ -112,6 +118,8 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
   wsalloc(&ws.F, sizeof(double2) * pool * batch, ws, "alloc(F)");
   wsalloc(&ws.Y, sizeof(double2) * pool * batch, ws, "alloc(Y)");
   wsalloc(&ws.part, sizeof(double2) * size_t(p->part_stride) * batch, ws, "alloc(partials)");
+  if (kpart_stride(p) > 0)
+    wsalloc(&ws.kpart, sizeof(double2) * size_t(kpart_stride(p)) * batch, ws, "alloc(split-K partials)");
   wsalloc(&ws.H, sizeof(double) * nnz, ws, "alloc(H)");
   wsalloc(&ws.S, sizeof(double) * nnz, ws, "alloc(S)");
   wsalloc(&ws.out, sizeof(double) * nnz * 4, ws, "alloc(outputs)");
@@ -138,7 +146,7 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
 
 void workspace_free(Workspace& ws) {
   void* ptrs[] = {ws.F,  ws.Y,        ws.part,  ws.H,    ws.S,   ws.out, ws.brk, ws.minpiv, ws.neg,
-                  ws.partials, ws.trace3, ws.ainv, ws.ozA, ws.ozB, ws.exA, ws.exB, ws.ozfail, ws.ymax};
+                  ws.partials, ws.trace3, ws.ainv, ws.ozA, ws.ozB, ws.exA, ws.exB, ws.ozfail, ws.ymax, ws.kpart};
   for (void* q : ptrs) {
     if (!q) continue;
     if (ws.async) cudaFreeAsync(q, ws.stream);
@@ -380,7 +388,8 @@ void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Pro
         launch_oz_takahashi(ws.Y, ws.F, fr, dfr, g.nact, g.max_mp, p0, b, S, oz, sh.nb, st, false);
         pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by, 1, nb * w.off_fl * 4.0 * S * (S + 1) / 2 / 8.0 * 2.0);
       } else {
-        launch_selinv_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, p0, b, sh, st);
+        launch_selinv_offdiag(ws.Y, ws.F, fr, dfr, g.nact, g.row_tiles, g.max_mp, p0, b, sh, ws.kpart, p->d_part_off,
+                              kpart_stride(p), st);
         pf.end(a, P_OFFDIAG, st, nb * w.off_fl, nb * w.off_by);
       }
       if (p->oz_slices > 0) {

@@ -23,6 +23,8 @@
 #include <cfloat>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 
 namespace pexsi {
@@ -97,6 +99,13 @@ __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
   while ((i + 1) * (i + 2) / 2 <= t) ++i;
   I = i;
   J = t - i * (i + 1) / 2;
+}
+
+// K splits of the FP64 Takahashi step of a front with m_p trailing rows:
+// at least 384 of K per split, at most kMaxKsplit splits.
+__host__ __device__ __forceinline__ int ksplit_of(int mp) {
+  const int k = mp / 384;
+  return k < 1 ? 1 : (k > kMaxKsplit ? kMaxKsplit : k);
 }
 
 // ------------------------------------------------------------ GEMM tile
@@ -644,6 +653,143 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
   }
 }
 
+// The same inversion of a complex panel block, split over a cluster of
+// kDiagCluster CTAs (one SM each): CTA r owns columns [r W, (r+1) W) of the
+// bb x bb block (W = ceil(bb / kDiagCluster)) in its shared memory. At pivot
+// step k the owner of column k searches it for the pivot, swaps rows k and
+// pr in its columns and writes the pivot row index, the reciprocal of the
+// pivot and the (swapped) column k into every CTA's shared memory
+// (distributed shared memory, double-buffered by step parity); after one
+// cluster barrier every CTA swaps, scales row k and updates its own columns.
+// The buffer written at step k + 2 is no longer read then: every CTA has
+// passed the barrier of step k + 1, after its update of step k. The final
+// column interchanges are applied when the columns are written back. One
+// inversion thus runs on kDiagCluster SMs' FP64 pipes instead of one.
+constexpr int kDiagCluster = 8;
+
+template <bool GEN>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __restrict__ F, DevFronts fr,
+                                                                   const int32_t* __restrict__ fronts, int p0, int b,
+                                                                   DevStatus st) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ double2 A[64][64 / kDiagCluster + 1];  // this CTA's columns (row-major in i)
+  __shared__ double2 pub_fac[2][64];
+  __shared__ double2 pub_inv[2];
+  __shared__ int pub_piv[2];
+  __shared__ double pub_best[2];
+  __shared__ double s_maxes[kDiagCluster];
+  __shared__ int s_perm[64];
+  __shared__ double s_lmax;
+  const int f = fronts[blockIdx.x / kDiagCluster];
+  const int r = int(cluster.block_rank());
+  const int pb = blockIdx.y;
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;  // the same for every CTA of the cluster
+  const int bb = min(b, s - p0);
+  const int W = (bb + kDiagCluster - 1) / kDiagCluster;
+  const int c0 = r * W, nc = max(0, min(bb, c0 + W) - c0);
+  double2* Fd = F + int64_t(pb) * fr.pool + fr.off[f] + p0 + int64_t(m) * p0;
+  if (threadIdx.x == 0) s_lmax = 0.0;
+  __syncthreads();
+  double lmax = 0.0;
+  for (int idx = threadIdx.x; idx < bb * nc; idx += blockDim.x) {
+    const int i = idx % bb, jl = idx / bb, j = c0 + jl;
+    const double2 v = (GEN || i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
+    A[i][jl] = v;
+    lmax = fmax(lmax, absv(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&s_lmax), __double_as_longlong(lmax));
+  __syncthreads();
+  if (threadIdx.x == 0) *cluster.map_shared_rank(&s_maxes[r], 0) = s_lmax;  // block max, gathered in CTA 0
+  bool bad = false;
+  double pmin = DBL_MAX;
+  for (int k = 0; k < bb; ++k) {
+    const int par = k & 1, owner = k / W;
+    if (r == owner) {
+      const int lk = k - c0;
+      if (threadIdx.x < 32) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < bb; i += 32) {
+          const double a = absv(A[i][lk]);
+          if (a > best) { best = a; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (threadIdx.x == 0) {
+          pub_piv[par] = bi;
+          pub_best[par] = best;
+        }
+      }
+      __syncthreads();
+      const int pr = pub_piv[par];
+      if (pr != k)
+        for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) {
+          const double2 t = A[k][jl]; A[k][jl] = A[pr][jl]; A[pr][jl] = t;
+        }
+      __syncthreads();
+      const double best = pub_best[par];
+      const bool now_bad = bad || !(best > 0.0) || !isfinite(best);
+      const double2 inv = now_bad ? zero_of(double2()) : recipv(A[k][lk]);
+      for (int q = 0; q < kDiagCluster; ++q) {  // publish into every CTA of the cluster
+        double2* fac = cluster.map_shared_rank(&pub_fac[par][0], q);
+        for (int i = threadIdx.x; i < bb; i += blockDim.x) fac[i] = A[i][lk];
+        if (threadIdx.x == 0) {
+          *cluster.map_shared_rank(&pub_inv[par], q) = inv;
+          *cluster.map_shared_rank(&pub_piv[par], q) = pr;
+          *cluster.map_shared_rank(&pub_best[par], q) = best;
+        }
+      }
+    }
+    cluster.sync();
+    const int pr = pub_piv[par];
+    const double best = pub_best[par];
+    const double2 inv = pub_inv[par];
+    bad = bad || !(best > 0.0) || !isfinite(best);
+    pmin = fmin(pmin, best);
+    if (threadIdx.x == 0) s_perm[k] = pr;
+    if (r != owner && pr != k)
+      for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) {
+        const double2 t = A[k][jl]; A[k][jl] = A[pr][jl]; A[pr][jl] = t;
+      }
+    __syncthreads();
+    // row k scaled by the pivot's reciprocal; column k keeps the multipliers' negatives over the pivot
+    for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) A[k][jl] = (c0 + jl == k) ? inv : mulv(A[k][jl], inv);
+    __syncthreads();
+    const double2* fac = pub_fac[par];
+    for (int idx = threadIdx.x; idx < bb * nc; idx += blockDim.x) {
+      const int i = idx / nc, jl = idx % nc;
+      if (i == k) continue;
+      A[i][jl] = (c0 + jl == k) ? fmsv(zero_of(double2()), fac[i], inv) : fmsv(A[i][jl], fac[i], A[k][jl]);
+    }
+    __syncthreads();
+  }
+  // write back: the row interchanges are column interchanges of the inverse,
+  // undone in reverse order, applied to each column's destination index
+  for (int jl = 0; jl < nc; ++jl) {
+    int pos = c0 + jl;
+    for (int k = bb - 1; k >= 0; --k) {
+      const int q = s_perm[k];
+      if (pos == k) pos = q;
+      else if (pos == q) pos = k;
+    }
+    for (int i = threadIdx.x; i < bb; i += blockDim.x) Fd[i + int64_t(m) * pos] = A[i][jl];
+  }
+  cluster.sync();  // every remote write of the cluster is done before any CTA leaves
+  if (r == 0 && threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int q = 0; q < kDiagCluster; ++q) mx = fmax(mx, s_maxes[q]);
+    const double ratio = mx > 0 ? pmin / mx : 0.0;
+    atomicMin(st.min_pivot, (unsigned long long)__double_as_longlong(ratio));
+    if (bad || ratio < 1e-13) atomicMin(st.breakdown_front, f);
+  }
+}
+
 // ------------------------------------------------------------ panel solve
 template <typename T, bool GEN = false>
 __global__ void __launch_bounds__(256) k_panel_solve(T* __restrict__ F, DevFronts fr, const int32_t* __restrict__ fronts,
@@ -772,9 +918,21 @@ __global__ void k_gather(double2* __restrict__ Y, DevFronts fr, const int32_t* _
 // Y[S,P] = -Y[S,S] L[S,P] over 64-row tiles of S, and its mirror Y[P,S] =
 // Y[S,P]^T. LDU fronts (GEN) have no mirror: blocks blockIdx.x >= gridDim.x
 // / 2 compute Y[P,S] = -U[P,S] Y[S,S] over 64-column tiles of S instead.
+//
+// Split-K (complex-symmetric fronts, kpart != NULL): a front's ks = ksplit_of(m_p)
+// blocks per tile (block x = tile * ks + split) take ks contiguous K ranges
+// (multiples of 16) and write their 64 x bb partial products to kpart;
+// k_offdiag_reduce adds the partials in split order and writes Y[S,P] and
+// its mirror. The CTAs of a long-K launch are equal in size, so their last
+// wave can leave most SMs idle (the FP64 pipe of each SM is the bound);
+// ks times as many, ks times shorter CTAs fill the waves. ks depends on the
+// front alone, so results do not depend on the batch or on the launch's
+// other fronts.
 template <bool GEN = false>
 __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y, const double2* __restrict__ F, DevFronts fr,
-                                                        const int32_t* __restrict__ fronts, int p0, int b) {
+                                                        const int32_t* __restrict__ fronts, int p0, int b,
+                                                        double2* __restrict__ kpart, const int64_t* __restrict__ part_off,
+                                                        int64_t kstride) {
   extern __shared__ __align__(16) double gsm[];
   const int f = fronts[blockIdx.y];
   const int s = fr.s[f], m = fr.m[f];
@@ -782,19 +940,38 @@ __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y,
   const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
   const int half = GEN ? int(gridDim.x) / 2 : int(gridDim.x);
   const bool upper = GEN && int(blockIdx.x) >= half;
-  const int I0 = (upper ? int(blockIdx.x) - half : int(blockIdx.x)) * kTile;
+  const int ks = (GEN || kpart == nullptr) ? 1 : ksplit_of(mp);
+  const int tile = GEN ? (upper ? int(blockIdx.x) - half : int(blockIdx.x)) : int(blockIdx.x) / ks;
+  const int split = GEN ? 0 : int(blockIdx.x) % ks;
+  const int I0 = tile * kTile;
   if (I0 >= mp) return;
   const int64_t base = int64_t(blockIdx.z) * fr.pool + fr.off[f];
   double2* Yb = Y + base;
   const double2* Fb = F + base;
   const int Mv = min(kTile, mp - I0);
+  // this block's K range (the whole of it unless split)
+  const int kc = ks > 1 ? ((mp + ks - 1) / ks + 15) / 16 * 16 : mp;
+  const int k0 = min(mp, split * kc), k1 = min(mp, k0 + kc);
   double2 acc[4][4];
   zero_acc(acc);
   if (upper)  // U[P,S] (bb x mp) times the columns I0.. of Y[S,S]
     gemm_any<double2, false>(acc, Fb + p0 + int64_t(m) * q0, m, Yb + q0 + int64_t(m) * (q0 + I0), m, bb, Mv, mp, gsm);
   else
-    gemm_any<double2, false>(acc, Yb + q0 + I0 + int64_t(m) * q0, m, Fb + q0 + int64_t(m) * p0, m, Mv, bb, mp, gsm);
+    gemm_any<double2, false>(acc, Yb + q0 + I0 + int64_t(m) * (q0 + k0), m, Fb + q0 + k0 + int64_t(m) * p0, m, Mv, bb,
+                             k1 - k0, gsm);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (!GEN && ks > 1) {
+    const int64_t slot = part_off[f] / (int64_t(b) * b) + tile;
+    double2* out = kpart + int64_t(blockIdx.z) * kstride + (slot * kMaxKsplit + split) * (int64_t(kTile) * b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int r = tx + 16 * i, c = ty + 16 * j;
+        if (r < Mv && c < bb) out[r + kTile * c] = acc[i][j];
+      }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -808,6 +985,31 @@ __global__ void __launch_bounds__(256) k_selinv_offdiag(double2* __restrict__ Y,
         if (!GEN) Yb[(p0 + c) + int64_t(m) * (q0 + I0 + r)] = v;
       }
     }
+}
+
+__global__ void __launch_bounds__(256) k_offdiag_reduce(double2* __restrict__ Y, DevFronts fr,
+                                                        const int32_t* __restrict__ fronts, int p0, int b,
+                                                        const double2* __restrict__ kpart,
+                                                        const int64_t* __restrict__ part_off, int64_t kstride) {
+  const int f = fronts[blockIdx.y];
+  const int s = fr.s[f], m = fr.m[f];
+  if (p0 >= s) return;
+  const int bb = min(b, s - p0), q0 = p0 + bb, mp = m - q0;
+  const int ks = ksplit_of(mp);
+  const int I0 = blockIdx.x * kTile;
+  if (ks == 1 || I0 >= mp) return;
+  const int Mv = min(kTile, mp - I0);
+  double2* Yb = Y + int64_t(blockIdx.z) * fr.pool + fr.off[f];
+  const int64_t slot = part_off[f] / (int64_t(b) * b) + blockIdx.x;
+  const double2* in = kpart + int64_t(blockIdx.z) * kstride + slot * kMaxKsplit * (int64_t(kTile) * b);
+  for (int idx = threadIdx.x; idx < Mv * bb; idx += blockDim.x) {
+    const int r = idx % Mv, c = idx / Mv;
+    double2 v = in[r + kTile * c];
+    for (int j = 1; j < ks; ++j) v = addv(v, in[j * (int64_t(kTile) * b) + r + kTile * c]);
+    v = negv(v);
+    Yb[(q0 + I0 + r) + int64_t(m) * (p0 + c)] = v;
+    Yb[(p0 + c) + int64_t(m) * (q0 + I0 + r)] = v;
+  }
 }
 
 template <bool GEN = false>
@@ -1006,10 +1208,36 @@ void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int n
   k_extend_add<T><<<grid, block, 0, st>>>(F, fr, children, nchild, pref);
 }
 
+// One cluster of kDiagCluster CTAs per block inverse (complex poles, which
+// need no inertia count).
+template <bool GEN>
+void launch_diag_inv_cluster(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+                             const BatchShifts& sh, DevStatus status, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(nfronts * kDiagCluster), unsigned(sh.nb), 1);
+  cfg.blockDim = dim3(kDiagThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kDiagCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_diag_inv_cluster<GEN>, F, fr, fronts, p0, b, status);
+}
+
 template <typename T>
 void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                      const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
   if (nfronts <= 0) return;
+  if constexpr (sizeof(T) == sizeof(double2)) {
+    if (!count_inertia && b <= 64) {
+      launch_diag_inv_cluster<false>(reinterpret_cast<double2*>(F), fr, fronts, nfronts, p0, b, sh, status, st);
+      return;
+    }
+  }
   size_t smem = sizeof(T) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
   k_diag_inv<T><<<grid, kDiagThreads, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
@@ -1039,10 +1267,16 @@ void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int n
 }
 
 void launch_selinv_offdiag(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
-                           int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
+                           int max_row_tiles, int max_mp, int p0, int b, const BatchShifts& sh, double2* kpart,
+                           const int64_t* part_off, int64_t kstride, cudaStream_t st) {
   if (nfronts <= 0 || max_row_tiles <= 0) return;
-  dim3 grid(max_row_tiles, nfronts, sh.nb);
-  k_selinv_offdiag<<<grid, 256, kSmem3m, st>>>(Y, F, fr, fronts, p0, b);
+  // every front's ks tiles fit: ksplit_of is non-decreasing in m_p
+  const int ks = kpart ? ksplit_of(max_mp) : 1;
+  dim3 grid(max_row_tiles * ks, nfronts, sh.nb);
+  k_selinv_offdiag<false><<<grid, 256, kSmem3m, st>>>(Y, F, fr, fronts, p0, b, kpart, part_off, kstride);
+  if (ks > 1)
+    k_offdiag_reduce<<<dim3(max_row_tiles, nfronts, sh.nb), 256, 0, st>>>(Y, fr, fronts, p0, b, kpart, part_off,
+                                                                            kstride);
 }
 
 void launch_selinv_diag_partial(const double2* Y, const double2* F, double2* part, const int64_t* part_off,
@@ -1127,6 +1361,10 @@ void launch_extend_add_full(double2* F, const DevFronts& fr, const int32_t* chil
 void launch_diag_inv_gen(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                          const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
   if (nfronts <= 0) return;
+  if (!count_inertia && b <= 64) {
+    launch_diag_inv_cluster<true>(F, fr, fronts, nfronts, p0, b, sh, status, st);
+    return;
+  }
   size_t smem = sizeof(double2) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double2) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
   k_diag_inv<double2, true><<<grid, kDiagThreads, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
@@ -1151,7 +1389,7 @@ void launch_selinv_offdiag_gen(double2* Y, const double2* F, const DevFronts& fr
                                int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st) {
   if (nfronts <= 0 || max_row_tiles <= 0) return;
   dim3 grid(2 * max_row_tiles, nfronts, sh.nb);
-  k_selinv_offdiag<true><<<grid, 256, kSmem3m, st>>>(Y, F, fr, fronts, p0, b);
+  k_selinv_offdiag<true><<<grid, 256, kSmem3m, st>>>(Y, F, fr, fronts, p0, b, nullptr, nullptr, 0);
 }
 
 void launch_selinv_diag_partial_gen(const double2* Y, const double2* F, double2* part, const int64_t* part_off,

@@ -9,6 +9,7 @@ namespace pexsi {
 
 constexpr int kMaxBatch = 64;  // poles (or shifts) processed together
 constexpr int kTile = 64;      // GEMM output tile edge
+constexpr int kMaxKsplit = 8;  // K splits of the FP64 Takahashi step (kpart slots per 64-row tile)
 
 // Shifts of one batch, passed by value: complex z_b (re, im) for poles, or
 // real sigma_b (im = 0) for inertia shifts. Weights of the pole sum.
@@ -91,8 +92,11 @@ void launch_trailing(T* F, const DevFronts& fr, const int32_t* fronts, int nfron
 void launch_gather(double2* Y, const DevFronts& fr, const int32_t* fronts, int nfronts, const int32_t* pref,
                    int64_t total_tiles, const BatchShifts& sh, cudaStream_t st);
 
+// kpart (kstride elements per batch member, kMaxKsplit * kTile * b per tile
+// slot of part_off) enables the split-K form; NULL runs one block per tile.
 void launch_selinv_offdiag(double2* Y, const double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts,
-                           int max_row_tiles, int p0, int b, const BatchShifts& sh, cudaStream_t st);
+                           int max_row_tiles, int max_mp, int p0, int b, const BatchShifts& sh, double2* kpart,
+                           const int64_t* part_off, int64_t kstride, cudaStream_t st);
 
 void launch_selinv_diag_partial(const double2* Y, const double2* F, double2* part, const int64_t* part_off,
                                 int64_t part_stride, const DevFronts& fr, const int32_t* fronts, int nfronts,

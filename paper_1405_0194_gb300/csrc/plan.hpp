@@ -82,6 +82,7 @@ enum ProfClass {
 struct Workspace {
   int batch = 0;
   double2 *F = nullptr, *Y = nullptr, *part = nullptr;
+  double2* kpart = nullptr;  // split-K partials of the FP64 Takahashi step
   int* brk = nullptr;
   unsigned long long* minpiv = nullptr;
   int* neg = nullptr;
