@@ -808,7 +808,8 @@ int selinv_one_herm(const pexsi_plan* p, Workspace& ws, const double2* dH, const
 Symbolic merge_symbolic(const std::vector<const Symbolic*>& parts) {
   Symbolic m;
   int64_t off_n = 0, off_rows = 0, off_pool = 0;
-  int32_t off_super = 0;
+  int32_t off_super = 0, hmax = 0;
+  for (const Symbolic* q : parts) hmax = std::max(hmax, q->nlevels);
   for (const Symbolic* q : parts) {
     for (int32_t v : q->perm) m.perm.push_back(v + int32_t(off_n));
     for (int32_t v : q->iperm) m.iperm.push_back(v + int32_t(off_n));
@@ -816,7 +817,7 @@ Symbolic merge_symbolic(const std::vector<const Symbolic*>& parts) {
       m.first.push_back(q->first[K] + int32_t(off_n));
       m.rptr.push_back(q->rptr[K] + off_rows);
       m.parent.push_back(q->parent[K] >= 0 ? q->parent[K] + off_super : -1);
-      m.height.push_back(q->height[K]);
+      m.height.push_back(q->height[K] + hmax - q->nlevels);
       m.front_off.push_back(q->front_off[K] + off_pool);
     }
     for (int32_t v : q->rows) m.rows.push_back(v + int32_t(off_n));
@@ -824,9 +825,13 @@ Symbolic merge_symbolic(const std::vector<const Symbolic*>& parts) {
     for (int64_t v : q->entry_pos) m.entry_pos.push_back(v + off_pool);
     for (int64_t v : q->entry_pos_up) m.entry_pos_up.push_back(v + off_pool);
     m.entry_lower.insert(m.entry_lower.end(), q->entry_lower.begin(), q->entry_lower.end());
-    if (int32_t(m.level_fronts.size()) < q->nlevels) m.level_fronts.resize(q->nlevels);
+    // levels aligned at the roots: system q's level L becomes L + (H - H_q)
+    // (H the tallest tree), so that the widest fronts -- the roots and the
+    // separators just below them, which hold most panels -- of every system
+    // share launches; shifting a whole tree keeps its children before parents
+    if (int32_t(m.level_fronts.size()) < hmax) m.level_fronts.resize(hmax);
     for (int32_t L = 0; L < q->nlevels; ++L)
-      for (int32_t K : q->level_fronts[L]) m.level_fronts[L].push_back(K + off_super);
+      for (int32_t K : q->level_fronts[L]) m.level_fronts[L + hmax - q->nlevels].push_back(K + off_super);
     m.nnz += q->nnz;
     m.nnz_L += q->nnz_L;
     m.max_front = std::max(m.max_front, q->max_front);
@@ -1229,11 +1234,14 @@ int pexsi::hermitian_prepare(pexsi_plan* p) {
 
 namespace {
 
-// Runs fn with the plan's workspace temporarily on `stream` (NULL = its own).
+// Runs fn with the plan's workspace temporarily on `stream`: the caller's
+// stream of a device-buffer call, NULL being the legacy default stream (as
+// the header states), so that the caller's events on that stream bracket
+// the work. The plan's own stream serves the host-buffer calls.
 template <typename Fn>
 int on_stream(pexsi_plan* p, void* stream, Fn fn) {
   cudaStream_t own = p->ws.stream;
-  if (stream) p->ws.stream = static_cast<cudaStream_t>(stream);
+  p->ws.stream = static_cast<cudaStream_t>(stream);
   int rc;
   try {
     rc = fn();

@@ -702,6 +702,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __re
   for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&s_lmax), __double_as_longlong(lmax));
   __syncthreads();
+  cluster.sync();  // every CTA of the cluster runs before any distributed shared memory access
   if (threadIdx.x == 0) *cluster.map_shared_rank(&s_maxes[r], 0) = s_lmax;  // block max, gathered in CTA 0
   bool bad = false;
   double pmin = DBL_MAX;
