@@ -1912,12 +1912,15 @@ int pexsi_group_tune(pexsi_group* g, const double* const* dH, const double* cons
     }
     if (dS)
       for (int q = 0; q < n; ++q) S[q] = dS[q];
+    // wave candidates: the capacity, half and a quarter of it, each evened
+    // out over the pole table (P = 64 at capacity 9 runs 8 waves of 8, not 7
+    // of 9 and a last one of 1, which costs almost a full wave's launches)
     std::vector<int> waves;
-    for (int w = p->ws.batch; w >= 1 && waves.size() < 3; w /= 2) {
-      if (w > n_poles) continue;
-      waves.push_back(w);
+    for (int cap = std::min(p->ws.batch, int(n_poles)); cap >= 1 && waves.size() < 3; cap /= 2) {
+      const int nw = (int(n_poles) + cap - 1) / cap, w = (int(n_poles) + nw - 1) / nw;
+      if (std::find(waves.begin(), waves.end(), w) == waves.end()) waves.push_back(w);
+      if (cap == 1) break;
     }
-    if (waves.empty()) waves.push_back(std::min(p->ws.batch, int(n_poles)));
     std::vector<int> blocks = p->oz_slices > 0 ? std::vector<int>{4, 2, 1} : std::vector<int>{p->oz_block};
     std::vector<pexsi_dm_info> info(n);
     std::string err;

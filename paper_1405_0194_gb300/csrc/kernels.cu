@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
 }
 
 // The same inversion of a complex panel block, split over a cluster of
-// kDiagCluster CTAs (one SM each): CTA r owns columns [r W, (r+1) W) of the
+// kDiagCluster (2, 4 or 8) CTAs (one SM each): CTA r owns columns [r W, (r+1) W) of the
 // bb x bb block (W = ceil(bb / kDiagCluster)) in its shared memory. At pivot
 // step k the owner of column k searches it for the pivot, swaps rows k and
 // pr in its columns and writes the pivot row index, the reciprocal of the
@@ -665,9 +665,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
 // passed the barrier of step k + 1, after its update of step k. The final
 // column interchanges are applied when the columns are written back. One
 // inversion thus runs on kDiagCluster SMs' FP64 pipes instead of one.
-constexpr int kDiagCluster = 8;
-
-template <bool GEN>
+template <bool GEN, int kDiagCluster>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __restrict__ F, DevFronts fr,
                                                                    const int32_t* __restrict__ fronts, int p0, int b,
                                                                    DevStatus st) {
@@ -1209,11 +1207,12 @@ void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int n
   k_extend_add<T><<<grid, block, 0, st>>>(F, fr, children, nchild, pref);
 }
 
-// One cluster of kDiagCluster CTAs per block inverse (complex poles, which
-// need no inertia count).
-template <bool GEN>
-void launch_diag_inv_cluster(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
-                             const BatchShifts& sh, DevStatus status, cudaStream_t st) {
+// One cluster of C CTAs per block inverse (complex poles, which need no
+// inertia count).
+template <bool GEN, int C>
+void launch_diag_inv_cluster_c(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+                               const BatchShifts& sh, DevStatus status, cudaStream_t st) {
+  constexpr int kDiagCluster = C;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(nfronts * kDiagCluster), unsigned(sh.nb), 1);
   cfg.blockDim = dim3(kDiagThreads, 1, 1);
@@ -1226,7 +1225,24 @@ void launch_diag_inv_cluster(double2* F, const DevFronts& fr, const int32_t* fro
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_diag_inv_cluster<GEN>, F, fr, fronts, p0, b, status);
+  cudaLaunchKernelEx(&cfg, k_diag_inv_cluster<GEN, C>, F, fr, fronts, p0, b, status);
+}
+
+// The cluster size: wide enough to spread the launch's inversions over the
+// SMs, 1 (the single-CTA kernel) once they already fill them.
+int diag_cluster_size(int inversions) {
+  return inversions >= 152 ? 1 : inversions >= 76 ? 2 : inversions >= 38 ? 4 : 8;
+}
+
+template <bool GEN>
+bool launch_diag_inv_cluster(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+                             const BatchShifts& sh, DevStatus status, cudaStream_t st) {
+  switch (diag_cluster_size(nfronts * sh.nb)) {
+    case 8: launch_diag_inv_cluster_c<GEN, 8>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
+    case 4: launch_diag_inv_cluster_c<GEN, 4>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
+    case 2: launch_diag_inv_cluster_c<GEN, 2>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
+    default: return false;
+  }
 }
 
 template <typename T>
@@ -1234,10 +1250,9 @@ void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfron
                      const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
   if (nfronts <= 0) return;
   if constexpr (sizeof(T) == sizeof(double2)) {
-    if (!count_inertia && b <= 64) {
-      launch_diag_inv_cluster<false>(reinterpret_cast<double2*>(F), fr, fronts, nfronts, p0, b, sh, status, st);
+    if (!count_inertia && b <= 64 &&
+        launch_diag_inv_cluster<false>(reinterpret_cast<double2*>(F), fr, fronts, nfronts, p0, b, sh, status, st))
       return;
-    }
   }
   size_t smem = sizeof(T) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
@@ -1362,10 +1377,8 @@ void launch_extend_add_full(double2* F, const DevFronts& fr, const int32_t* chil
 void launch_diag_inv_gen(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                          const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
   if (nfronts <= 0) return;
-  if (!count_inertia && b <= 64) {
-    launch_diag_inv_cluster<true>(F, fr, fronts, nfronts, p0, b, sh, status, st);
+  if (!count_inertia && b <= 64 && launch_diag_inv_cluster<true>(F, fr, fronts, nfronts, p0, b, sh, status, st))
     return;
-  }
   size_t smem = sizeof(double2) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double2) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
   k_diag_inv<double2, true><<<grid, kDiagThreads, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);

@@ -235,3 +235,38 @@ def test_full_size_fluid_all_poles_split(full_fluid):
     """The split-precision path (S = 6) on all 60 poles: entries within the
     split tolerance 1e-7, |Tr[DM S] - N_P| within 1e-8."""
     _full_size_all_poles(full_fluid, 6, 1e-7)
+
+
+@pytest.mark.slow
+def test_full_size_sheet_two_poles():
+    """The 2D sheet at full size (sheet32x32, n = 26,624, 60-pole table): two
+    poles of the occupied side (one next to the real axis, one further out),
+    FP64 and split paths, against the oracle's dense LU with 4 sampled column
+    solves (about two minutes of host LAPACK per pole)."""
+    s = ns.make_sheet(ncell=32, seed=0)
+    mu, dE = ns.mu_and_delta_e(s)
+    P = 60
+    tab = poles.pole_table(s.beta, dE, P, mu)
+    dH = torch.from_numpy(s.H).cuda(); dS = torch.from_numpy(s.S).cuda()
+    st = torch.cuda.current_stream().cuda_stream
+    cols = np.sort(np.random.default_rng(5).choice(s.n, 4, replace=False))
+    for l in (59, 45):
+        ref = {}
+        lu = sampled.factor_shifted_dense(s.n, s.colptr, s.rowind, s.H, s.S, tab["z"][l])
+        sel = sampled.selected_columns_dense(s.n, s.colptr, s.rowind, s.H, s.S, tab["z"][l], cols, lu=lu)
+        del lu
+        for j, v in sel.items():
+            ref[j] = [np.imag(tab[k][l] * v) for k in ("w_rho", "w_E", "w_F")]
+        for split, tol in ((0, TOL_DM), (6, 1e-7)):
+            plan = _plan(s, max_batch=1, split_slices=split)
+            out = torch.zeros(3, s.nnz, dtype=torch.float64, device="cuda")
+            px.pexsi_dm_device(plan, dH.data_ptr(), dS.data_ptr(), mu, s.beta, P, dE, l, l + 1, 0,
+                               out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), st, want_info=True)
+            px.pexsi_plan_destroy(plan)
+            got = out.cpu().numpy()
+            worst = max(float(np.max(np.abs(got[q, s.colptr[j]:s.colptr[j + 1]] - ref[j][q])))
+                        for j in cols for q in range(3))
+            big = max(float(np.max(np.abs(ref[j][0]))) for j in cols)
+            print(f"sheet32x32 pole {l} split={split}: max sampled |d| = {worst:.3e} (largest sampled DM entry "
+                  f"{big:.3e})")
+            assert worst <= tol * max(1.0, big)
