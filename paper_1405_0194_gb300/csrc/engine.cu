@@ -78,6 +78,7 @@ int64_t kpart_stride(const pexsi_plan* p) {
 
 int64_t bytes_per_pole(const pexsi_plan* p) {
   return (2 * p->sym.front_elems + p->part_stride + kpart_stride(p)) * int64_t(sizeof(double2)) +
+         2 * p->sym.n * int64_t(p->b) * int64_t(sizeof(double)) +
          std::max(p->ozA_stride, 2 * p->ozA_stride_r) + std::max(p->ozB_stride, 2 * p->ozB_stride_r) +
          8 * (p->exA_stride + p->exB_stride) + 4 * p->ymax_stride;
 }
@@ -124,6 +125,9 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
   wsalloc(&ws.S, sizeof(double) * nnz, ws, "alloc(S)");
   wsalloc(&ws.out, sizeof(double) * nnz * 4, ws, "alloc(outputs)");
   // status words: [0] the pole chain (DM calls), [1] the inertia shifts
+  // the inertia shifts' panel blocks before inversion: n x b per member, up to
+  // 2 batch real members (or batch complex Hermitian ones)
+  wsalloc(&ws.dsave, sizeof(double) * size_t(p->sym.n) * p->b * 2 * batch, ws, "alloc(inertia blocks)");
   wsalloc(&ws.brk, 2 * sizeof(int), ws, "alloc(status)");
   wsalloc(&ws.minpiv, 2 * sizeof(unsigned long long), ws, "alloc(status)");
   wsalloc(&ws.neg, sizeof(int) * kMaxBatch, ws, "alloc(status)");
@@ -146,7 +150,8 @@ void workspace_alloc(const pexsi_plan* p, Workspace& ws, int batch, cudaStream_t
 
 void workspace_free(Workspace& ws) {
   void* ptrs[] = {ws.F,  ws.Y,        ws.part,  ws.H,    ws.S,   ws.out, ws.brk, ws.minpiv, ws.neg,
-                  ws.partials, ws.trace3, ws.ainv, ws.ozA, ws.ozB, ws.exA, ws.exB, ws.ozfail, ws.ymax, ws.kpart};
+                  ws.partials, ws.trace3, ws.ainv, ws.ozA, ws.ozB, ws.exA, ws.exB, ws.ozfail, ws.ymax, ws.kpart,
+                  ws.dsave};
   for (void* q : ptrs) {
     if (!q) continue;
     if (ws.async) cudaFreeAsync(q, ws.stream);
@@ -254,8 +259,10 @@ template <typename T>
 void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& sh, bool count, Profiler& pf) {
   cudaStream_t st = ws.stream;
   DevFronts fr = p->fronts();
-  // the inertia shifts (count) keep their own status words
-  DevStatus status{ws.brk + (count ? 1 : 0), ws.minpiv + (count ? 1 : 0), ws.neg};
+  // the inertia shifts (count) keep their own status words; their panel blocks
+  // are saved and counted after the factorisation
+  DevStatus status{ws.brk + (count ? 1 : 0), ws.minpiv + (count ? 1 : 0), ws.neg, count ? ws.dsave : nullptr,
+                   p->d_col0, p->sym.n * int64_t(p->b)};
   const int b = p->b;
   const double es = double(sizeof(T)), fl = sizeof(T) == 16 ? 8.0 : 2.0, nb = sh.nb;
   for (size_t L = 0; L < p->levels.size(); ++L) {
@@ -352,6 +359,11 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
         pf.end(a, P_SCHUR, st, nb * w.schur_fl, nb * w.schur_by);
       }
     }
+  }
+  if (count) {
+    cudaEvent_t a = pf.begin(st);
+    launch_bk_count_all<T>(p->d_bk_slots, p->n_bk_slots, fr, b, sh.nb, status, st);
+    pf.end(a, P_DIAG, st, 0.0, 0.0);
   }
   ck(cudaGetLastError(), "factor kernels");
 }
@@ -607,7 +619,8 @@ namespace {
 void factor_batch_gen(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, bool count, Profiler& pf) {
   cudaStream_t st = ws.stream;
   DevFronts fr = p->fronts();
-  DevStatus status{ws.brk + (count ? 1 : 0), ws.minpiv + (count ? 1 : 0), ws.neg};
+  DevStatus status{ws.brk + (count ? 1 : 0), ws.minpiv + (count ? 1 : 0), ws.neg, count ? ws.dsave : nullptr,
+                   p->d_col0, p->sym.n * int64_t(p->b)};
   const int b = p->b;
   const double nb = sh.nb;
   for (size_t L = 0; L < p->levels.size(); ++L) {
@@ -636,6 +649,7 @@ void factor_batch_gen(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh,
       pf.end(a, P_PANEL, st, nb * w.panel_fl, nb * w.panel_by);
     }
   }
+  if (count) launch_bk_count_all<double2>(p->d_bk_slots, p->n_bk_slots, fr, b, sh.nb, status, st);
   ck(cudaGetLastError(), "LDU factor kernels");
 }
 
@@ -943,7 +957,8 @@ void free_plan_device(pexsi_plan* p) {
   void* ptrs[] = {p->d_front_off, p->d_s, p->d_m, p->d_parent, p->d_rel, p->d_rptr, p->d_asm_src, p->d_asm_pos,
                   p->d_entry_pos, p->d_level_fronts, p->d_ea, p->d_tile_pref, p->d_part_off, p->d_ident,
                   p->d_ozA_off, p->d_ozB_off, p->d_exA_off, p->d_exB_off, p->d_ozA_off_r, p->d_ozB_off_r,
-                  p->d_ymax_off, p->d_pos_full, p->d_pos_t, p->d_ident_c, p->d_hH, p->d_hS, p->d_hout};
+                  p->d_ymax_off, p->d_pos_full, p->d_pos_t, p->d_ident_c, p->d_hH, p->d_hS, p->d_hout,
+                  p->d_col0, p->d_bk_slots};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   cudaStream_t st = p->ws.stream;
@@ -1180,6 +1195,19 @@ int upload_plan(pexsi_plan* p) {
   p->d_ea = dev_upload(ea);
   p->d_tile_pref = dev_upload(tile_pref);
   p->d_part_off = dev_upload(part_off);
+  {
+    std::vector<int32_t> col0(S.nsuper), slots;
+    for (int32_t K = 0; K < S.nsuper; ++K) {
+      col0[K] = S.first[K];
+      for (int32_t p0 = 0; p0 < S.s(K); p0 += p->b) {
+        slots.push_back(K);
+        slots.push_back(p0);
+      }
+    }
+    p->d_col0 = dev_upload(col0);
+    p->d_bk_slots = dev_upload(slots);
+    p->n_bk_slots = int32_t(slots.size() / 2);
+  }
   if (p->oz_slices > 0) {
     std::vector<int64_t> oa, ob, xa, xb, ra, rb;
     build_split_layout(p, oa, ob, xa, xb, ra, rb);

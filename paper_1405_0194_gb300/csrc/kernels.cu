@@ -570,7 +570,14 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&s_max), __double_as_longlong(lmax));
   __syncthreads();
 
-  if (count_inertia) {
+  if (count_inertia && st.dsave) {
+    // the block as it is before inversion, counted later (launch_bk_count_all)
+    T* save = reinterpret_cast<T*>(st.dsave) + int64_t(pb) * st.dsave_stride + int64_t(st.col0[f] + p0) * b;
+    for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+      const int i = idx / bb, j = idx % bb;
+      save[i * b + j] = Aug[i * ld + j];
+    }
+  } else if (count_inertia) {
     // Bunch-Kaufman count on a copy placed after the augmented matrix
     // (real symmetric blocks, or Hermitian ones of an LDU front with a real shift)
     if constexpr (sizeof(T) == sizeof(double) || GEN) {
@@ -786,6 +793,32 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __re
     const double ratio = mx > 0 ? pmin / mx : 0.0;
     atomicMin(st.min_pivot, (unsigned long long)__double_as_longlong(ratio));
     if (bad || ratio < 1e-13) atomicMin(st.breakdown_front, f);
+  }
+}
+
+// Deferred inertia count: one CTA per (saved panel block, batch member).
+template <typename T>
+__global__ void __launch_bounds__(kDiagThreads) k_bk_count_all(const int32_t* __restrict__ slots, DevFronts fr, int b,
+                                                               DevStatus st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Bm = reinterpret_cast<T*>(smem_raw);  // bb x bb, row stride b
+  const int f = slots[2 * blockIdx.x], p0 = slots[2 * blockIdx.x + 1];
+  const int pb = blockIdx.y;
+  const int bb = min(b, fr.s[f] - p0);
+  const T* save = reinterpret_cast<const T*>(st.dsave) + int64_t(pb) * st.dsave_stride + int64_t(st.col0[f] + p0) * b;
+  for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+    const int i = idx / bb, j = idx % bb;
+    Bm[i * b + j] = save[i * b + j];
+  }
+  __syncthreads();
+  __shared__ int s_neg;
+  __shared__ bool s_sing;
+  if (threadIdx.x == 0) s_sing = false;
+  __syncthreads();
+  bk_count<T>(Bm, bb, b, &s_neg, &s_sing);
+  if (threadIdx.x == 0) {
+    if (s_neg) atomicAdd(&st.neg_count[pb], s_neg);
+    if (s_sing) atomicMin(st.breakdown_front, f);
   }
 }
 
@@ -1339,6 +1372,9 @@ cudaError_t configure_kernels(int b) {
   e = cudaFuncSetAttribute(k_diag_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_r));
   if (e != cudaSuccess) return e;
   // LDU fronts: the Hermitian inertia count keeps a complex copy of the block
+  e = cudaFuncSetAttribute(k_bk_count_all<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(sizeof(double2) * b * b));
+  if (e != cudaSuccess) return e;
   const size_t need_g = sizeof(double2) * size_t(b) * (b + 1) + sizeof(double2) * b * b;
   e = cudaFuncSetAttribute(k_diag_inv<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_g));
   if (e != cudaSuccess) return e;
@@ -1428,6 +1464,15 @@ void launch_pole_sum_herm(const double2* Y, int64_t pool, const int64_t* pos, co
                           cudaStream_t st) {
   k_pole_sum_herm<<<grid_for(nnz, 256), 256, 0, st>>>(Y, pool, pos, pos_t, nnz, sh, overwrite, dm, edm, fdm, ddm);
 }
+
+template <typename T>
+void launch_bk_count_all(const int32_t* slots, int nslots, const DevFronts& fr, int b, int nb, DevStatus status,
+                         cudaStream_t st) {
+  if (nslots <= 0 || nb <= 0) return;
+  k_bk_count_all<T><<<dim3(nslots, nb), kDiagThreads, sizeof(T) * b * b, st>>>(slots, fr, b, status);
+}
+template void launch_bk_count_all<double>(const int32_t*, int, const DevFronts&, int, int, DevStatus, cudaStream_t);
+template void launch_bk_count_all<double2>(const int32_t*, int, const DevFronts&, int, int, DevStatus, cudaStream_t);
 
 #define PEXSI_INSTANTIATE(T)                                                                                        \
   template void launch_assemble<T>(T*, const double*, const double*, const int64_t*, const int64_t*, int64_t,    \

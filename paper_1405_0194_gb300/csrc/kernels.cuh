@@ -38,6 +38,12 @@ struct DevStatus {
   int* breakdown_front;              // atomicMin of the first failing front (INT_MAX = none)
   unsigned long long* min_pivot;     // atomicMin of the bit pattern of min |pivot| / max |entry|
   int* neg_count;                    // per batch member: negative eigenvalues of D (inertia)
+  // inertia: the panel blocks D saved before inversion, counted afterwards by
+  // launch_bk_count_all off the factorisation's critical path; the block of
+  // (front f, panel p0) of member b sits at dsave + b * dsave_stride + (col0[f] + p0) * b_panel
+  void* dsave;
+  const int32_t* col0;               // first column of each front
+  int64_t dsave_stride;
 };
 
 // Scratch of the split-precision GEMM: bf16 slice tiles of A = Y[S,S] and
@@ -198,6 +204,14 @@ void launch_selinv_diag_reduce_gen(double2* Y, const double2* F, const double2* 
 void launch_pole_sum_herm(const double2* Y, int64_t pool, const int64_t* pos, const int64_t* pos_t, int64_t nnz,
                           const BatchShifts& sh, int overwrite, double2* dm, double2* edm, double2* fdm, double2* ddm,
                           cudaStream_t st);
+
+// Inertia counts of all saved panel blocks (slots: (front, p0) pairs, nslots
+// of them) for nb batch members: one CTA per block and member, a Bunch-Kaufman
+// LDL^T (real, or Hermitian for T = double2) adding its negative eigenvalues
+// to status.neg_count and flagging singular blocks.
+template <typename T>
+void launch_bk_count_all(const int32_t* slots, int nslots, const DevFronts& fr, int b, int nb, DevStatus status,
+                         cudaStream_t st);
 
 // Raises the dynamic shared-memory limits the kernels need for panel width b.
 cudaError_t configure_kernels(int b);

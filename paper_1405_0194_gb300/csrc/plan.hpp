@@ -83,6 +83,7 @@ struct Workspace {
   int batch = 0;
   double2 *F = nullptr, *Y = nullptr, *part = nullptr;
   double2* kpart = nullptr;  // split-K partials of the FP64 Takahashi step
+  void* dsave = nullptr;     // inertia shifts: panel blocks before inversion (counted afterwards)
   int* brk = nullptr;
   unsigned long long* minpiv = nullptr;
   int* neg = nullptr;
@@ -140,6 +141,8 @@ struct pexsi_plan {
   // front position of each CSC entry and of its transpose, a complex
   // identity S, and the plan API's complex staging (H, S: nnz; outputs: 4 nnz)
   int64_t *d_pos_full = nullptr, *d_pos_t = nullptr;
+  int32_t *d_col0 = nullptr, *d_bk_slots = nullptr;  // first column per front; (front, p0) of every panel
+  int32_t n_bk_slots = 0;
   std::vector<int64_t> diag_entries;  // CSC entries on the diagonal
   // A plan that merges several systems (pexsi_group): the first CSC entry of
   // each system among the concatenated entries (nsys + 1), and each system's
