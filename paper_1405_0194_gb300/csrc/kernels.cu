@@ -180,28 +180,46 @@ __device__ __forceinline__ void gemm_tile_3m(double2 (&acc)[4][4], const double2
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
+  // The global loads of the next 16-deep chunk are issued into registers
+  // before the current chunk's multiply-adds, so that their latency hides
+  // behind them (one CTA per SM leaves no other CTA to cover it).
+  double2 va[4], vb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q, r, k;
+      if (!AT) { r = idx & 63; k = idx >> 6; }
+      else { k = idx & 15; r = idx >> 4; }
+      va[q] = make_double2(0.0, 0.0);
+      if (r < Mv && k0 + k < K) va[q] = AT ? A[(k0 + k) + lda * r] : A[r + lda * (k0 + k)];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = tid + 256 * q, k = idx & 15, c = idx >> 4;
+      vb[q] = make_double2(0.0, 0.0);
+      if (c < Nv && k0 + k < K) vb[q] = B[(k0 + k) + ldb * c];
+    }
+  };
+  if (K > 0) load(0);
   for (int k0 = 0; k0 < K; k0 += kKc) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int idx = tid + 256 * q, r, k;
       if (!AT) { r = idx & 63; k = idx >> 6; }
       else { k = idx & 15; r = idx >> 4; }
-      double2 v = make_double2(0.0, 0.0);
-      if (r < Mv && k0 + k < K) v = AT ? A[(k0 + k) + lda * r] : A[r + lda * (k0 + k)];
-      Ar[k * kLd + r] = v.x;
-      Ai[k * kLd + r] = v.y;
-      As[k * kLd + r] = v.x + v.y;
+      Ar[k * kLd + r] = va[q].x;
+      Ai[k * kLd + r] = va[q].y;
+      As[k * kLd + r] = va[q].x + va[q].y;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int idx = tid + 256 * q, k = idx & 15, c = idx >> 4;
-      double2 v = make_double2(0.0, 0.0);
-      if (c < Nv && k0 + k < K) v = B[(k0 + k) + ldb * c];
-      Br[k * kLd + c] = v.x;
-      Bi[k * kLd + c] = v.y;
-      Bs[k * kLd + c] = v.x + v.y;
+      Br[k * kLd + c] = vb[q].x;
+      Bi[k * kLd + c] = vb[q].y;
+      Bs[k * kLd + c] = vb[q].x + vb[q].y;
     }
     __syncthreads();
+    if (k0 + kKc < K) load(k0 + kKc);
 #pragma unroll 2
     for (int k = 0; k < kKc; ++k) {
       double ar[4], ai[4], as[4], br[4], bi[4], bs[4];
