@@ -416,6 +416,11 @@ def run_ours(args):
     roofline["traffic"] = traffic_of(args.workload, dom, args.split)
 
     latency = dm_latency(px, plan, s, mu, dE, args.latency_calls) if args.latency_calls > 0 else None
+    # the 16 inertia shifts of a counting cycle (Sec. II.C) in one call
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    px.pexsi_inertia_device(plan, dH.data_ptr(), dS.data_ptr(), all_shifts, stream)
+    inertia_ms = 1e3 * (time.perf_counter() - t0)
     line = {
         "metric": "pole-solves/sec", "value": value, "unit": "pole-solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -435,6 +440,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "pole-solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
         "dm_latency": latency,
+        "inertia_16_shifts": {"ms": inertia_ms, "shifts_per_s": 16 / (inertia_ms / 1e3),
+                              "call": "pexsi_inertia_device, 16 shifts in [mu - 0.5, mu + 0.5] Ha"},
         "gpu_launches": int(round(per_step_launches * args.steps)),
         "clocks": clk,
         "peaks_source": peak_src,
