@@ -159,6 +159,8 @@ void workspace_free(Workspace& ws) {
   }
   if (ws.ev0) cudaEventDestroy(ws.ev0);
   if (ws.ev1) cudaEventDestroy(ws.ev1);
+  for (Workspace::Graph& g : ws.graphs) cudaGraphExecDestroy(g.exec);
+  if (ws.capture) cudaStreamDestroy(ws.capture);
   cudaStream_t st = ws.stream;
   bool async = ws.async;
   ws = Workspace();
@@ -466,6 +468,52 @@ int split_failed(Workspace& ws, int which, std::string* err, const char* what) {
 
 // One batch of complex shifts through assembly, factorisation and selected
 // inversion; the result is left in ws.Y.
+// Factorisation and selected inversion of the nb assembled poles in ws.F.
+// Their launches depend on nb (and on the plan, the workspace's buffers and
+// the Schur block width) but not on the shifts, so they are captured once
+// into a CUDA graph per (nb, block width) and replayed on ws.stream: one
+// launch instead of thousands, which matters for the short launches of small
+// fronts. Captured on the workspace's own capture stream (the legacy default
+// stream cannot capture); with the profiler on, and for the server's
+// per-request workspaces (whose buffers live for one request), the kernels
+// are launched directly.
+void factor_selinv(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Profiler& pf) {
+  if (pf.on || !ws.use_graphs) {
+    factor_batch<double2>(p, ws, ws.F, sh, false, pf);
+    selinv_batch(p, ws, sh, pf);
+    return;
+  }
+  for (Workspace::Graph& g : ws.graphs)
+    if (g.nb == sh.nb && g.block == p->oz_block) {
+      ck(cudaGraphLaunch(g.exec, ws.stream), "cudaGraphLaunch");
+      return;
+    }
+  if (!ws.capture) ck(cudaStreamCreateWithFlags(&ws.capture, cudaStreamNonBlocking), "cudaStreamCreate(capture)");
+  cudaStream_t run = ws.stream;
+  ws.stream = ws.capture;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    try {
+      factor_batch<double2>(p, ws, ws.F, sh, false, g_off);
+      selinv_batch(p, ws, sh, g_off);
+    } catch (...) {
+      cudaStreamEndCapture(ws.capture, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      ws.stream = run;
+      throw;
+    }
+    e = cudaStreamEndCapture(ws.capture, &graph);
+  }
+  ws.stream = run;
+  Workspace::Graph g{sh.nb, p->oz_block, nullptr};
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  ck(e, "CUDA graph capture of the level schedule");
+  ws.graphs.push_back(g);
+  ck(cudaGraphLaunch(g.exec, ws.stream), "cudaGraphLaunch");
+}
+
 void run_complex_batch(const pexsi_plan* p, Workspace& ws, const double* dH, const double* dS, const BatchShifts& sh,
                        Profiler& pf) {
   const int64_t pool = p->sym.front_elems;
@@ -473,8 +521,7 @@ void run_complex_batch(const pexsi_plan* p, Workspace& ws, const double* dH, con
   cudaEvent_t a = pf.begin(ws.stream);
   launch_assemble<double2>(ws.F, dH, dS, p->d_asm_src, p->d_asm_pos, p->nlow, pool, sh, ws.stream);
   pf.end(a, P_ASSEMBLE, ws.stream, 0.0, double(p->nlow) * (32.0 + 16.0 * sh.nb));
-  factor_batch<double2>(p, ws, ws.F, sh, false, pf);
-  selinv_batch(p, ws, sh, pf);
+  factor_selinv(p, ws, sh, pf);
 }
 
 }  // namespace
@@ -899,8 +946,7 @@ int dm_range_group(const pexsi_plan* p, Workspace& ws, Profiler* prof, int wave,
       launch_assemble<double2>(ws.F, dH[q], S, p->d_asm_src + a0, p->d_asm_pos + a0, na, pool, sh[q], st);
       pf.end(a, P_ASSEMBLE, st, 0.0, double(na) * (32.0 + 16.0 * nb));
     }
-    factor_batch<double2>(p, ws, ws.F, sh[0], false, pf);
-    selinv_batch(p, ws, sh[0], pf);
+    factor_selinv(p, ws, sh[0], pf);
     const int overwrite = (first && !accumulate) ? 1 : 0;
     for (int q = 0; q < nsys; ++q) {
       const int64_t e0 = p->sys_entry_off[q], ne = p->sys_entry_off[q + 1] - e0;

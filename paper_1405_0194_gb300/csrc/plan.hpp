@@ -96,6 +96,15 @@ struct Workspace {
   uint32_t* ymax = nullptr;  // split path: row maxima of Y per pole
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // captured level schedules (factorisation + selected inversion of nb
+  // complex poles at a Schur block width) and the stream they are captured on
+  struct Graph {
+    int nb, block;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t capture = nullptr;
+  bool use_graphs = true;
   bool async = false;  // buffers from cudaMallocAsync on `stream`
   int64_t bytes = 0;
 };

@@ -82,6 +82,7 @@ int execute(Request& r, cudaStream_t st, std::string* err) {
   const size_t nnz = size_t(p->sym.nnz);
   pexsi::Workspace ws;
   ws.stream = st;
+  ws.use_graphs = false;  // a request's workspace lives for one request
   int rc = PEXSI_OK;
   try {
     pexsi::workspace_alloc(p, ws, r.batch, st, true);
