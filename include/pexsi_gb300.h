@@ -407,9 +407,11 @@ int pexsi_ldos(pexsi_plan* plan, const double* H, const double* S, double eps, d
  * A continuous-batching request loop for DM and inertia solves of systems of
  * different sizes (the serving pattern around Sec. II.C's inertia counting and
  * Sec. II.A's pole expansion). The server owns `slots` worker threads, each
- * with its own CUDA stream. A request waits in a FIFO queue until a slot is
- * free AND its device footprint (fronts of `batch` poles of its plan plus
- * staging) fits the HBM budget still unused; it is then admitted, its
+ * with its own CUDA stream. Requests queue in arrival order; when a slot is
+ * free, the first one whose device footprint (fronts of `batch` poles of its
+ * plan plus staging) fits the HBM budget still unused is admitted (a request
+ * passed over 8 times by later, smaller ones holds back everything behind it
+ * until it fits, so none starves); its
  * workspace is taken from the stream-ordered allocator, and its kernels run
  * concurrently with those of the other admitted requests. Plans (symbolic
  * structure and device maps) stay resident across requests; several requests

@@ -2,9 +2,11 @@
 // different sizes, admitted by device-memory footprint, running concurrently
 // on per-slot CUDA streams.
 //
-// Admission: FIFO; the head request is admitted when a slot is idle and its
-// footprint (workspace for `batch` poles of its plan, from the stream-ordered
-// allocator) fits the budget that running requests leave free. Requests that
+// Admission: when a slot is idle, the first queued request (in arrival order)
+// whose footprint (workspace for `batch` poles of its plan, from the
+// stream-ordered allocator) fits the budget that running requests leave free;
+// a request passed over kMaxBypass times blocks the ones behind it until it
+// fits, so large requests are not starved. Requests that
 // arrive while others run are admitted as slots and memory free up, and their
 // kernels overlap on the device with those of the running requests.
 #include <algorithm>
@@ -40,6 +42,7 @@ struct Request {
   int64_t footprint = 0;
   enum State { QUEUED, RUNNING, DONE } state = QUEUED;
   std::atomic<bool> cancel{false};
+  int bypassed = 0;  // times a later request was admitted before this one
   pexsi_result res{};
   Clock::time_point t_submit, t_start, t_end;
 };
@@ -134,6 +137,21 @@ int execute(Request& r, cudaStream_t st, std::string* err) {
   return rc;
 }
 
+// The queued request to admit next: the first (in arrival order) whose
+// footprint fits what running requests leave of the budget. A request may be
+// passed over by later, smaller ones at most kMaxBypass times; after that
+// nothing behind it is admitted until it fits, so a large request cannot
+// starve. Returns queue.end() when none may run now.
+constexpr int kMaxBypass = 8;
+
+std::deque<std::shared_ptr<Request>>::iterator next_admissible(pexsi_server* s) {
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if (s->in_use + (*it)->footprint <= s->budget) return it;
+    if ((*it)->bypassed >= kMaxBypass) break;  // it waits for room; no one passes it
+  }
+  return s->queue.end();
+}
+
 void worker(pexsi_server* s, int slot) {
   cudaSetDevice(s->opts.device);
   cudaStream_t st = s->streams[slot];
@@ -141,16 +159,16 @@ void worker(pexsi_server* s, int slot) {
     std::shared_ptr<Request> r;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] {
-        return s->stop || (!s->queue.empty() && s->in_use + s->queue.front()->footprint <= s->budget);
-      });
+      s->cv_work.wait(lk, [&] { return s->stop || next_admissible(s) != s->queue.end(); });
       if (s->stop && s->queue.empty()) return;
-      if (s->queue.empty() || s->in_use + s->queue.front()->footprint > s->budget) {
+      auto it = next_admissible(s);
+      if (it == s->queue.end()) {
         if (s->stop) return;
         continue;
       }
-      r = s->queue.front();
-      s->queue.pop_front();
+      for (auto q = s->queue.begin(); q != it; ++q) ++(*q)->bypassed;
+      r = *it;
+      s->queue.erase(it);
       r->state = Request::RUNNING;
       r->t_start = Clock::now();
       s->in_use += r->footprint;
