@@ -109,3 +109,40 @@ def test_cancel_and_bad_requests(systems):
         px.pexsi_server_destroy(server)
     assert res[-1]["status"] == -7
     assert all(x["status"] == 0 for x in res[:-1])
+
+
+def test_small_request_passes_a_large_one_that_does_not_fit(systems):
+    """Under a budget that holds the large request alone or the small ones
+    beside the one running, a small request queued behind a large one that
+    does not fit yet is admitted first (the large one runs once there is
+    room; bypasses are bounded, so it still runs)."""
+    small_s, mu_s, dE_s, small_plan = systems[0]   # chain64, n = 256
+    big_s, mu_b, dE_b, big_plan = systems[2]        # sheet8, n = 1,664
+    server = px.pexsi_server_create(px.pexsi_server_opts_default(slots=4, batch=8))
+    probes = [px.ServerRequest(p, s.H, s.S, mu=m, beta=s.beta, n_poles=16, delta_e=d)
+              for s, m, d, p in ((small_s, mu_s, dE_s, small_plan), (big_s, mu_b, dE_b, big_plan))]
+    fps = []
+    for r in probes:
+        px.pexsi_server_submit(server, r)
+        fps.append(px.pexsi_server_wait(server, r.ticket)["footprint_bytes"])
+    px.pexsi_server_destroy(server)
+    fs, fb = fps
+    assert fb > 2 * fs
+    # room for the large one alone, or for a few small ones, not for both
+    server = px.pexsi_server_create(px.pexsi_server_opts_default(slots=4, batch=8, hbm_budget=int(fb + 0.5 * fs)))
+    try:
+        first = px.ServerRequest(small_plan, small_s.H, small_s.S, mu=mu_s, beta=small_s.beta, n_poles=40,
+                                 delta_e=dE_s)
+        big = px.ServerRequest(big_plan, big_s.H, big_s.S, mu=mu_b, beta=big_s.beta, n_poles=16, delta_e=dE_b)
+        late = px.ServerRequest(small_plan, small_s.H, small_s.S, mu=mu_s, beta=small_s.beta, n_poles=8,
+                                delta_e=dE_s)
+        for r in (first, big, late):
+            px.pexsi_server_submit(server, r)
+        res = [px.pexsi_server_wait(server, r.ticket) for r in (first, big, late)]
+    finally:
+        px.pexsi_server_destroy(server)
+    assert all(x["status"] == 0 for x in res)
+    r_first, r_big, r_late = res
+    # the late small request ran beside the first one, before the large one started
+    assert r_late["max_concurrent"] == 2
+    assert r_big["queue_ms"] > r_late["queue_ms"]
