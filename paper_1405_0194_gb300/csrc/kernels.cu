@@ -690,15 +690,15 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
 // passed the barrier of step k + 1, after its update of step k. The final
 // column interchanges are applied when the columns are written back. One
 // inversion thus runs on kDiagCluster SMs' FP64 pipes instead of one.
-template <bool GEN, int kDiagCluster>
-__global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __restrict__ F, DevFronts fr,
+template <typename T, bool GEN, int kDiagCluster>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(T* __restrict__ F, DevFronts fr,
                                                                    const int32_t* __restrict__ fronts, int p0, int b,
                                                                    DevStatus st) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ double2 A[64][64 / kDiagCluster + 1];  // this CTA's columns (row-major in i)
-  __shared__ double2 pub_fac[2][64];
-  __shared__ double2 pub_inv[2];
+  __shared__ T A[64][64 / kDiagCluster + 1];  // this CTA's columns (row-major in i)
+  __shared__ T pub_fac[2][64];
+  __shared__ T pub_inv[2];
   __shared__ int pub_piv[2];
   __shared__ double pub_best[2];
   __shared__ double s_maxes[kDiagCluster];
@@ -712,15 +712,22 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __re
   const int bb = min(b, s - p0);
   const int W = (bb + kDiagCluster - 1) / kDiagCluster;
   const int c0 = r * W, nc = max(0, min(bb, c0 + W) - c0);
-  double2* Fd = F + int64_t(pb) * fr.pool + fr.off[f] + p0 + int64_t(m) * p0;
+  T* Fd = F + int64_t(pb) * fr.pool + fr.off[f] + p0 + int64_t(m) * p0;
   if (threadIdx.x == 0) s_lmax = 0.0;
   __syncthreads();
   double lmax = 0.0;
   for (int idx = threadIdx.x; idx < bb * nc; idx += blockDim.x) {
     const int i = idx % bb, jl = idx / bb, j = c0 + jl;
-    const double2 v = (GEN || i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
+    const T v = (GEN || i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
     A[i][jl] = v;
     lmax = fmax(lmax, absv(v));
+  }
+  if (st.dsave) {  // inertia shifts: this CTA's columns of the block before inversion, counted later
+    T* save = reinterpret_cast<T*>(st.dsave) + int64_t(pb) * st.dsave_stride + int64_t(st.col0[f] + p0) * b;
+    for (int idx = threadIdx.x; idx < bb * nc; idx += blockDim.x) {
+      const int i = idx % bb, jl = idx / bb;
+      save[i * b + c0 + jl] = A[i][jl];
+    }
   }
   for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&s_lmax), __double_as_longlong(lmax));
@@ -754,14 +761,14 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __re
       const int pr = pub_piv[par];
       if (pr != k)
         for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) {
-          const double2 t = A[k][jl]; A[k][jl] = A[pr][jl]; A[pr][jl] = t;
+          const T t = A[k][jl]; A[k][jl] = A[pr][jl]; A[pr][jl] = t;
         }
       __syncthreads();
       const double best = pub_best[par];
       const bool now_bad = bad || !(best > 0.0) || !isfinite(best);
-      const double2 inv = now_bad ? zero_of(double2()) : recipv(A[k][lk]);
+      const T inv = now_bad ? zero_of(T()) : recipv(A[k][lk]);
       for (int q = 0; q < kDiagCluster; ++q) {  // publish into every CTA of the cluster
-        double2* fac = cluster.map_shared_rank(&pub_fac[par][0], q);
+        T* fac = cluster.map_shared_rank(&pub_fac[par][0], q);
         for (int i = threadIdx.x; i < bb; i += blockDim.x) fac[i] = A[i][lk];
         if (threadIdx.x == 0) {
           *cluster.map_shared_rank(&pub_inv[par], q) = inv;
@@ -773,23 +780,23 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(double2* __re
     cluster.sync();
     const int pr = pub_piv[par];
     const double best = pub_best[par];
-    const double2 inv = pub_inv[par];
+    const T inv = pub_inv[par];
     bad = bad || !(best > 0.0) || !isfinite(best);
     pmin = fmin(pmin, best);
     if (threadIdx.x == 0) s_perm[k] = pr;
     if (r != owner && pr != k)
       for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) {
-        const double2 t = A[k][jl]; A[k][jl] = A[pr][jl]; A[pr][jl] = t;
+        const T t = A[k][jl]; A[k][jl] = A[pr][jl]; A[pr][jl] = t;
       }
     __syncthreads();
     // row k scaled by the pivot's reciprocal; column k keeps the multipliers' negatives over the pivot
     for (int jl = threadIdx.x; jl < nc; jl += blockDim.x) A[k][jl] = (c0 + jl == k) ? inv : mulv(A[k][jl], inv);
     __syncthreads();
-    const double2* fac = pub_fac[par];
+    const T* fac = pub_fac[par];
     for (int idx = threadIdx.x; idx < bb * nc; idx += blockDim.x) {
       const int i = idx / nc, jl = idx % nc;
       if (i == k) continue;
-      A[i][jl] = (c0 + jl == k) ? fmsv(zero_of(double2()), fac[i], inv) : fmsv(A[i][jl], fac[i], A[k][jl]);
+      A[i][jl] = (c0 + jl == k) ? fmsv(zero_of(T()), fac[i], inv) : fmsv(A[i][jl], fac[i], A[k][jl]);
     }
     __syncthreads();
   }
@@ -1260,8 +1267,8 @@ void launch_extend_add(T* F, const DevFronts& fr, const int32_t* children, int n
 
 // One cluster of C CTAs per block inverse (complex poles, which need no
 // inertia count).
-template <bool GEN, int C>
-void launch_diag_inv_cluster_c(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+template <typename T, bool GEN, int C>
+void launch_diag_inv_cluster_c(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                                const BatchShifts& sh, DevStatus status, cudaStream_t st) {
   constexpr int kDiagCluster = C;
   cudaLaunchConfig_t cfg = {};
@@ -1276,7 +1283,7 @@ void launch_diag_inv_cluster_c(double2* F, const DevFronts& fr, const int32_t* f
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_diag_inv_cluster<GEN, C>, F, fr, fronts, p0, b, status);
+  cudaLaunchKernelEx(&cfg, k_diag_inv_cluster<T, GEN, C>, F, fr, fronts, p0, b, status);
 }
 
 // The cluster size: wide enough to spread the launch's inversions over the
@@ -1285,13 +1292,13 @@ int diag_cluster_size(int inversions) {
   return inversions >= 152 ? 1 : inversions >= 76 ? 2 : inversions >= 38 ? 4 : 8;
 }
 
-template <bool GEN>
-bool launch_diag_inv_cluster(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
+template <typename T, bool GEN>
+bool launch_diag_inv_cluster(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                              const BatchShifts& sh, DevStatus status, cudaStream_t st) {
   switch (diag_cluster_size(nfronts * sh.nb)) {
-    case 8: launch_diag_inv_cluster_c<GEN, 8>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
-    case 4: launch_diag_inv_cluster_c<GEN, 4>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
-    case 2: launch_diag_inv_cluster_c<GEN, 2>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
+    case 8: launch_diag_inv_cluster_c<T, GEN, 8>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
+    case 4: launch_diag_inv_cluster_c<T, GEN, 4>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
+    case 2: launch_diag_inv_cluster_c<T, GEN, 2>(F, fr, fronts, nfronts, p0, b, sh, status, st); return true;
     default: return false;
   }
 }
@@ -1300,11 +1307,11 @@ template <typename T>
 void launch_diag_inv(T* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                      const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
   if (nfronts <= 0) return;
-  if constexpr (sizeof(T) == sizeof(double2)) {
-    if (!count_inertia && b <= 64 &&
-        launch_diag_inv_cluster<false>(reinterpret_cast<double2*>(F), fr, fronts, nfronts, p0, b, sh, status, st))
-      return;
-  }
+  // the cluster kernel: complex poles, and inertia shifts whose blocks are
+  // saved for the deferred count
+  if ((!count_inertia || status.dsave) && b <= 64 &&
+      launch_diag_inv_cluster<T, false>(F, fr, fronts, nfronts, p0, b, sh, status, st))
+    return;
   size_t smem = sizeof(T) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
   k_diag_inv<T><<<grid, kDiagThreads, smem, st>>>(F, fr, fronts, p0, b, status, count_inertia ? 1 : 0);
@@ -1431,7 +1438,8 @@ void launch_extend_add_full(double2* F, const DevFronts& fr, const int32_t* chil
 void launch_diag_inv_gen(double2* F, const DevFronts& fr, const int32_t* fronts, int nfronts, int p0, int b,
                          const BatchShifts& sh, DevStatus status, bool count_inertia, cudaStream_t st) {
   if (nfronts <= 0) return;
-  if (!count_inertia && b <= 64 && launch_diag_inv_cluster<true>(F, fr, fronts, nfronts, p0, b, sh, status, st))
+  if ((!count_inertia || status.dsave) && b <= 64 &&
+      launch_diag_inv_cluster<double2, true>(F, fr, fronts, nfronts, p0, b, sh, status, st))
     return;
   size_t smem = sizeof(double2) * size_t(b) * (b + 1) + (count_inertia ? sizeof(double2) * b * b : 0);
   dim3 grid(nfronts, sh.nb);
