@@ -352,6 +352,7 @@ template <>
 __device__ void bk_count<double2>(double2* Bm, int n, int ld, int* out_neg, bool* singular) {
   __shared__ int s_piv[3];
   __shared__ int s_neg;
+  __shared__ double s_div;
   __shared__ double2 s_u[64], s_w[64];
   const double alpha = (1.0 + sqrt(17.0)) / 8.0;
   if (threadIdx.x == 0) s_neg = 0;
@@ -410,7 +411,9 @@ __device__ void bk_count<double2>(double2* Bm, int n, int ld, int* out_neg, bool
         if (d < 0) ++s_neg;
         if (d == 0.0) *singular = true;
       }
-      const double inv = d != 0.0 ? 1.0 / d : 0.0;
+      if (threadIdx.x == 0) s_div = d != 0.0 ? 1.0 / d : 0.0;  // one division per pivot
+      __syncthreads();
+      const double inv = s_div;
       // u_j = D(k, j) / d = conj(D(j, k)) / d
       for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) s_u[j] = scalev(conjv(Bm[j * ld + k]), inv);
       __syncthreads();
@@ -429,7 +432,9 @@ __device__ void bk_count<double2>(double2* Bm, int n, int ld, int* out_neg, bool
         else if (det > 0 && a + c < 0) s_neg += 2;
         if (det == 0.0) *singular = true;
       }
-      const double id = det != 0.0 ? 1.0 / det : 0.0;
+      if (threadIdx.x == 0) s_div = det != 0.0 ? 1.0 / det : 0.0;
+      __syncthreads();
+      const double id = s_div;
       const int nn = n - k - 2;
       // E^{-1} = [c -conj(b); -b a] / det applied to (x0, x1) = (D(k, j), D(k+1, j))
       for (int j = k + 2 + threadIdx.x; j < n; j += blockDim.x) {
@@ -454,6 +459,7 @@ template <>
 __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* singular) {
   __shared__ int s_piv[3];  // kind (1 or 2), row r, flag
   __shared__ int s_neg;
+  __shared__ double s_div;
   __shared__ double s_u[64], s_w[64];  // the pivot columns times the pivot's inverse, per row j
   const double alpha = (1.0 + sqrt(17.0)) / 8.0;
   if (threadIdx.x == 0) s_neg = 0;
@@ -512,7 +518,9 @@ __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* 
         if (d < 0) ++s_neg;
         if (d == 0.0) *singular = true;
       }
-      double inv = d != 0.0 ? 1.0 / d : 0.0;
+      if (threadIdx.x == 0) s_div = d != 0.0 ? 1.0 / d : 0.0;  // one division per pivot
+      __syncthreads();
+      const double inv = s_div;
       for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) s_u[j] = Bm[j * ld + k] * inv;
       __syncthreads();
       for (int idx = threadIdx.x; idx < (n - k - 1) * (n - k - 1); idx += blockDim.x) {
@@ -529,7 +537,9 @@ __device__ void bk_count<double>(double* Bm, int n, int ld, int* out_neg, bool* 
         else if (det > 0 && a + c < 0) s_neg += 2;
         if (det == 0.0) *singular = true;
       }
-      double id = det != 0.0 ? 1.0 / det : 0.0;
+      if (threadIdx.x == 0) s_div = det != 0.0 ? 1.0 / det : 0.0;
+      __syncthreads();
+      const double id = s_div;
       int nn = n - k - 2;
       // [xi0 xi1] E^{-1} [xj0; xj1], E^{-1} = [c -b; -b a] / det: the
       // factor E^{-1} [xj0; xj1] = (u_j, w_j) once per row j
@@ -572,6 +582,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
   __shared__ double s_pmin;
   __shared__ bool s_bad;
   __shared__ T s_fac[64];
+  __shared__ T s_inv;
   __shared__ int s_perm[64];
   if (threadIdx.x == 0) { s_max = 0.0; s_pmin = DBL_MAX; s_bad = false; }
   __syncthreads();
@@ -645,10 +656,12 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
       }
     __syncthreads();
     // in-place Gauss-Jordan step: column k keeps the multipliers' negatives
-    // over the pivot, row k is scaled by the pivot's reciprocal
-    const T inv = s_bad ? zero_of(T()) : recipv(Aug[k * ld + k]);
+    // over the pivot, row k is scaled by the pivot's reciprocal (one thread
+    // divides: the FP64 pipe of an SM does 2 multiply-adds per clock)
+    if (threadIdx.x == 0) s_inv = s_bad ? zero_of(T()) : recipv(Aug[k * ld + k]);
     for (int i = threadIdx.x; i < bb; i += blockDim.x) s_fac[i] = Aug[i * ld + k];
     __syncthreads();
+    const T inv = s_inv;
     for (int j = threadIdx.x; j < bb; j += blockDim.x) Aug[k * ld + j] = (j == k) ? inv : mulv(Aug[k * ld + j], inv);
     __syncthreads();
     for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
@@ -699,6 +712,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(T* __restrict
   __shared__ T A[64][64 / kDiagCluster + 1];  // this CTA's columns (row-major in i)
   __shared__ T pub_fac[2][64];
   __shared__ T pub_inv[2];
+  __shared__ T s_inv;
   __shared__ int pub_piv[2];
   __shared__ double pub_best[2];
   __shared__ double s_maxes[kDiagCluster];
@@ -766,7 +780,10 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(T* __restrict
       __syncthreads();
       const double best = pub_best[par];
       const bool now_bad = bad || !(best > 0.0) || !isfinite(best);
-      const T inv = now_bad ? zero_of(T()) : recipv(A[k][lk]);
+      // one thread divides (the FP64 pipe of an SM does 2 multiply-adds per clock)
+      if (threadIdx.x == 0) s_inv = now_bad ? zero_of(T()) : recipv(A[k][lk]);
+      __syncthreads();
+      const T inv = s_inv;
       for (int q = 0; q < kDiagCluster; ++q) {  // publish into every CTA of the cluster
         T* fac = cluster.map_shared_rank(&pub_fac[par][0], q);
         for (int i = threadIdx.x; i < bb; i += blockDim.x) fac[i] = A[i][lk];
