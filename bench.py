@@ -470,6 +470,8 @@ def run_ours(args):
                                         heavy, eig, peaks)
     if world == 1 and args.batched_passes > 0:
         line["batched_split"] = batched_systems(px, local, args.split_compare or 6, args.batched_passes)
+        line["batched_split_small"] = batched_systems(px, local, args.split_compare or 6, args.batched_passes,
+                                                      which="small")
     if world == 1 and args.serve_requests > 0:
         line["serving"] = serve_trace(px, local, args.serve_rate, args.serve_requests, args.serve_set,
                                       args.serve_fp64_budget, capacity_frac=args.serve_capacity_frac)
@@ -573,15 +575,27 @@ def split_path(px, s, mu, dE, device, dH, dS, stream, args, per60, all_shifts, r
 
 
 # ------------------------------------------------------------------ batched systems
-BATCHED = [("chain500", lambda: ns.make_chain(natoms=500, seed=21)),
-           ("fluid96", lambda: ns.make_fluid(nmol=96, seed=22)),
-           ("sheet14", lambda: ns.make_sheet(ncell=14, seed=23)),
-           ("fluid384", lambda: ns.make_fluid(nmol=384, seed=24)),
-           ("sheet23", lambda: ns.make_sheet(ncell=23, seed=25)),
-           ("chain7500", lambda: ns.make_chain(natoms=7500, seed=26))]
+BATCHED_SETS = {
+    # the six systems of the batched configuration, n = 2,000 to 30,000
+    "config": [("chain500", lambda: ns.make_chain(natoms=500, seed=21)),
+               ("fluid96", lambda: ns.make_fluid(nmol=96, seed=22)),
+               ("sheet14", lambda: ns.make_sheet(ncell=14, seed=23)),
+               ("fluid384", lambda: ns.make_fluid(nmol=384, seed=24)),
+               ("sheet23", lambda: ns.make_sheet(ncell=23, seed=25)),
+               ("chain7500", lambda: ns.make_chain(natoms=7500, seed=26))],
+    # six systems at the small end of the range (n = 1,472 to 4,000), where no
+    # single system fills the GPU
+    "small": [("chain500", lambda: ns.make_chain(natoms=500, seed=21)),
+              ("fluid96", lambda: ns.make_fluid(nmol=96, seed=22)),
+              ("sheet8", lambda: ns.make_sheet(ncell=8, seed=27)),
+              ("fluid64", lambda: ns.make_fluid(nmol=64, seed=28)),
+              ("chain1000", lambda: ns.make_chain(natoms=1000, seed=29)),
+              ("sheet12", lambda: ns.make_sheet(ncell=12, seed=30))],
+}
+BATCHED = BATCHED_SETS["config"]
 
 
-def batched_systems(px, device, split, passes, P=64):
+def batched_systems(px, device, split, passes, P=64, which="config"):
     """Six systems of uneven size (chain, sheet and bulk recipes, n = 2,000
     to 30,000), P = 64 poles each, split precision, in one group: every
     level launch covers the fronts of all six systems for a wave of poles,
@@ -592,7 +606,7 @@ def batched_systems(px, device, split, passes, P=64):
     import torch
     from oracle import dense, poles as opoles
     systems = []
-    for name, make in BATCHED:
+    for name, make in BATCHED_SETS[which]:
         s = make()
         mu, dE = ns.mu_and_delta_e(s)
         systems.append((name, s, mu, dE))
