@@ -26,6 +26,8 @@ ERR_NAMES = {0: "PEXSI_OK", -1: "PEXSI_ERR_INVALID_ARG", -2: "PEXSI_ERR_NOT_SYMM
              -4: "PEXSI_ERR_CUDA", -5: "PEXSI_ERR_BREAKDOWN", -6: "PEXSI_ERR_INTERNAL", -7: "PEXSI_ERR_CANCELLED",
              -8: "PEXSI_ERR_TIMEOUT", 1: "PEXSI_PENDING"}
 PEXSI_PENDING = 1
+PEXSI_ERR_INVALID_ARG = -1
+PEXSI_ERR_NOMEM = -3
 PEXSI_ERR_CANCELLED = -7
 PEXSI_ERR_TIMEOUT = -8
 PEXSI_ERR_BREAKDOWN = -5

@@ -259,6 +259,7 @@ OzScratch split_scratch(const pexsi_plan* p, Workspace& ws, bool real) {
 // Factor the batch in F (assembled), leaves to root.
 template <typename T>
 void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& sh, bool count, Profiler& pf) {
+  NvtxRange range("pexsi: multifrontal LDL^T");
   cudaStream_t st = ws.stream;
   DevFronts fr = p->fronts();
   // the inertia shifts (count) keep their own status words; their panel blocks
@@ -371,6 +372,7 @@ void factor_batch(const pexsi_plan* p, Workspace& ws, T* F, const BatchShifts& s
 }
 
 void selinv_batch(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Profiler& pf) {
+  NvtxRange range("pexsi: selected inversion");
   cudaStream_t st = ws.stream;
   DevFronts fr = p->fronts();
   const int b = p->b;
@@ -529,6 +531,7 @@ void run_complex_batch(const pexsi_plan* p, Workspace& ws, const double* dH, con
 int dm_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* dH, const double* dS, double mu,
              double beta, int P, double delta_e, int begin, int end, int accumulate, double* d_dm, double* d_edm,
              double* d_fdm, pexsi_dm_info* info, std::string* err) {
+  NvtxRange range("pexsi: poles (assemble, LDL^T, selected inversion, pole sum)");
   Profiler& pf = prof ? *prof : g_off;
   std::vector<std::complex<double>> z, wr, we, wf, wd;
   int rc = pole_table(beta, delta_e, P, mu, z, wr, we, wf, &wd);
@@ -597,6 +600,7 @@ int dm_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* d
 
 int inertia_range(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double* dH, const double* dS,
                   const double* shifts, int n_shifts, int64_t* counts, std::string* err) {
+  NvtxRange range("pexsi: inertia shifts (real LDL^T, Bunch-Kaufman count)");
   Profiler& pf = prof ? *prof : g_off;
   const double* S = dS ? dS : p->d_ident;
   cudaStream_t st = ws.stream;
@@ -664,6 +668,7 @@ int selinv_one(const pexsi_plan* p, Workspace& ws, const double* dH, const doubl
 namespace {
 
 void factor_batch_gen(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, bool count, Profiler& pf) {
+  NvtxRange range("pexsi: multifrontal LDU");
   cudaStream_t st = ws.stream;
   DevFronts fr = p->fronts();
   DevStatus status{ws.brk + (count ? 1 : 0), ws.minpiv + (count ? 1 : 0), ws.neg, count ? ws.dsave : nullptr,
@@ -701,6 +706,7 @@ void factor_batch_gen(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh,
 }
 
 void selinv_batch_gen(const pexsi_plan* p, Workspace& ws, const BatchShifts& sh, Profiler& pf) {
+  NvtxRange range("pexsi: two-sided selected inversion");
   cudaStream_t st = ws.stream;
   DevFronts fr = p->fronts();
   const int b = p->b;
@@ -746,6 +752,7 @@ void run_gen_batch(const pexsi_plan* p, Workspace& ws, const double2* dH, const 
 int dm_range_herm(const pexsi_plan* p, Workspace& ws, Profiler* prof, const double2* dH, const double2* dS, double mu,
                   double beta, int P, double delta_e, int begin, int end, int accumulate, double2* d_dm,
                   double2* d_edm, double2* d_fdm, pexsi_dm_info* info, std::string* err) {
+  NvtxRange range("pexsi: Hermitian poles (LDU fronts)");
   Profiler& pf = prof ? *prof : g_off;
   std::vector<std::complex<double>> z, wr, we, wf, wd;
   int rc = pole_table(beta, delta_e, P, mu, z, wr, we, wf, &wd);
@@ -921,6 +928,7 @@ int dm_range_group(const pexsi_plan* p, Workspace& ws, Profiler* prof, int wave,
                    const double* const* dS, const double* mu, const double* beta, int P, const double* delta_e,
                    int begin, int end, int accumulate, double* const* d_dm, double* const* d_edm, double* const* d_fdm,
                    pexsi_dm_info* info, const std::vector<int32_t>& f_off, std::string* err) {
+  NvtxRange range("pexsi: group of systems (merged forest)");
   Profiler& pf = prof ? *prof : g_off;
   const int nsys = int(p->sys_entry_off.size()) - 1;
   std::vector<std::vector<std::complex<double>>> z(nsys), wr(nsys), we(nsys), wf(nsys), wd(nsys);
@@ -1427,7 +1435,10 @@ int pexsi_setup(int64_t n, const int64_t* colptr, const int32_t* rowind, const i
       return rc;
     }
     std::string err;
-    rc = analyse(n, colptr, rowind, perm_or_null, p->opts.leaf_cols, p->opts.amalgamate != 0, p->sym, err);
+    {
+      NvtxRange range("pexsi: ordering and symbolic analysis");
+      rc = analyse(n, colptr, rowind, perm_or_null, p->opts.leaf_cols, p->opts.amalgamate != 0, p->sym, err);
+    }
     if (rc) {
       delete p;
       return rc;

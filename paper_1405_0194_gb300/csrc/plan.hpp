@@ -9,6 +9,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pexsi_gb300.h"
 #include "kernels.cuh"
@@ -19,6 +20,15 @@ namespace pexsi {
 int pole_table(double beta, double delta_e, int P, double mu, std::vector<std::complex<double>>& z,
                std::vector<std::complex<double>>& w_rho, std::vector<std::complex<double>>& w_E,
                std::vector<std::complex<double>>& w_F, std::vector<std::complex<double>>* w_d = nullptr);
+
+// An NVTX range over a host-side phase (visible in timeline profilers; a
+// no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct CudaError {
   cudaError_t e;

@@ -6,6 +6,9 @@
   role of the CTA returns, TMEM is freed, the later launches of the call
   return at once, and the call returns PEXSI_ERR_TIMEOUT. The context stays
   usable: a plan without injection then gives the oracle's result.
+- A device budget below one pole's workspace: the call returns
+  PEXSI_ERR_NOMEM before it allocates anything; a budget that fits a few
+  poles gives a smaller batch and the oracle's result.
 - A breakdown in an early pole batch of a chain: with inject = 2 the host
   records a breakdown of front 0 after the first batch of a call with
   accumulate = 0. Calls that accumulate keep the status, so the call that
@@ -115,3 +118,31 @@ def test_server_reports_a_breakdown_of_an_early_batch(chain):
     # four batches of 4 poles; the breakdown happened in the first
     assert rb["status"] == px.capi.PEXSI_ERR_BREAKDOWN and rb["breakdown_front"] == 0
     assert rg["status"] == 0
+
+
+def test_budget_below_one_pole_returns_nomem(chain):
+    s, mu, dE = chain
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(hbm_budget=4096))
+    try:
+        with pytest.raises(px.PexsiError) as e:
+            px.pexsi_dm(plan, s.H, s.S, mu, s.beta, 8, dE)
+        assert e.value.code == px.capi.PEXSI_ERR_NOMEM
+        assert "exceeds the HBM budget" in str(e.value)
+        assert px.pexsi_plan_get_stats(plan)["batch"] == 0  # nothing allocated
+    finally:
+        px.pexsi_plan_destroy(plan)
+    # the workspace of a 2-pole batch as the budget: the plan chooses a
+    # batch that fits it and still gives the oracle's result
+    probe = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(max_batch=2))
+    px.pexsi_inertia(probe, s.H, s.S, [mu])
+    two = px.pexsi_plan_get_stats(probe)["workspace_bytes"]
+    px.pexsi_plan_destroy(probe)
+    plan = px.pexsi_setup(s.n, s.colptr, s.rowind, opts=px.pexsi_opts_default(hbm_budget=two))
+    try:
+        dm, *_ = px.pexsi_dm(plan, s.H, s.S, mu, s.beta, 8, dE)
+        st = px.pexsi_plan_get_stats(plan)
+    finally:
+        px.pexsi_plan_destroy(plan)
+    assert 1 <= st["batch"] <= 2 and st["workspace_bytes"] <= two
+    dm0, *_ = dense.density_matrices(s.n, s.colptr, s.rowind, s.H, s.S, mu, s.beta, 8, dE)
+    assert np.max(np.abs(dm - dm0)) <= 1e-10
