@@ -260,6 +260,15 @@ __device__ __forceinline__ void tmem_ld8_nw(uint32_t addr, uint32_t (&v)[8]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 32 lanes x 16 consecutive TMEM columns, without the wait.
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t addr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
@@ -957,17 +966,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_oz_gemm(void* __restrict__ 
       unsigned long long acc[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) acc[c] = 0ull;
-      for (int D = 2; D <= S + 1; ++D) {
+      for (int D = 2; D <= S + 1; ++D) {  // one TMEM round trip per diagonal
         const int sh = 7 * (S + 1 - D);
+        uint32_t v[32];
+        tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32), v);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          uint32_t v[16];
-          tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 16), v);
-#pragma unroll
-          for (int c = 0; c < 16; ++c)
-            acc[hh * 16 + c] +=
-                static_cast<unsigned long long>(static_cast<long long>(__float2int_rn(__uint_as_float(v[c])))) << sh;
-        }
+        for (int c = 0; c < 32; ++c)
+          acc[c] += static_cast<unsigned long long>(static_cast<long long>(__float2int_rn(__uint_as_float(v[c])))) << sh;
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
@@ -1274,23 +1279,27 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
 #pragma unroll 1
       for (int hh = 0; hh < 4; ++hh) {  // 8 output columns at a time
         uint32_t w[16];
-        if (pending > 0) {
-          tmem_ld16(tsum + hh * 16, w);
-        } else {
+        // the partial sum and every diagonal's 8 columns in one TMEM round trip
+        with_slices(S, [&](auto SC) {
+          constexpr int SS = decltype(SC)::value;
+          uint32_t v[SS][8];
+          if (pending > 0) tmem_ld16_nw(tsum + hh * 16, w);
+          const uint32_t ta = tmem + (uint32_t(q * 32) << 16) + uint32_t(h * 32 + hh * 8);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) w[c] = 0u;
-        }
-        for (int D = 2; D <= S + 1; D += 2) {  // two diagonals per TMEM round trip
-          const uint32_t ta = tmem + (uint32_t(q * 32) << 16) + uint32_t((D - 2) * 64 + h * 32 + hh * 8);
-          uint32_t v0[8], v1[8];
-          tmem_ld8_nw(ta, v0);
-          if (D + 1 <= S + 1) tmem_ld8_nw(ta + 64, v1);
+          for (int t = 0; t < SS; ++t) tmem_ld8_nw(ta + uint32_t(t * 64), v[t]);
           tmem_wait_ld();
-          if (D + 1 <= S + 1)
-            acc_add_pair8(w, v0, v1, 7 * (S - D));
-          else
-            acc_add8(w, v0, 7 * (S + 1 - D));
-        }
+          if (pending == 0) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) w[c] = 0u;
+          }
+#pragma unroll
+          for (int D = 2; D <= SS + 1; D += 2) {  // diagonal D at columns 64 (D - 2)
+            if (D + 1 <= SS + 1)
+              acc_add_pair8(w, v[D - 2], v[D - 1], 7 * (SS - D));
+            else
+              acc_add8(w, v[D - 2], 7 * (SS + 1 - D));
+          }
+        });
         if (flush) {
           // K > 2048: move the exact partial sum into this thread's own
           // Y[S,P] entries (rounded once), which no operand of the launch reads
