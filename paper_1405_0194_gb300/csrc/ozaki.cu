@@ -304,26 +304,41 @@ __device__ __forceinline__ void acc_add8(uint32_t (&w)[16], const uint32_t (&v)[
   }
 }
 
-// w_c += (v0_c 2^7 + v1_c) 2^sh for the accumulators of two adjacent
-// diagonals. When every |v| of the warp is below 2^22 both convert exactly by
-// the add-and-subtract and the pair fits in 32 bits (below 2^30), so one
-// 64-bit shift-add serves two diagonals.
-__device__ __forceinline__ void acc_add_pair8(uint32_t (&w)[16], const uint32_t (&v0)[8], const uint32_t (&v1)[8],
-                                              int sh) {
+// w_c += sum over the diagonals D = 2 .. S + 1 of v[D - 2]_c 2^(7 (S + 1 - D)),
+// c < 8, for the FP32 accumulators of all S diagonals at once. When every
+// |v| of the warp is below 2^22, each converts by the add-and-subtract and
+// adjacent diagonals pair in 32 bits: the biased words h = 0x4B400000 + a
+// and l = 0x4B400000 + b give a 2^7 + b = 128 h + l - 129 0x4B400000 modulo
+// 2^32, exact since |a 2^7 + b| < 2^30; one multiply-add per pair and one
+// 64-bit multiply-add by 2^shift. Otherwise each diagonal takes the
+// conversion instruction.
+template <int S>
+__device__ __forceinline__ void acc_add_diags8(uint32_t (&w)[16], const uint32_t (&v)[S][8]) {
   float mx = 0.0f;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) mx = fmaxf(mx, fmaxf(fabsf(__uint_as_float(v0[c])), fabsf(__uint_as_float(v1[c]))));
+  for (int t = 0; t < S; ++t)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) mx = fmaxf(mx, fabsf(__uint_as_float(v[t][c])));
   if (!__all_sync(0xFFFFFFFFu, mx < 4194304.0f)) {
-    acc_add8(w, v0, sh + 7);
-    acc_add8(w, v1, sh);
+#pragma unroll
+    for (int D = 2; D <= S + 1; ++D) acc_add8(w, v[D - 2], 7 * (S + 1 - D));
     return;
   }
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int a = __float_as_int(__uint_as_float(v0[c]) + 12582912.0f) - 0x4B400000;
-    const int b = __float_as_int(__uint_as_float(v1[c]) + 12582912.0f) - 0x4B400000;
     unsigned long long a64 = (static_cast<unsigned long long>(w[2 * c + 1]) << 32) | w[2 * c];
-    a64 += static_cast<unsigned long long>(static_cast<long long>(a * 128 + b)) << sh;
+#pragma unroll
+    for (int D = 2; D <= S + 1; D += 2) {
+      const uint32_t h = __float_as_uint(__uint_as_float(v[D - 2][c]) + 12582912.0f);
+      if (D + 1 <= S + 1) {
+        const uint32_t l = __float_as_uint(__uint_as_float(v[D - 1][c]) + 12582912.0f);
+        const int pr = int(h * 128u + l - 0x4B400000u * 129u);
+        a64 += static_cast<unsigned long long>(static_cast<long long>(pr) * (1LL << (7 * (S - D))));
+      } else {
+        const int a = int(h - 0x4B400000u);
+        a64 += static_cast<unsigned long long>(static_cast<long long>(a) * (1LL << (7 * (S + 1 - D))));
+      }
+    }
     w[2 * c] = uint32_t(a64);
     w[2 * c + 1] = uint32_t(a64 >> 32);
   }
@@ -1292,13 +1307,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
 #pragma unroll
             for (int c = 0; c < 16; ++c) w[c] = 0u;
           }
-#pragma unroll
-          for (int D = 2; D <= SS + 1; D += 2) {  // diagonal D at columns 64 (D - 2)
-            if (D + 1 <= SS + 1)
-              acc_add_pair8(w, v[D - 2], v[D - 1], 7 * (SS - D));
-            else
-              acc_add8(w, v[D - 2], 7 * (SS + 1 - D));
-          }
+          acc_add_diags8<SS>(w, v);  // diagonal D at columns 64 (D - 2)
         });
         if (flush) {
           // K > 2048: move the exact partial sum into this thread's own
