@@ -160,14 +160,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
-// 16-byte asynchronous copy global -> shared through L2; zero-filled when
-// !valid (no bytes are read then).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -238,16 +230,6 @@ __device__ __forceinline__ void mma_slice(int c, uint32_t acc, uint64_t a1, uint
       mma_group<CPLX, KSTEPS, BLK, 0, 1>(acc, a1, a2, br, bi, first);
       break;
   }
-}
-
-// 32 lanes x 16 / 32 consecutive TMEM columns of this warp's lane quarter.
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
 }
 
 // 32 lanes x 8 consecutive TMEM columns, without the wait: tcgen05.wait::ld
@@ -1050,8 +1032,7 @@ constexpr int kFSlot = kFSlotA + 6 * kFSliceB;
 constexpr int kFChunk = 256 / kFK;          // K tiles per exact chunk
 constexpr int kFWorkers = 8;
 constexpr int kFThreads = (kFWorkers + 1) * 32;
-constexpr int kFStage = 4 * 32 * 8 * 16;  // FP64 entries of A for one half's next tile (16 KiB)
-constexpr int kFSmem = kFSlots * kFSlot + 2 * kFStage;
+constexpr int kFSmem = kFSlots * kFSlot;
 
 // Row exponents of A = Y[S,S] from the row maxima of Y (A groups, 256 rows
 // each) and the slices of B = L[S,P] in the 16-deep tile layout (B groups, 8
@@ -1336,20 +1317,17 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
       pending = (multi && pending + 1 == kOzFlush && ch != nchunks - 1) ? 0 : pending + 1;
       return true;
     };
-    // the FP64 entries of A for this half's next tile are copied into
-    // shared memory one tile ahead (entry u of thread `item` at u * 2 KiB +
-    // 16 item), so that their latency hides behind the cutting of the current
-    // one; each thread reads back only what it copied
-    const uint32_t stage = smem_u32(osm + kFSlots * kFSlot + half * kFStage) + uint32_t(item * 16);
+    // the FP64 entries of A for this half's next tile are loaded into
+    // registers one tile ahead, so that their latency hides behind the
+    // cutting of the current one (no shared-memory staging: the MMAs' operand
+    // fetch already takes most of the shared-memory bandwidth)
+    double2 an[8];
     auto load_a = [&](int kt) {
-      if (kt >= nkt) return;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int k = (kt0 + kt) * kFK + oct * 8 + u;
-        const bool in = rowok && k < d.mp;
-        cp_async16(stage + uint32_t(u * 2048), col + (in ? k : 0), in);
+        an[u] = (kt < nkt && rowok && k < d.mp) ? col[k] : make_double2(0.0, 0.0);
       }
-      cp_async_commit();
     };
     load_a(half);
     for (int kt = half; kt < nkt && ok; kt += 2) {
@@ -1394,23 +1372,19 @@ __global__ void __launch_bounds__(kFThreads, 1) k_oz_tak_fused(double2* __restri
         with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(YB, pb, pb + S * kFBlk, nullptr, kFBlk); });
       }
       // A: 8 entries of row r at k = 16 kt + 8 oct .. + 7, cut into Ar, Ai, -Ar words
-      cp_async_wait_all();
       long long Y[16];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        double2 v;
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(stage + uint32_t(u * 2048)) : "memory");
-        Y[2 * u] = fixed_of(v.x, scale, e, S) + bias;
-        Y[2 * u + 1] = fixed_point(v.y, e, S) + bias;
+        Y[2 * u] = fixed_of(an[u].x, scale, e, S) + bias;
+        Y[2 * u + 1] = fixed_point(an[u].y, e, S) + bias;
       }
-      load_a(kt + 2);  // after this thread's reads of the buffer, in program order
+      load_a(kt + 2);
       uint8_t* ps = sbase + wbase;
       with_slices(S, [&](auto SC) { store_slices_c<decltype(SC)::value>(Y, ps, ps + kFBlk, ps + 2 * kFBlk, kFSliceA); });
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_arrive(smem_u32(&full_a[slot]));
     }
     while (ok && drained < nchunks) ok = drain(drained++);
-    cp_async_wait_all();  // after a failure too: no staging copy outlives the CTA
   }
 
   __syncthreads();
