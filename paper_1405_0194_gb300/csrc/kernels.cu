@@ -59,15 +59,30 @@ __device__ __forceinline__ double scalev(double a, double s) { return a * s; }
 __device__ __forceinline__ double2 scalev(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double absv(double a) { return fabs(a); }
 __device__ __forceinline__ double absv(double2 a) { return hypot(a.x, a.y); }
-__device__ __forceinline__ double recipv(double a) { return 1.0 / a; }
-__device__ __forceinline__ double2 recipv(double2 a) {
-  // 1/(x+iy) with scaling against overflow (Smith's method)
-  if (fabs(a.x) >= fabs(a.y)) {
-    double r = a.y / a.x, d = a.x + a.y * r;
-    return make_double2(1.0 / d, -r / d);
-  }
-  double r = a.x / a.y, d = a.x * r + a.y;
-  return make_double2(r / d, -1.0 / d);
+// Magnitudes for partial pivoting in the block inverses: |Re| + |Im| (the
+// norm of LAPACK's complex i?amax). The search compares FP32 copies (the
+// FP64 pipe of an SM does 2 operations per clock, and a search is on the
+// critical path of every pivot step); the chosen pivot's magnitude for the
+// pivot ratio is taken in FP64.
+__device__ __forceinline__ float pivmag(double a) { return fabsf(__double2float_rn(a)); }
+__device__ __forceinline__ float pivmag(double2 a) {
+  return fabsf(__double2float_rn(a.x)) + fabsf(__double2float_rn(a.y));
+}
+__device__ __forceinline__ double mag1(double a) { return fabs(a); }
+__device__ __forceinline__ double mag1(double2 a) { return fabs(a.x) + fabs(a.y); }
+// Reciprocal of a pivot: 1 / a by the correctly rounded reciprocal; for
+// complex a = x + iy, (x - iy) / (x^2 + y^2) with x and y first scaled by a
+// power of two (exact) that puts max(|x|, |y|) in [1, 2), so that the sum of
+// squares neither overflows nor underflows; one reciprocal instead of the
+// three divisions of Smith's method.
+__device__ __forceinline__ double recip_piv(double a) { return __drcp_rn(a); }
+__device__ __forceinline__ double2 recip_piv(double2 a) {
+  const double m = fmax(fabs(a.x), fabs(a.y));
+  const int e = min(((__double2hiint(m) >> 20) & 0x7FF) - 1023, 1022);  // exponent of m (subnormal: -1023)
+  const double sc = __hiloint2double((1023 - e) << 20, 0);             // 2^-e
+  const double x = a.x * sc, y = a.y * sc;
+  const double r = __drcp_rn(fma(x, x, y * y));
+  return make_double2(x * r * sc, -(y * r) * sc);
 }
 __device__ __forceinline__ bool finitev(double a) { return isfinite(a); }
 __device__ __forceinline__ bool finitev(double2 a) { return isfinite(a.x) && isfinite(a.y); }
@@ -592,7 +607,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
     // symmetric fronts hold the lower triangle; LDU fronts (GEN) both
     T v = (GEN || i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
     Aug[i * ld + j] = v;
-    lmax = fmax(lmax, absv(v));
+    lmax = fmax(lmax, mag1(v));
   }
   // block max |entry| for the pivot ratio
   for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -630,18 +645,19 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
 
   for (int k = 0; k < bb; ++k) {
     if (threadIdx.x < 32) {
-      double best = -1.0;
+      float bestf = -1.0f;
       int bi = k;
       for (int i = k + threadIdx.x; i < bb; i += 32) {
-        double a = absv(Aug[i * ld + k]);
-        if (a > best) { best = a; bi = i; }
+        const float a = pivmag(Aug[i * ld + k]);
+        if (a > bestf) { bestf = a; bi = i; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        const float ob = __shfl_xor_sync(0xffffffffu, bestf, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > bestf || (ob == bestf && oi < bi)) { bestf = ob; bi = oi; }
       }
       if (threadIdx.x == 0) {
+        const double best = mag1(Aug[bi * ld + k]);
         s_piv = bi;
         s_pmin = fmin(s_pmin, best);
         if (!(best > 0.0) || !isfinite(best)) s_bad = true;
@@ -658,7 +674,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
     // in-place Gauss-Jordan step: column k keeps the multipliers' negatives
     // over the pivot, row k is scaled by the pivot's reciprocal (one thread
     // divides: the FP64 pipe of an SM does 2 multiply-adds per clock)
-    if (threadIdx.x == 0) s_inv = s_bad ? zero_of(T()) : recipv(Aug[k * ld + k]);
+    if (threadIdx.x == 0) s_inv = s_bad ? zero_of(T()) : recip_piv(Aug[k * ld + k]);
     for (int i = threadIdx.x; i < bb; i += blockDim.x) s_fac[i] = Aug[i * ld + k];
     __syncthreads();
     const T inv = s_inv;
@@ -734,7 +750,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(T* __restrict
     const int i = idx % bb, jl = idx / bb, j = c0 + jl;
     const T v = (GEN || i >= j) ? Fd[i + int64_t(m) * j] : Fd[j + int64_t(m) * i];
     A[i][jl] = v;
-    lmax = fmax(lmax, absv(v));
+    lmax = fmax(lmax, mag1(v));
   }
   if (st.dsave) {  // inertia shifts: this CTA's columns of the block before inversion, counted later
     T* save = reinterpret_cast<T*>(st.dsave) + int64_t(pb) * st.dsave_stride + int64_t(st.col0[f] + p0) * b;
@@ -755,20 +771,20 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(T* __restrict
     if (r == owner) {
       const int lk = k - c0;
       if (threadIdx.x < 32) {
-        double best = -1.0;
+        float bestf = -1.0f;
         int bi = k;
         for (int i = k + threadIdx.x; i < bb; i += 32) {
-          const double a = absv(A[i][lk]);
-          if (a > best) { best = a; bi = i; }
+          const float a = pivmag(A[i][lk]);
+          if (a > bestf) { bestf = a; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const float ob = __shfl_xor_sync(0xffffffffu, bestf, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          if (ob > bestf || (ob == bestf && oi < bi)) { bestf = ob; bi = oi; }
         }
         if (threadIdx.x == 0) {
           pub_piv[par] = bi;
-          pub_best[par] = best;
+          pub_best[par] = mag1(A[bi][lk]);
         }
       }
       __syncthreads();
@@ -781,17 +797,19 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(T* __restrict
       const double best = pub_best[par];
       const bool now_bad = bad || !(best > 0.0) || !isfinite(best);
       // one thread divides (the FP64 pipe of an SM does 2 multiply-adds per clock)
-      if (threadIdx.x == 0) s_inv = now_bad ? zero_of(T()) : recipv(A[k][lk]);
+      if (threadIdx.x == 0) s_inv = now_bad ? zero_of(T()) : recip_piv(A[k][lk]);
       __syncthreads();
       const T inv = s_inv;
-      for (int q = 0; q < kDiagCluster; ++q) {  // publish into every CTA of the cluster
-        T* fac = cluster.map_shared_rank(&pub_fac[par][0], q);
-        for (int i = threadIdx.x; i < bb; i += blockDim.x) fac[i] = A[i][lk];
-        if (threadIdx.x == 0) {
-          *cluster.map_shared_rank(&pub_inv[par], q) = inv;
-          *cluster.map_shared_rank(&pub_piv[par], q) = pr;
-          *cluster.map_shared_rank(&pub_best[par], q) = best;
-        }
+      // publish into every CTA of the cluster, all (CTA, row) pairs at once
+      for (int idx = threadIdx.x; idx < kDiagCluster * bb; idx += blockDim.x) {
+        const int q = idx / bb, i = idx - q * bb;
+        *cluster.map_shared_rank(&pub_fac[par][i], q) = A[i][lk];
+      }
+      if (threadIdx.x < kDiagCluster) {
+        const int q = threadIdx.x;
+        *cluster.map_shared_rank(&pub_inv[par], q) = inv;
+        *cluster.map_shared_rank(&pub_piv[par], q) = pr;
+        *cluster.map_shared_rank(&pub_best[par], q) = best;
       }
     }
     cluster.sync();
