@@ -214,12 +214,9 @@ def _full_size_all_poles(full_fluid, split, tol):
     assert float(torch.max(torch.abs(tot - out))) <= tol
     assert abs(full["trace_fdm_s"] - tr[2]) <= 1e-8 * max(1.0, abs(tr[2]))
     assert cnt.tolist() == [int(np.sum(lam < x)) for x in shifts]
-    if split and dtr > 1e-8:
-        # 1e-8 on N = 11,709 is 8.5e-13 relative; the 42-bit row-scaled fixed
-        # point of the six slices gives each product about 2^-43 of its row
-        # maximum, and the trace sums 5.7e6 weighted entries. Recorded, not
-        # hidden: every other bound of this test holds.
-        pytest.xfail(f"split path: |Tr[DM S] - N_P| = {dtr:.2e} > 1e-8 at fluid512 (60 poles)")
+    # the trace invariant Tr[DM S] = N_P (Eq. Nmu) to 1e-8 on both paths:
+    # 8.5e-13 relative to N = 11,709; the split path's six slices give each
+    # product about 2^-43 of its row maximum over 5.7e6 weighted entries
     assert dtr <= 1e-8
 
 
