@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv(T* __restrict__ F, De
     __syncthreads();
     // in-place Gauss-Jordan step: column k keeps the multipliers' negatives
     // over the pivot, row k is scaled by the pivot's reciprocal (one thread
-    // divides: the FP64 pipe of an SM does 2 multiply-adds per clock)
+    // takes the reciprocal: the FP64 pipe of an SM does 2 multiply-adds per clock)
     if (threadIdx.x == 0) s_inv = s_bad ? zero_of(T()) : recip_piv(Aug[k * ld + k]);
     for (int i = threadIdx.x; i < bb; i += blockDim.x) s_fac[i] = Aug[i * ld + k];
     __syncthreads();
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_inv_cluster(T* __restrict
       __syncthreads();
       const double best = pub_best[par];
       const bool now_bad = bad || !(best > 0.0) || !isfinite(best);
-      // one thread divides (the FP64 pipe of an SM does 2 multiply-adds per clock)
+      // one thread takes the reciprocal (the FP64 pipe of an SM does 2 multiply-adds per clock)
       if (threadIdx.x == 0) s_inv = now_bad ? zero_of(T()) : recip_piv(A[k][lk]);
       __syncthreads();
       const T inv = s_inv;
