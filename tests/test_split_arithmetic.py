@@ -105,3 +105,32 @@ def test_fast_conversion_and_pairing():
     assert np.array_equal(t, v)
     a, b = v[:50000], v[50000:100000]
     assert np.max(np.abs(a * 128 + b)) < 2 ** 30
+
+
+@pytest.mark.parametrize("S", [2, 3, 4, 5, 6])
+def test_biased_word_pairing_and_drain_sum(S):
+    """The drain's 32-bit pairing on the biased words: h = bits(a + 1.5 2^23),
+    l = bits(b + 1.5 2^23) give a 2^7 + b = 128 h + l - 129 * 0x4B400000
+    modulo 2^32 (exact, as |a 2^7 + b| < 2^30); summed with the pairs' powers
+    of two (diagonals D and D + 1 at 2^(7 (S - D)), a last odd diagonal alone)
+    it equals sum_D acc_D 2^(7 (S + 1 - D)) in int64."""
+    rng = np.random.default_rng(20 + S)
+    n = 20000
+    acc = rng.integers(-(1 << 22) + 1, 1 << 22, size=(S, n))  # acc[D - 2], |v| < 2^22
+    acc[:, 0], acc[:, 1], acc[:, 2] = -(1 << 22) + 1, (1 << 22) - 1, 0  # extremes
+    acc[::2, 3], acc[1::2, 3] = (1 << 22) - 1, -(1 << 22) + 1
+    f = acc.astype(np.float32)
+    words = (f + np.float32(12582912.0)).view(np.uint32).astype(np.uint64)
+    total = np.zeros(n, dtype=np.int64)
+    for D in range(2, S + 2, 2):
+        h = words[D - 2]
+        if D + 1 <= S + 1:
+            l = words[D - 1]
+            pr = ((h * 128 + l - 0x4B400000 * 129) % (1 << 32)).astype(np.int64)
+            pr = np.where(pr >= 1 << 31, pr - (1 << 32), pr)
+            assert np.array_equal(pr, acc[D - 2] * 128 + acc[D - 1])
+            total += pr * (1 << (7 * (S - D)))
+        else:
+            total += (h.astype(np.int64) - 0x4B400000) * (1 << (7 * (S + 1 - D)))
+    want = sum(acc[D - 2].astype(object) * (1 << (7 * (S + 1 - D))) for D in range(2, S + 2))
+    assert all(int(t) == int(w) for t, w in zip(total, want))
