@@ -63,8 +63,10 @@ __device__ __forceinline__ double absv(double2 a) { return hypot(a.x, a.y); }
 // norm of LAPACK's complex i?amax). The search compares FP32 copies (the
 // FP64 pipe of an SM does 2 operations per clock, and a search is on the
 // critical path of every pivot step); the chosen pivot's magnitude for the
-// pivot ratio is taken in FP64. Entries below the FP32 range compare as zero,
-// so a column that small reports a breakdown rather than an inaccurate pivot.
+// pivot ratio is taken in FP64. Entries below the FP32 range (1e-45) compare
+// as zero: in a column whose entries all lie below it the search keeps the
+// diagonal entry, unpivoted (far outside the scale of H - zS here; a zero or
+// relatively tiny pivot still reports a breakdown through the pivot ratio).
 __device__ __forceinline__ float pivmag(double a) { return fabsf(__double2float_rn(a)); }
 __device__ __forceinline__ float pivmag(double2 a) {
   return fabsf(__double2float_rn(a.x)) + fabsf(__double2float_rn(a.y));
