@@ -125,7 +125,7 @@ typedef struct pexsi_dm_info {
   double trace_dm_s;       /* Tr[DM S] = N_e (Eq. Nmu); computed on the device   */
   double trace_edm_s;      /* Tr[EDM S]                                          */
   double trace_fdm_s;      /* Tr[FDM S] (grand potential)                        */
-  double min_pivot_ratio;  /* min over diagonal blocks of |pivot| / max |entry| */
+  double min_pivot_ratio;  /* min over diagonal blocks of |pivot| / max |entry|, |z| = |Re z| + |Im z| */
   double ms_total;         /* wall time of the call (device events)             */
   double gemm_flops;       /* algorithmic GEMM flops executed by the call       */
   int32_t n_poles;         /* poles evaluated by the call                       */
